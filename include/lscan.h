@@ -1,0 +1,182 @@
+/*
+ * lscan.h -- C ABI of the GB300 single-pass scan library (liblscan.so).
+ *
+ * Operation (LightScan, Section 1): given an associative operator (+) and
+ * x_0..x_{N-1}, the inclusive scan writes y_j = x_0 (+) ... (+) x_j and the
+ * exclusive scan writes y_j = x_0 (+) ... (+) x_{j-1}, with y_0 = identity
+ * (0 for add, INT32_MIN / -infinity for max).
+ *
+ * Method (Section 4): the array is cut into tiles of L elements; each tile is
+ * scanned in registers by one thread block (thread-serial scan, warp-shuffle
+ * Hillis-Steele scan of thread totals as in Algorithm 2, block scan of warp
+ * totals as in Algorithm 3), the carry between tiles travels through per-tile
+ * status words in L2 (Section 4.3, Algorithm 4; here either the paper's
+ * chained neighbour-to-neighbour hand-off or a decoupled look-back), and each
+ * tile applies its carry and stores y once (Section 4.4, Algorithm 5).  Every
+ * element of x is read once and every element of y written once (Section 1,
+ * contribution (i)); y may equal x (in-place, Section 4.5).
+ *
+ * Conventions shared by every entry point:
+ *  - x, y are DEVICE pointers owned by the caller; any element-aligned address
+ *    is accepted (16-byte-aligned x and y take the TMA bulk-copy path).
+ *  - y == x is allowed when input and output elements have the same size;
+ *    any other overlap of [x, x+n) and [y, y+n) returns LSCAN_ERR_INVALID.
+ *  - n == 0 returns LSCAN_OK without a launch; n < 0 is LSCAN_ERR_INVALID.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous: argument errors are returned at once; errors the
+ *    device detects (a carry or tile-ring wait that ran out of time) are
+ *    latched in the stream's device error word and returned by
+ *    lscan_stream_status().
+ *  - Scratch (per-tile status words, tile ticket, epoch and error word) is
+ *    owned by the library, one set per (device, stream), grown on demand with
+ *    cudaMalloc and released by lscan_shutdown().  Growing it is not allowed
+ *    while the stream is being captured; call lscan_reserve() first.
+ *  - Different streams may be used from different host threads concurrently;
+ *    two calls on the same stream are ordered by the stream.
+ *  - Output dtype equals the input dtype, except bf16 add, which writes fp32
+ *    unless lscan_options.out_dtype asks for bf16.
+ *  - int32 add wraps modulo 2^32; max keeps the earlier element on ties
+ *    (so +0/-0 ties keep the first one's bits); NaN inputs are outside the
+ *    contract.
+ */
+#ifndef LSCAN_H
+#define LSCAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LSCAN_ADD = 0, LSCAN_MAX = 1 } lscan_op;
+
+typedef enum { LSCAN_I32 = 0, LSCAN_F32 = 1, LSCAN_BF16 = 2 } lscan_dtype;
+
+typedef enum {
+    LSCAN_OK = 0,
+    LSCAN_ERR_INVALID = 1,     /* bad argument (pointer, size, overlap, ...) */
+    LSCAN_ERR_UNSUPPORTED = 2, /* combination not built (op, dtype, config) */
+    LSCAN_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    LSCAN_ERR_TIMEOUT = 4,     /* a device-side carry wait ran out of time */
+    LSCAN_ERR_NOMEM = 5,       /* device allocation or HBM budget exhausted */
+    LSCAN_ERR_BUSY = 6,        /* scratch growth needed during stream capture */
+    LSCAN_ERR_DEVICE = 7       /* the device latched an unclassified error */
+} lscan_status;
+
+/* Float-add precision of the cross-tile carry chain (the one step whose
+ * rounding error grows with N / L).  Integer and max scans are exact and
+ * ignore this field. */
+typedef enum {
+    LSCAN_PREC_DEFAULT = 0,     /* = LSCAN_PREC_F64_CARRY */
+    LSCAN_PREC_F32_CARRY = 1,   /* fp32 in tile, fp32 carry chain (plain) */
+    LSCAN_PREC_F64_CARRY = 2,   /* fp32 in tile, FP64 carry chain */
+    LSCAN_PREC_COMPENSATED = 3  /* fp32 hi/lo pairs in tile, FP64 carry */
+} lscan_precision;
+
+/* Inter-tile carry protocol (Section 4.3). */
+typedef enum {
+    LSCAN_CARRY_AUTO = 0,     /* the tuned choice (decoupled look-back) */
+    LSCAN_CARRY_LOOKBACK = 1, /* decoupled look-back over a 32-tile window */
+    LSCAN_CARRY_CHAINED = 2   /* wait for the left neighbour only (Alg. 4) */
+} lscan_carry;
+
+/* Optional per-call settings; pass NULL for all defaults.  Zero in any field
+ * means "default / tuned". */
+typedef struct lscan_options {
+    int32_t out_dtype;   /* 0 or -1 = default; LSCAN_F32 / LSCAN_BF16 select
+                            the output of a bf16 add */
+    int32_t precision;   /* lscan_precision */
+    int32_t carry;       /* lscan_carry */
+    int32_t config;      /* 0 = tuned; 1..lscan_num_configs() pick a
+                            bulk-copy tile configuration */
+    int32_t max_ctas;    /* cap on persistent CTAs, 0 = occupancy x SMs */
+    int32_t reserved[3];
+} lscan_options;
+
+/* Single-array scan (Section 4; Algorithm 1).  x: n input elements, y: n
+ * output elements (layout: contiguous, element type from dtype/out_dtype). */
+lscan_status lscan_inclusive(lscan_op op, lscan_dtype dtype, const void *x,
+                             void *y, int64_t n, void *stream);
+lscan_status lscan_exclusive(lscan_op op, lscan_dtype dtype, const void *x,
+                             void *y, int64_t n, void *stream);
+/* Same with options and an inclusive flag (1 = inclusive, 0 = exclusive). */
+lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
+                        const void *x, void *y, int64_t n,
+                        const lscan_options *opts, void *stream);
+
+/* Batched scan of n_seg independent arrays stored back to back in x (and y):
+ * segment s is elements [offsets[s], offsets[s+1]).  d_offsets is a DEVICE
+ * array of n_seg+1 int64, non-decreasing, offsets[0] = 0 and
+ * offsets[n_seg] = n_total (n_total passed by the caller so that no
+ * device-to-host read is needed).  One persistent launch; tiles span segment
+ * boundaries and the carry restarts at every segment head.  Malformed
+ * offsets never cause an out-of-bounds access; they give undefined results.
+ * (Not in the paper: the batched pattern of this library.) */
+lscan_status lscan_batched(lscan_op op, lscan_dtype dtype, int inclusive,
+                           const void *x, void *y, const int64_t *d_offsets,
+                           int64_t n_seg, int64_t n_total,
+                           const lscan_options *opts, void *stream);
+
+/* A scan captured once into a CUDA graph (one kernel node) with a private
+ * scratch set, replayed by lscan_graph_launch.  The pointers, sizes and
+ * options are fixed at creation.  Replays of one graph must be ordered (same
+ * stream or synchronised) because they share that scratch.  The kernel
+ * re-arms the scratch at the end of each launch, so a replay needs no memset.
+ * (CUDA-graph capture is this library's batched pattern, not the paper's.) */
+typedef struct lscan_graph lscan_graph;
+lscan_status lscan_graph_create_scan(lscan_op op, lscan_dtype dtype,
+                                     int inclusive, const void *x, void *y,
+                                     int64_t n, const lscan_options *opts,
+                                     lscan_graph **out);
+lscan_status lscan_graph_create_batched(lscan_op op, lscan_dtype dtype,
+                                        int inclusive, const void *x, void *y,
+                                        const int64_t *d_offsets, int64_t n_seg,
+                                        int64_t n_total,
+                                        const lscan_options *opts,
+                                        lscan_graph **out);
+lscan_status lscan_graph_launch(lscan_graph *g, void *stream);
+/* Synchronises the device and returns/clears the graph's device error. */
+lscan_status lscan_graph_status(lscan_graph *g);
+void lscan_graph_destroy(lscan_graph *g);
+
+/* Waits for the stream, then returns and clears its latched device error:
+ * LSCAN_OK or LSCAN_ERR_TIMEOUT (LSCAN_ERR_CUDA if a CUDA call failed). */
+lscan_status lscan_stream_status(void *stream);
+
+/* Makes sure the stream's scratch holds status words for scans of up to
+ * max_elems elements (all configurations), so that later calls on the
+ * stream never allocate (e.g. before CUDA-graph capture). */
+lscan_status lscan_reserve(void *stream, int64_t max_elems);
+
+/* Frees every scratch buffer, captured graph and tuning entry. */
+void lscan_shutdown(void);
+
+const char *lscan_strerror(lscan_status s);
+const char *lscan_version(void);
+
+/* Number of kernels this library has launched in this process (used to
+ * count launches inside a timed region). */
+uint64_t lscan_launch_count(void);
+
+/* Upper bound, in nanoseconds, on any device-side wait (carry flags, bulk
+ * copy barriers).  A wait that runs out sets the stream's error word to
+ * LSCAN_ERR_TIMEOUT and the kernel finishes without hanging.  Default 1 s. */
+lscan_status lscan_set_wait_limit_ns(uint64_t ns);
+
+/* Fault injection for tests: the next launch on any stream skips publishing
+ * the status word of tile `tile` (-1 disables), so that its successors'
+ * waits run out and the timeout path is exercised on the host's request. */
+lscan_status lscan_debug_skip_publish(int64_t tile);
+
+/* Describes a tile configuration: writes items per thread, consumer threads
+ * per CTA, pipeline stages and tile length L for dtype `dtype`. */
+lscan_status lscan_config_info(int32_t config, lscan_dtype dtype,
+                               int32_t *items, int32_t *threads,
+                               int32_t *stages, int32_t *tile);
+int32_t lscan_num_configs(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSCAN_H */

@@ -1,0 +1,163 @@
+"""GB300-native single-pass scan (LightScan, arXiv 1604.04815), torch front.
+
+Everything below marshals torch tensors into the C ABI of liblscan.so
+(include/lscan.h); every step of the scan runs in the library's CUDA kernels.
+torch is used for device memory and streams only.
+
+    import paper_1604_04815_gb300 as lscan
+    y = lscan.inclusive(x)                 # add, x: int32/float32/bfloat16
+    y = lscan.exclusive(x, op="max")
+    y = lscan.batched(x, offsets)          # offsets: int64 cuda tensor [S+1]
+"""
+import torch
+
+from . import _lib
+from ._lib import LscanError, load  # noqa: F401
+
+_DT = {torch.int32: _lib.LSCAN_I32, torch.float32: _lib.LSCAN_F32,
+       torch.bfloat16: _lib.LSCAN_BF16}
+_TORCH_DT = {_lib.LSCAN_I32: torch.int32, _lib.LSCAN_F32: torch.float32,
+             _lib.LSCAN_BF16: torch.bfloat16}
+_OPS = {"add": _lib.LSCAN_ADD, "max": _lib.LSCAN_MAX}
+_PREC = {None: 0, "default": 0, "f32": 1, "plain": 1, "f64": 2,
+         "compensated": 3, "comp": 3}
+_CARRY = {None: 0, "auto": 0, "lookback": 1, "chained": 2}
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def out_dtype_for(op, dtype, out_dtype=None):
+    """Output torch dtype of a scan (bf16 add writes fp32 by default)."""
+    if out_dtype is not None:
+        return out_dtype
+    if op == "add" and dtype == torch.bfloat16:
+        return torch.float32
+    return dtype
+
+
+def _options(op, x_dtype, out_dtype, precision, carry, config, max_ctas):
+    od = 0
+    if out_dtype is not None and out_dtype != out_dtype_for(op, x_dtype):
+        od = _DT[out_dtype]
+    return _lib.make_options(out_dtype=od, precision=_PREC[precision],
+                             carry=_CARRY[carry], config=int(config),
+                             max_ctas=int(max_ctas))
+
+
+def _check_input(x):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("x must be a CUDA tensor")
+    if x.dtype not in _DT:
+        raise TypeError(f"unsupported dtype {x.dtype}")
+    if x.dim() != 1 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous 1-D tensor")
+
+
+def scan(x, op="add", inclusive=True, out=None, *, precision=None,
+         carry=None, config=0, max_ctas=0, out_dtype=None, stream=None):
+    """Inclusive or exclusive scan of a 1-D CUDA tensor (one kernel launch)."""
+    _check_input(x)
+    odt = out_dtype_for(op, x.dtype, out_dtype)
+    if out is None:
+        out = torch.empty(x.shape[0], dtype=odt, device=x.device)
+    elif out.dtype != odt or out.shape != x.shape or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype, shape or layout")
+    opts = _options(op, x.dtype, out_dtype, precision, carry, config, max_ctas)
+    st = _lib.lscan_scan(_OPS[op], _DT[x.dtype], int(bool(inclusive)),
+                         x.data_ptr(), out.data_ptr(), x.shape[0], opts,
+                         _stream_ptr(stream))
+    _lib.check(st, "lscan_scan")
+    return out
+
+
+def inclusive(x, op="add", out=None, **kw):
+    return scan(x, op, True, out, **kw)
+
+
+def exclusive(x, op="add", out=None, **kw):
+    return scan(x, op, False, out, **kw)
+
+
+def batched(x, offsets, op="add", inclusive=True, out=None, *, n_total=None,
+            precision=None, carry=None, config=0, max_ctas=0, out_dtype=None,
+            stream=None):
+    """Scan every segment [offsets[s], offsets[s+1]) of x independently."""
+    _check_input(x)
+    if offsets.dtype != torch.int64 or not offsets.is_cuda:
+        raise TypeError("offsets must be an int64 CUDA tensor")
+    n_total = x.shape[0] if n_total is None else int(n_total)
+    odt = out_dtype_for(op, x.dtype, out_dtype)
+    if out is None:
+        out = torch.empty(x.shape[0], dtype=odt, device=x.device)
+    opts = _options(op, x.dtype, out_dtype, precision, carry, config, max_ctas)
+    st = _lib.lscan_batched(_OPS[op], _DT[x.dtype], int(bool(inclusive)),
+                            x.data_ptr(), out.data_ptr(), offsets.data_ptr(),
+                            offsets.shape[0] - 1, n_total, opts,
+                            _stream_ptr(stream))
+    _lib.check(st, "lscan_batched")
+    return out
+
+
+def stream_status(stream=None):
+    """Synchronise the stream and raise if the device latched an error."""
+    _lib.check(_lib.lscan_stream_status(_stream_ptr(stream)),
+               "lscan_stream_status")
+
+
+class Graph:
+    """A scan captured into a CUDA graph once and replayed (one kernel)."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep  # tensors the graph's baked pointers refer to
+
+    @classmethod
+    def scan(cls, x, out, op="add", inclusive=True, **kw):
+        import ctypes
+        _check_input(x)
+        opts = _options(op, x.dtype, kw.get("out_dtype"), kw.get("precision"),
+                        kw.get("carry"), kw.get("config", 0),
+                        kw.get("max_ctas", 0))
+        h = ctypes.c_void_p()
+        st = _lib.load().lscan_graph_create_scan(
+            _OPS[op], _DT[x.dtype], int(bool(inclusive)), x.data_ptr(),
+            out.data_ptr(), x.shape[0], ctypes.byref(opts), ctypes.byref(h))
+        _lib.check(st, "lscan_graph_create_scan")
+        return cls(h, (x, out))
+
+    @classmethod
+    def batched(cls, x, offsets, out, op="add", inclusive=True, **kw):
+        import ctypes
+        _check_input(x)
+        opts = _options(op, x.dtype, kw.get("out_dtype"), kw.get("precision"),
+                        kw.get("carry"), kw.get("config", 0),
+                        kw.get("max_ctas", 0))
+        h = ctypes.c_void_p()
+        st = _lib.load().lscan_graph_create_batched(
+            _OPS[op], _DT[x.dtype], int(bool(inclusive)), x.data_ptr(),
+            out.data_ptr(), offsets.data_ptr(), offsets.shape[0] - 1,
+            x.shape[0], ctypes.byref(opts), ctypes.byref(h))
+        _lib.check(st, "lscan_graph_create_batched")
+        return cls(h, (x, offsets, out))
+
+    def launch(self, stream=None):
+        _lib.check(_lib.load().lscan_graph_launch(self._h, _stream_ptr(stream)),
+                   "lscan_graph_launch")
+
+    def status(self):
+        _lib.check(_lib.load().lscan_graph_status(self._h), "lscan_graph_status")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.load().lscan_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,186 @@
+"""ctypes binding of liblscan.so (argument marshalling only).
+
+Every function of include/lscan.h is exposed under the same name.  The library
+is built in-tree by ``paper_1604_04815_gb300.build``; if it is missing this
+module raises -- there is no CPU or eager fallback.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblscan.so")
+
+LSCAN_ADD, LSCAN_MAX = 0, 1
+LSCAN_I32, LSCAN_F32, LSCAN_BF16 = 0, 1, 2
+LSCAN_OK = 0
+LSCAN_ERR_INVALID = 1
+LSCAN_ERR_UNSUPPORTED = 2
+LSCAN_ERR_CUDA = 3
+LSCAN_ERR_TIMEOUT = 4
+LSCAN_ERR_NOMEM = 5
+LSCAN_ERR_BUSY = 6
+LSCAN_ERR_DEVICE = 7
+LSCAN_PREC_DEFAULT, LSCAN_PREC_F32_CARRY, LSCAN_PREC_F64_CARRY, \
+    LSCAN_PREC_COMPENSATED = 0, 1, 2, 3
+LSCAN_CARRY_AUTO, LSCAN_CARRY_LOOKBACK, LSCAN_CARRY_CHAINED = 0, 1, 2
+
+# every symbol include/lscan.h declares (checked by the ABI test)
+EXPORTED = [
+    "lscan_inclusive", "lscan_exclusive", "lscan_scan", "lscan_batched",
+    "lscan_graph_create_scan", "lscan_graph_create_batched",
+    "lscan_graph_launch", "lscan_graph_status", "lscan_graph_destroy",
+    "lscan_stream_status", "lscan_reserve", "lscan_shutdown",
+    "lscan_strerror", "lscan_version", "lscan_launch_count",
+    "lscan_set_wait_limit_ns", "lscan_debug_skip_publish",
+    "lscan_config_info", "lscan_num_configs",
+]
+
+
+class lscan_options(ctypes.Structure):
+    _fields_ = [("out_dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("carry", ctypes.c_int32), ("config", ctypes.c_int32),
+                ("max_ctas", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class LscanError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+_lib = None
+
+
+def load():
+    """Load liblscan.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"liblscan.so not found at {LIB_PATH}; build it with "
+            "`python -m paper_1604_04815_gb300.build` (needs nvcc); "
+            "there is no fallback path")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    optp = ctypes.POINTER(lscan_options)
+    sig = {
+        "lscan_inclusive": [i32, i32, vp, vp, i64, vp],
+        "lscan_exclusive": [i32, i32, vp, vp, i64, vp],
+        "lscan_scan": [i32, i32, i32, vp, vp, i64, optp, vp],
+        "lscan_batched": [i32, i32, i32, vp, vp, vp, i64, i64, optp, vp],
+        "lscan_graph_create_scan": [i32, i32, i32, vp, vp, i64, optp,
+                                    ctypes.POINTER(vp)],
+        "lscan_graph_create_batched": [i32, i32, i32, vp, vp, vp, i64, i64,
+                                       optp, ctypes.POINTER(vp)],
+        "lscan_graph_launch": [vp, vp],
+        "lscan_graph_status": [vp],
+        "lscan_stream_status": [vp],
+        "lscan_reserve": [vp, i64],
+        "lscan_set_wait_limit_ns": [ctypes.c_uint64],
+        "lscan_debug_skip_publish": [i64],
+        "lscan_config_info": [ctypes.c_int32, i32] +
+                             [ctypes.POINTER(ctypes.c_int32)] * 4,
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.lscan_graph_destroy.argtypes = [vp]
+    lib.lscan_graph_destroy.restype = None
+    lib.lscan_shutdown.argtypes = []
+    lib.lscan_shutdown.restype = None
+    lib.lscan_strerror.argtypes = [ctypes.c_int]
+    lib.lscan_strerror.restype = ctypes.c_char_p
+    lib.lscan_version.argtypes = []
+    lib.lscan_version.restype = ctypes.c_char_p
+    lib.lscan_launch_count.argtypes = []
+    lib.lscan_launch_count.restype = ctypes.c_uint64
+    lib.lscan_num_configs.argtypes = []
+    lib.lscan_num_configs.restype = ctypes.c_int32
+    _lib = lib
+    return lib
+
+
+def strerror(status):
+    return load().lscan_strerror(int(status)).decode()
+
+
+def check(status, where):
+    if status != LSCAN_OK:
+        raise LscanError(status, where)
+
+
+def make_options(out_dtype=0, precision=0, carry=0, config=0, max_ctas=0):
+    o = lscan_options()
+    o.out_dtype = out_dtype
+    o.precision = precision
+    o.carry = carry
+    o.config = config
+    o.max_ctas = max_ctas
+    return o
+
+
+# Thin same-name wrappers: plain integers/pointers in, status out.
+def lscan_inclusive(op, dtype, x, y, n, stream=None):
+    return load().lscan_inclusive(op, dtype, x, y, n, stream)
+
+
+def lscan_exclusive(op, dtype, x, y, n, stream=None):
+    return load().lscan_exclusive(op, dtype, x, y, n, stream)
+
+
+def lscan_scan(op, dtype, inclusive, x, y, n, opts=None, stream=None):
+    return load().lscan_scan(op, dtype, inclusive, x, y, n,
+                             ctypes.byref(opts) if opts is not None else None,
+                             stream)
+
+
+def lscan_batched(op, dtype, inclusive, x, y, d_offsets, n_seg, n_total,
+                  opts=None, stream=None):
+    return load().lscan_batched(op, dtype, inclusive, x, y, d_offsets, n_seg,
+                                n_total,
+                                ctypes.byref(opts) if opts is not None
+                                else None, stream)
+
+
+def lscan_stream_status(stream=None):
+    return load().lscan_stream_status(stream)
+
+
+def lscan_reserve(stream, max_elems):
+    return load().lscan_reserve(stream, max_elems)
+
+
+def lscan_launch_count():
+    return int(load().lscan_launch_count())
+
+
+def lscan_set_wait_limit_ns(ns):
+    return load().lscan_set_wait_limit_ns(ns)
+
+
+def lscan_debug_skip_publish(tile):
+    return load().lscan_debug_skip_publish(tile)
+
+
+def lscan_shutdown():
+    load().lscan_shutdown()
+
+
+def lscan_config_info(config, dtype):
+    vals = [ctypes.c_int32() for _ in range(4)]
+    st = load().lscan_config_info(config, dtype, *[ctypes.byref(v)
+                                                   for v in vals])
+    check(st, "lscan_config_info")
+    return dict(items=vals[0].value, threads=vals[1].value,
+                stages=vals[2].value, tile=vals[3].value)
+
+
+def lscan_num_configs():
+    return int(load().lscan_num_configs())
+
+
+def lscan_version():
+    return load().lscan_version().decode()

@@ -1,0 +1,59 @@
+// kernel_inst.cuh -- explicit instantiation of the scan kernel for one kind.
+#pragma once
+#include "kernel_table.h"
+#include "scan_kernel.cuh"
+
+namespace lscan {
+
+// Tile configurations by input element size.  Variant 0 (G) loads straight
+// from global memory; C1..C3 stream 8, 16 and 32 KiB input tiles through the
+// bulk-copy ring.
+template <int ISZ>
+struct Cfgs;
+template <>
+struct Cfgs<4> {
+    using G = TileCfg<8, 8, 4>;
+    using C1 = TileCfg<8, 8, 4>;
+    using C2 = TileCfg<16, 8, 4>;
+    using C3 = TileCfg<16, 16, 3>;
+};
+template <>
+struct Cfgs<2> {
+    using G = TileCfg<16, 8, 4>;
+    using C1 = TileCfg<16, 8, 4>;
+    using C2 = TileCfg<32, 8, 4>;
+    using C3 = TileCfg<32, 16, 2>;
+};
+
+template <class K, class Cfg, int MODE, bool TMA>
+void fill_entry(int kind, int variant) {
+    using L = Layout<K, Cfg, MODE, TMA>;
+    KernelEntry &e = g_kernels[kind][MODE][variant];
+    e.fn = reinterpret_cast<const void *>(&lscan_kernel<K, Cfg, MODE, TMA>);
+    e.threads = Cfg::THREADS;
+    e.smem = L::bytes;
+    e.tile = Cfg::TILE;
+    e.items = Cfg::ITEMS;
+    e.cwarps = Cfg::CWARPS;
+    e.stages = Cfg::STAGES;
+    e.car_words = int(sizeof(typename K::Car) / 4);
+    e.in_size = int(sizeof(typename K::In));
+    e.out_size = int(sizeof(typename K::Out));
+}
+
+template <class K, int MODE>
+void fill_mode(int kind) {
+    using C = Cfgs<int(sizeof(typename K::In))>;
+    fill_entry<K, typename C::G, MODE, false>(kind, 0);
+    fill_entry<K, typename C::C1, MODE, true>(kind, 1);
+    fill_entry<K, typename C::C2, MODE, true>(kind, 2);
+    fill_entry<K, typename C::C3, MODE, true>(kind, 3);
+}
+
+template <class K>
+void fill_kind(int kind) {
+    fill_mode<K, MODE_SINGLE>(kind);
+    fill_mode<K, MODE_SEGMENTED>(kind);
+}
+
+}  // namespace lscan

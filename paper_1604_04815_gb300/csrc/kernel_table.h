@@ -1,0 +1,33 @@
+// kernel_table.h -- registry of compiled scan kernels (host side).
+#pragma once
+#include <cstdint>
+
+#include "scan_common.h"
+
+namespace lscan {
+
+// Variant 0 is the plain-load path for pointers that are not 16-byte
+// aligned; variants 1..kNumTmaCfg are bulk-copy (TMA) tile configurations.
+constexpr int kNumTmaCfg = 3;
+constexpr int kNumVariants = 1 + kNumTmaCfg;
+constexpr int kNumKinds = 13;
+
+struct KernelEntry {
+    const void *fn = nullptr;
+    int threads = 0;   // CTA size (consumer warps + 1 producer warp)
+    int smem = 0;      // dynamic shared memory bytes
+    int tile = 0;      // elements per tile
+    int items = 0;     // elements per consumer thread
+    int cwarps = 0;    // consumer warps
+    int stages = 0;    // tile-ring depth
+    int car_words = 0; // 64-bit status words per tile
+    int in_size = 0;
+    int out_size = 0;
+};
+
+// [kind][mode][variant]
+extern KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
+
+void register_all_kernels();
+
+}  // namespace lscan

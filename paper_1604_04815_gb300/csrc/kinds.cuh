@@ -1,0 +1,254 @@
+// kinds.cuh -- operator / element-type traits of the scan kernels.
+//
+// A "kind" fixes: storage types In/Out, the in-tile accumulation type Acc,
+// the inter-tile carry type Car (what the status words carry), and CarA, the
+// form in which a tile applies its carry to its elements.  The operator is
+// always combined as op(earlier, later), so the code never relies on
+// commutativity even though add and max are commutative (Section 1 only asks
+// for associativity).
+//
+//   int32 add  : wrapping uint32 arithmetic (two's complement mod 2^32)
+//   int32 max  : signed compare, identity INT32_MIN
+//   fp32/bf16 max : b > a ? b : a  (a tie keeps the earlier element's bits),
+//                identity -inf; bf16 widened exactly to fp32 and narrowed
+//                back exactly
+//   fp32/bf16 add, three precision paths for the carry chain:
+//     Plain : fp32 in tile, fp32 carry
+//     F64   : fp32 in tile, FP64 carry; the carry is split once per tile into
+//             an fp32 (hi, lo) pair and applied with fp32 two-sum arithmetic,
+//             so no per-element FP64 work is done
+//     Comp  : fp32 (hi, lo) pairs in tile (compensated two-sum arithmetic),
+//             FP64 carry, result rounded to fp32 once at the end
+//
+// Two-sum (Knuth, TAOCP vol. 2, 4.2.2) and fast-two-sum (Dekker 1971) are
+// written with __fadd_rn / __fsub_rn so the compiler cannot contract or
+// reassociate them.
+#pragma once
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+namespace lscan {
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ float bf16_bits_to_f32(uint16_t b) {
+    return __uint_as_float(static_cast<uint32_t>(b) << 16);
+}
+// exact when f came from a bf16 (low 16 bits zero)
+__device__ __forceinline__ uint16_t f32_to_bf16_bits_exact(float f) {
+    return static_cast<uint16_t>(__float_as_uint(f) >> 16);
+}
+__device__ __forceinline__ uint16_t f32_to_bf16_bits_rn(float f) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// s + e == a + b exactly (Knuth two-sum)
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+// requires |a| >= |b| or a == 0 (Dekker fast-two-sum)
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return make_float2(s, e);
+}
+// double-float addition (hi, lo) + (hi, lo); absolute error O(u^2 (|a|+|b|))
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    float2 s = two_sum(a.x, b.x);
+    float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
+    return fast_two_sum(s.x, e);
+}
+// FP64 value -> fp32 (hi, lo) with hi + lo == d to ~2^-48 |d|
+__device__ __forceinline__ float2 split_f64(double d) {
+    float h = __double2float_rn(d);
+    float l = __double2float_rn(__dsub_rn(d, static_cast<double>(h)));
+    return make_float2(h, l);
+}
+
+template <class T>
+__device__ __forceinline__ T max_keep_left(T a, T b) {
+    return (b > a) ? b : a;
+}
+
+// ----------------------------------------------------------------- kinds
+struct KI32Add {
+    using In = int32_t;
+    using Out = int32_t;
+    using Acc = uint32_t;
+    using Car = uint32_t;
+    using CarA = uint32_t;
+    __device__ static Acc ident() { return 0u; }
+    __device__ static Acc load(In v) { return static_cast<uint32_t>(v); }
+    __device__ static Acc op(Acc a, Acc b) { return a + b; }
+    __device__ static Car cident() { return 0u; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return a + b; }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return c + tb; }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) {
+        return static_cast<int32_t>(b + v);
+    }
+};
+
+struct KI32Max {
+    using In = int32_t;
+    using Out = int32_t;
+    using Acc = int32_t;
+    using Car = int32_t;
+    using CarA = int32_t;
+    __device__ static Acc ident() { return INT32_MIN; }
+    __device__ static Acc load(In v) { return v; }
+    __device__ static Acc op(Acc a, Acc b) { return max_keep_left(a, b); }
+    __device__ static Car cident() { return INT32_MIN; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return max_keep_left(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) { return max_keep_left(b, v); }
+};
+
+template <class InT>
+struct FloatIn;
+template <>
+struct FloatIn<float> {
+    __device__ static float load(float v) { return v; }
+};
+template <>
+struct FloatIn<uint16_t> {
+    __device__ static float load(uint16_t v) { return bf16_bits_to_f32(v); }
+};
+
+template <class OutT>
+struct FloatOut;
+template <>
+struct FloatOut<float> {
+    __device__ static float cvt(float v) { return v; }
+    __device__ static float cvt_exact(float v) { return v; }
+};
+template <>
+struct FloatOut<uint16_t> {
+    __device__ static uint16_t cvt(float v) { return f32_to_bf16_bits_rn(v); }
+    __device__ static uint16_t cvt_exact(float v) {
+        return f32_to_bf16_bits_exact(v);
+    }
+};
+
+// fp32 / bf16 max (InT = float or uint16_t bf16 bits; Out = In)
+template <class InT>
+struct KFMax {
+    using In = InT;
+    using Out = InT;
+    using Acc = float;
+    using Car = float;
+    using CarA = float;
+    __device__ static Acc ident() { return __uint_as_float(0xff800000u); }
+    __device__ static Acc load(In v) { return FloatIn<InT>::load(v); }
+    __device__ static Acc op(Acc a, Acc b) { return max_keep_left(a, b); }
+    __device__ static Car cident() { return __uint_as_float(0xff800000u); }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return max_keep_left(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) {
+        return FloatOut<InT>::cvt_exact(max_keep_left(b, v));
+    }
+};
+
+// float add, plain fp32 carry
+template <class InT, class OutT>
+struct KFAddPlain {
+    using In = InT;
+    using Out = OutT;
+    using Acc = float;
+    using Car = float;
+    using CarA = float;
+    __device__ static Acc ident() { return 0.0f; }
+    __device__ static Acc load(In v) { return FloatIn<InT>::load(v); }
+    __device__ static Acc op(Acc a, Acc b) { return __fadd_rn(a, b); }
+    __device__ static Car cident() { return 0.0f; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return __fadd_rn(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return __fadd_rn(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) {
+        return FloatOut<OutT>::cvt(__fadd_rn(b, v));
+    }
+};
+
+// float add, fp32 in tile, FP64 carry applied as an fp32 (hi, lo) pair
+template <class InT, class OutT>
+struct KFAddF64 {
+    using In = InT;
+    using Out = OutT;
+    using Acc = float;
+    using Car = double;
+    using CarA = float2;
+    __device__ static Acc ident() { return 0.0f; }
+    __device__ static Acc load(In v) { return FloatIn<InT>::load(v); }
+    __device__ static Acc op(Acc a, Acc b) { return __fadd_rn(a, b); }
+    __device__ static Car cident() { return 0.0; }
+    __device__ static Car to_car(Acc a) { return static_cast<double>(a); }
+    __device__ static Car cop(Car a, Car b) { return __dadd_rn(a, b); }
+    __device__ static CarA to_apply(Car c) { return split_f64(c); }
+    __device__ static CarA base(CarA c, Acc tb) {
+        float2 s = two_sum(c.x, tb);
+        return make_float2(s.x, __fadd_rn(s.y, c.y));
+    }
+    __device__ static CarA base_local(Acc tb) { return make_float2(tb, 0.0f); }
+    __device__ static Out fin(CarA b, Acc v) {
+        return FloatOut<OutT>::cvt(__fadd_rn(b.x, __fadd_rn(v, b.y)));
+    }
+};
+
+// float add, compensated (hi, lo) in tile, FP64 carry
+template <class InT, class OutT>
+struct KFAddComp {
+    using In = InT;
+    using Out = OutT;
+    using Acc = float2;
+    using Car = double;
+    using CarA = float2;
+    __device__ static Acc ident() { return make_float2(0.0f, 0.0f); }
+    __device__ static Acc load(In v) {
+        return make_float2(FloatIn<InT>::load(v), 0.0f);
+    }
+    __device__ static Acc op(Acc a, Acc b) { return df_add(a, b); }
+    __device__ static Car cident() { return 0.0; }
+    __device__ static Car to_car(Acc a) {
+        return __dadd_rn(static_cast<double>(a.x), static_cast<double>(a.y));
+    }
+    __device__ static Car cop(Car a, Car b) { return __dadd_rn(a, b); }
+    __device__ static CarA to_apply(Car c) { return split_f64(c); }
+    __device__ static CarA base(CarA c, Acc tb) { return df_add(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) {
+        return FloatOut<OutT>::cvt(df_add(b, v).x);
+    }
+};
+
+// ------------------------------------------------- kind ids (host + device)
+enum KindId : int {
+    KIND_I32_ADD = 0,
+    KIND_I32_MAX,
+    KIND_F32_MAX,
+    KIND_BF16_MAX,
+    KIND_F32_ADD_PLAIN,
+    KIND_F32_ADD_F64,
+    KIND_F32_ADD_COMP,
+    KIND_BF16_ADD_PLAIN_F32,
+    KIND_BF16_ADD_F64_F32,
+    KIND_BF16_ADD_COMP_F32,
+    KIND_BF16_ADD_PLAIN_BF16,
+    KIND_BF16_ADD_F64_BF16,
+    KIND_BF16_ADD_COMP_BF16,
+    KIND_COUNT
+};
+
+}  // namespace lscan

@@ -1,0 +1,458 @@
+// lscan_api.cu -- the C ABI of liblscan.so: argument checks, kernel choice,
+// per-stream scratch, launch, device error read-back.
+//
+// One scan is one kernel launch (LightScan Section 5.1: "only one kernel
+// launch is needed").  The scratch a launch needs -- a status word per tile,
+// the tile ticket, the epoch that tags status words, the error word -- lives
+// in device memory owned by this library, one set per (device, stream), and
+// is re-armed by the kernel itself (the last CTA resets the ticket and bumps
+// the epoch), so no memset runs between launches and graph replays work.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "../../include/lscan.h"
+#include "kernel_table.h"
+#include "kinds.cuh"
+#include "lscan_internal.h"
+
+namespace lscan {
+
+KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
+
+void register_i32_add();
+void register_i32_max();
+void register_f32_max();
+void register_bf16_max();
+void register_f32_add_plain();
+void register_f32_add_f64();
+void register_f32_add_comp();
+void register_bf16_add_plain_f32();
+void register_bf16_add_f64_f32();
+void register_bf16_add_comp_f32();
+void register_bf16_add_plain_bf16();
+void register_bf16_add_f64_bf16();
+void register_bf16_add_comp_bf16();
+
+void register_all_kernels() {
+    register_i32_add();
+    register_i32_max();
+    register_f32_max();
+    register_bf16_max();
+    register_f32_add_plain();
+    register_f32_add_f64();
+    register_f32_add_comp();
+    register_bf16_add_plain_f32();
+    register_bf16_add_f64_f32();
+    register_bf16_add_comp_f32();
+    register_bf16_add_plain_bf16();
+    register_bf16_add_f64_bf16();
+    register_bf16_add_comp_bf16();
+}
+
+namespace {
+
+std::mutex g_mu;
+std::once_flag g_reg_once;
+std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_wait_limit_ns{1000000000ull};
+std::atomic<int64_t> g_skip_tile{-1};
+
+struct Scratch {
+    int device = -1;
+    uint32_t *ctl = nullptr;     // CTL_WORDS
+    uint64_t *status = nullptr;  // status_words
+    size_t status_words = 0;
+    uint64_t launches = 0;       // launches since the last full reset
+};
+
+std::map<std::pair<int, void *>, Scratch *> g_scratch;
+
+struct FnState {
+    bool attr_set = false;
+    int blocks_per_sm = 0;
+};
+std::map<std::pair<int, const void *>, FnState> g_fn_state;
+std::map<int, int> g_sm_count;
+
+constexpr uint64_t kEpochPeriod = (1ull << 30) - 1;
+
+}  // namespace
+
+int sm_count(int dev) {
+    auto it = g_sm_count.find(dev);
+    if (it != g_sm_count.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        n = 1;
+    g_sm_count[dev] = n;
+    return n;
+}
+
+// Kind id for (op, dtype, out dtype, precision); -1 if not built.
+int select_kind(int op, int dtype, int out_dtype, int precision) {
+    if (op == LSCAN_MAX) {
+        if (out_dtype != dtype) return -1;
+        if (dtype == LSCAN_I32) return KIND_I32_MAX;
+        if (dtype == LSCAN_F32) return KIND_F32_MAX;
+        if (dtype == LSCAN_BF16) return KIND_BF16_MAX;
+        return -1;
+    }
+    if (op != LSCAN_ADD) return -1;
+    if (dtype == LSCAN_I32) return out_dtype == LSCAN_I32 ? KIND_I32_ADD : -1;
+    int prec = precision == LSCAN_PREC_DEFAULT ? LSCAN_PREC_F64_CARRY : precision;
+    if (prec < LSCAN_PREC_F32_CARRY || prec > LSCAN_PREC_COMPENSATED) return -1;
+    const int pi = prec - LSCAN_PREC_F32_CARRY;  // 0 plain, 1 f64, 2 comp
+    if (dtype == LSCAN_F32) {
+        if (out_dtype != LSCAN_F32) return -1;
+        return KIND_F32_ADD_PLAIN + pi;
+    }
+    if (dtype == LSCAN_BF16) {
+        if (out_dtype == LSCAN_F32) return KIND_BF16_ADD_PLAIN_F32 + pi;
+        if (out_dtype == LSCAN_BF16) return KIND_BF16_ADD_PLAIN_BF16 + pi;
+    }
+    return -1;
+}
+
+int dtype_size(int dt) {
+    if (dt == LSCAN_I32 || dt == LSCAN_F32) return 4;
+    if (dt == LSCAN_BF16) return 2;
+    return 0;
+}
+
+// Occupancy-derived persistent grid size for a kernel on device dev.
+static lscan_status kernel_prepare(int dev, const KernelEntry &e, int *blocks_per_sm) {
+    FnState &st = g_fn_state[{dev, e.fn}];
+    if (!st.attr_set) {
+        if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 e.smem) != cudaSuccess)
+            return LSCAN_ERR_CUDA;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, e.fn, e.threads,
+                                                          e.smem) != cudaSuccess)
+            return LSCAN_ERR_CUDA;
+        st.blocks_per_sm = nb > 0 ? nb : 1;
+        st.attr_set = true;
+    }
+    *blocks_per_sm = st.blocks_per_sm;
+    return LSCAN_OK;
+}
+
+static bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Scratch for (current device, stream), with room for `words` status words.
+static lscan_status get_scratch(void *stream, size_t words, Scratch **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    Scratch *&sc = g_scratch[{dev, stream}];
+    if (sc == nullptr) {
+        if (stream_capturing(cs)) return LSCAN_ERR_BUSY;
+        sc = new Scratch();
+        sc->device = dev;
+        if (cudaMalloc(&sc->ctl, CTL_WORDS * sizeof(uint32_t)) != cudaSuccess) {
+            delete sc;
+            sc = nullptr;
+            return LSCAN_ERR_NOMEM;
+        }
+        if (cudaMemsetAsync(sc->ctl, 0, CTL_WORDS * sizeof(uint32_t), cs) != cudaSuccess)
+            return LSCAN_ERR_CUDA;
+    }
+    if (sc->status_words < words) {
+        if (stream_capturing(cs)) return LSCAN_ERR_BUSY;
+        size_t want = sc->status_words ? sc->status_words : 4096;
+        while (want < words) want *= 2;
+        if (sc->status) {
+            // earlier launches on this stream may still read the old array
+            if (cudaStreamSynchronize(cs) != cudaSuccess) return LSCAN_ERR_CUDA;
+            cudaFree(sc->status);
+            sc->status = nullptr;
+            sc->status_words = 0;
+        }
+        if (cudaMalloc(&sc->status, want * sizeof(uint64_t)) != cudaSuccess)
+            return LSCAN_ERR_NOMEM;
+        if (cudaMemsetAsync(sc->status, 0, want * sizeof(uint64_t), cs) != cudaSuccess)
+            return LSCAN_ERR_CUDA;
+        sc->status_words = want;
+    }
+    *out = sc;
+    return LSCAN_OK;
+}
+
+// Every 2^30 - 1 launches the epoch field of the tags would wrap; clear the
+// status array and control block then, so an old tag can never match.
+static lscan_status epoch_maintenance(Scratch *sc, cudaStream_t cs) {
+    if (++sc->launches < kEpochPeriod) return LSCAN_OK;
+    if (stream_capturing(cs)) return LSCAN_OK;  // retried on the next launch
+    if (cudaMemsetAsync(sc->status, 0, sc->status_words * sizeof(uint64_t), cs) !=
+            cudaSuccess ||
+        cudaMemsetAsync(sc->ctl, 0, CTL_WORDS * sizeof(uint32_t), cs) != cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    sc->launches = 0;
+    return LSCAN_OK;
+}
+
+static bool ranges_partially_overlap(const void *x, size_t xb, const void *y, size_t yb) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(x), a1 = a0 + xb;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(y), b1 = b0 + yb;
+    if (a1 <= b0 || b1 <= a0) return false;  // disjoint
+    return !(a0 == b0 && xb == yb);          // identical = in place
+}
+
+lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
+                         cudaStream_t cs) {
+    const KernelEntry &e = g_kernels[ls.kind][ls.mode][ls.variant];
+    if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
+    int bps = 1;
+    lscan_status st = kernel_prepare(dev, e, &bps);
+    if (st != LSCAN_OK) return st;
+    const int64_t n_tiles = (ls.n + e.tile - 1) / e.tile;
+    int64_t grid = static_cast<int64_t>(bps) * sm_count(dev);
+    if (ls.max_ctas > 0 && grid > ls.max_ctas) grid = ls.max_ctas;
+    if (grid > n_tiles) grid = n_tiles;
+    if (grid < 1) grid = 1;
+
+    ScanParams p;
+    p.x = ls.x;
+    p.y = ls.y;
+    p.n = ls.n;
+    p.n_tiles = n_tiles;
+    p.offsets = ls.offsets;
+    p.n_seg = ls.n_seg;
+    p.ctl = buf.ctl;
+    p.status = buf.status;
+    p.wait_limit_ns = g_wait_limit_ns.load();
+    p.skip_tile = g_skip_tile.exchange(-1);
+    p.inclusive = ls.inclusive ? 1 : 0;
+    p.chained = ls.chained ? 1 : 0;
+    void *args[] = {&p};
+    cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
+                                      dim3(e.threads), args, e.smem, cs);
+    if (ce != cudaSuccess) return LSCAN_ERR_CUDA;
+    g_launches.fetch_add(1);
+    return LSCAN_OK;
+}
+
+lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
+                       int64_t n, const lscan_options *opts, int mode,
+                       const int64_t *offsets, int64_t n_seg, LaunchSpec *ls) {
+    std::call_once(g_reg_once, register_all_kernels);
+    if (n < 0) return LSCAN_ERR_INVALID;
+    const int isz = dtype_size(dtype);
+    if (isz == 0 || (op != LSCAN_ADD && op != LSCAN_MAX)) return LSCAN_ERR_INVALID;
+    int out_dtype = dtype;
+    if (op == LSCAN_ADD && dtype == LSCAN_BF16) out_dtype = LSCAN_F32;
+    if (opts && opts->out_dtype > 0 && opts->out_dtype <= LSCAN_BF16)
+        out_dtype = opts->out_dtype;
+    const int prec = opts ? opts->precision : LSCAN_PREC_DEFAULT;
+    const int kind = select_kind(op, dtype, out_dtype, prec);
+    if (kind < 0) return LSCAN_ERR_UNSUPPORTED;
+    const int osz = dtype_size(out_dtype);
+    if (n > 0) {
+        if (x == nullptr || y == nullptr) return LSCAN_ERR_INVALID;
+        if ((reinterpret_cast<uintptr_t>(x) % isz) != 0 ||
+            (reinterpret_cast<uintptr_t>(y) % osz) != 0)
+            return LSCAN_ERR_INVALID;
+        if (ranges_partially_overlap(x, static_cast<size_t>(n) * isz, y,
+                                     static_cast<size_t>(n) * osz))
+            return LSCAN_ERR_INVALID;
+    }
+    int cfg = opts ? opts->config : 0;
+    if (cfg < 0 || cfg > kNumTmaCfg) return LSCAN_ERR_INVALID;
+    int variant = cfg > 0 ? cfg : tuned_variant(kind, mode, n);
+    const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(y) % 16 == 0);
+    if (!aligned) variant = 0;
+    const KernelEntry &e = g_kernels[kind][mode][variant];
+    if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
+    const int64_t n_tiles = (n + e.tile - 1) / e.tile;
+    if (n_tiles > (int64_t{1} << 31) - 1) return LSCAN_ERR_INVALID;
+    const int carry = opts ? opts->carry : LSCAN_CARRY_AUTO;
+    if (carry < LSCAN_CARRY_AUTO || carry > LSCAN_CARRY_CHAINED) return LSCAN_ERR_INVALID;
+
+    ls->kind = kind;
+    ls->mode = mode;
+    ls->variant = variant;
+    ls->x = x;
+    ls->y = y;
+    ls->n = n;
+    ls->offsets = offsets;
+    ls->n_seg = n_seg;
+    ls->inclusive = inclusive != 0;
+    ls->chained = carry == LSCAN_CARRY_CHAINED;
+    ls->max_ctas = opts ? opts->max_ctas : 0;
+    ls->status_words = static_cast<size_t>(n_tiles) * e.car_words;
+    return LSCAN_OK;
+}
+
+lscan_status run_planned(const LaunchSpec &ls, void *stream) {
+    if (ls.n == 0) return LSCAN_OK;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_mu);
+    Scratch *sc = nullptr;
+    lscan_status st = get_scratch(stream, ls.status_words, &sc);
+    if (st != LSCAN_OK) return st;
+    st = epoch_maintenance(sc, cs);
+    if (st != LSCAN_OK) return st;
+    DevBuffers b{sc->ctl, sc->status};
+    return launch_scan(ls, b, cs);
+}
+
+std::mutex &api_mutex() { return g_mu; }
+
+void note_launch() { g_launches.fetch_add(1); }
+
+}  // namespace lscan
+
+using namespace lscan;
+
+extern "C" {
+
+lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive, const void *x,
+                        void *y, int64_t n, const lscan_options *opts, void *stream) {
+    LaunchSpec ls;
+    lscan_status st = plan_scan(op, dtype, inclusive, x, y, n, opts, MODE_SINGLE,
+                                nullptr, 0, &ls);
+    if (st != LSCAN_OK) return st;
+    return run_planned(ls, stream);
+}
+
+lscan_status lscan_inclusive(lscan_op op, lscan_dtype dtype, const void *x, void *y,
+                             int64_t n, void *stream) {
+    return lscan_scan(op, dtype, 1, x, y, n, nullptr, stream);
+}
+
+lscan_status lscan_exclusive(lscan_op op, lscan_dtype dtype, const void *x, void *y,
+                             int64_t n, void *stream) {
+    return lscan_scan(op, dtype, 0, x, y, n, nullptr, stream);
+}
+
+lscan_status lscan_batched(lscan_op op, lscan_dtype dtype, int inclusive, const void *x,
+                           void *y, const int64_t *d_offsets, int64_t n_seg,
+                           int64_t n_total, const lscan_options *opts, void *stream) {
+    if (n_seg < 0 || n_total < 0) return LSCAN_ERR_INVALID;
+    if (n_total > 0 && (d_offsets == nullptr || n_seg == 0)) return LSCAN_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_offsets) % 8 != 0) return LSCAN_ERR_INVALID;
+    LaunchSpec ls;
+    lscan_status st = plan_scan(op, dtype, inclusive, x, y, n_total, opts,
+                                MODE_SEGMENTED, d_offsets, n_seg, &ls);
+    if (st != LSCAN_OK) return st;
+    return run_planned(ls, stream);
+}
+
+lscan_status lscan_stream_status(void *stream) {
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(cs) != cudaSuccess) return LSCAN_ERR_CUDA;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
+    uint32_t *ctl = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_scratch.find({dev, stream});
+        if (it == g_scratch.end()) return LSCAN_OK;
+        ctl = it->second->ctl;
+    }
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, ctl + CTL_ERROR, sizeof(err), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    if (err == 0) return LSCAN_OK;
+    if (cudaMemset(ctl + CTL_ERROR, 0, sizeof(uint32_t)) != cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    if (err & (DEV_ERR_CARRY_WAIT | DEV_ERR_BARRIER_WAIT)) return LSCAN_ERR_TIMEOUT;
+    return LSCAN_ERR_DEVICE;
+}
+
+lscan_status lscan_reserve(void *stream, int64_t max_elems) {
+    if (max_elems < 0) return LSCAN_ERR_INVALID;
+    std::call_once(g_reg_once, register_all_kernels);
+    // smallest tile of any configuration x the widest carry (2 words)
+    int64_t min_tile = INT64_MAX;
+    for (int k = 0; k < kNumKinds; ++k)
+        for (int m = 0; m < MODE_COUNT; ++m)
+            for (int v = 0; v < kNumVariants; ++v)
+                if (g_kernels[k][m][v].fn && g_kernels[k][m][v].tile < min_tile)
+                    min_tile = g_kernels[k][m][v].tile;
+    const size_t words = static_cast<size_t>((max_elems + min_tile - 1) / min_tile) * 2;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Scratch *sc = nullptr;
+    return get_scratch(stream, words > 0 ? words : 1, &sc);
+}
+
+void lscan_shutdown(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_scratch) {
+        Scratch *sc = kv.second;
+        if (!sc) continue;
+        cudaSetDevice(sc->device);
+        cudaDeviceSynchronize();
+        if (sc->status) cudaFree(sc->status);
+        if (sc->ctl) cudaFree(sc->ctl);
+        delete sc;
+    }
+    g_scratch.clear();
+    cudaSetDevice(cur);
+    shutdown_graphs_locked();
+}
+
+const char *lscan_strerror(lscan_status s) {
+    switch (s) {
+        case LSCAN_OK: return "ok";
+        case LSCAN_ERR_INVALID: return "invalid argument";
+        case LSCAN_ERR_UNSUPPORTED: return "unsupported combination";
+        case LSCAN_ERR_CUDA: return "CUDA runtime error";
+        case LSCAN_ERR_TIMEOUT: return "device wait ran out of time";
+        case LSCAN_ERR_NOMEM: return "out of device memory or budget";
+        case LSCAN_ERR_BUSY: return "scratch must grow during stream capture";
+        case LSCAN_ERR_DEVICE: return "device reported malformed input";
+    }
+    return "unknown status";
+}
+
+const char *lscan_version(void) { return "lscan 0.1 (sm_103a)"; }
+
+uint64_t lscan_launch_count(void) { return g_launches.load(); }
+
+lscan_status lscan_set_wait_limit_ns(uint64_t ns) {
+    if (ns == 0) return LSCAN_ERR_INVALID;
+    g_wait_limit_ns.store(ns);
+    return LSCAN_OK;
+}
+
+lscan_status lscan_debug_skip_publish(int64_t tile) {
+    g_skip_tile.store(tile < 0 ? -1 : tile);
+    return LSCAN_OK;
+}
+
+int32_t lscan_num_configs(void) { return kNumTmaCfg; }
+
+lscan_status lscan_config_info(int32_t config, lscan_dtype dtype, int32_t *items,
+                               int32_t *threads, int32_t *stages, int32_t *tile) {
+    std::call_once(g_reg_once, register_all_kernels);
+    if (config < 0 || config > kNumTmaCfg) return LSCAN_ERR_INVALID;
+    int kind = dtype == LSCAN_I32 ? KIND_I32_ADD
+               : dtype == LSCAN_F32 ? KIND_F32_MAX
+               : dtype == LSCAN_BF16 ? KIND_BF16_MAX : -1;
+    if (kind < 0) return LSCAN_ERR_INVALID;
+    const KernelEntry &e = g_kernels[kind][MODE_SINGLE][config];
+    if (items) *items = e.items;
+    if (threads) *threads = e.cwarps * 32;
+    if (stages) *stages = e.stages;
+    if (tile) *tile = e.tile;
+    return LSCAN_OK;
+}
+
+}  // extern "C"

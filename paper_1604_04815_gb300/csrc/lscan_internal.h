@@ -1,0 +1,51 @@
+// lscan_internal.h -- declarations shared by the host-side translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/lscan.h"
+
+namespace lscan {
+
+// A fully checked launch request.
+struct LaunchSpec {
+    int kind = -1;
+    int mode = 0;
+    int variant = 0;
+    const void *x = nullptr;
+    void *y = nullptr;
+    int64_t n = 0;
+    const int64_t *offsets = nullptr;
+    int64_t n_seg = 0;
+    bool inclusive = true;
+    bool chained = false;
+    int max_ctas = 0;
+    size_t status_words = 0;
+};
+
+// Device scratch a launch uses (control block + status words).
+struct DevBuffers {
+    uint32_t *ctl;
+    uint64_t *status;
+};
+
+lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
+                       int64_t n, const lscan_options *opts, int mode,
+                       const int64_t *offsets, int64_t n_seg, LaunchSpec *ls);
+lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
+                         cudaStream_t cs);
+lscan_status run_planned(const LaunchSpec &ls, void *stream);
+
+// tile configuration the tuning table picks for (kind, mode, n); 1..3
+int tuned_variant(int kind, int mode, int64_t n);
+
+std::mutex &api_mutex();
+void shutdown_graphs_locked();
+int dtype_size(int dt);
+void note_launch();  // counts one kernel launch of this library
+void set_tuned_variant(int kind, int mode, int size_cls, int variant);
+
+}  // namespace lscan

@@ -1,0 +1,54 @@
+// scan_common.h -- definitions shared by the kernels and the host library.
+#pragma once
+#include <cstdint>
+
+namespace lscan {
+
+// Control block of one scratch set (device memory, 512 bytes).  Each field
+// sits on its own 128-byte line.  ticket/done/epoch are reset or advanced by
+// the last CTA of every launch, so consecutive launches on a stream (and CUDA
+// graph replays) need no host-side memset.
+enum CtlWord : int {
+    CTL_TICKET = 0,   // next tile to hand out (atomic ticket, Section 4 intro)
+    CTL_DONE = 32,    // CTAs finished in the current launch
+    CTL_EPOCH = 64,   // launch counter that tags status words
+    CTL_ERROR = 96,   // sticky device error bits (read + cleared by the host)
+    CTL_ERR_EPOCH = 100,  // epoch + 1 of the launch that last gave up a wait
+    CTL_WORDS = 128
+};
+
+enum DevError : uint32_t {
+    DEV_ERR_CARRY_WAIT = 1u,    // a predecessor's status never arrived in time
+    DEV_ERR_BARRIER_WAIT = 2u,  // a tile-ring barrier never completed in time
+};
+
+// Status word: (payload32 << 32) | tag32, tag = (epoch mod 2^30) << 2 | state.
+// A payload wider than 32 bits uses several words, each with the full tag.
+enum TileState : uint32_t { ST_INVALID = 0, ST_AGGREGATE = 1, ST_INCLUSIVE = 2 };
+constexpr uint32_t kEpochMask = 0x3fffffffu;
+
+enum ScanMode : int { MODE_SINGLE = 0, MODE_SEGMENTED = 1, MODE_COUNT = 2 };
+
+struct ScanParams {
+    const void *x;
+    void *y;
+    int64_t n;        // elements
+    int64_t n_tiles;  // ceil(n / TILE)
+    const int64_t *offsets;  // MODE_SEGMENTED: n_seg + 1 entries
+    int64_t n_seg;
+    uint32_t *ctl;    // CTL_WORDS uint32
+    uint64_t *status; // n_tiles * carry words
+    uint64_t wait_limit_ns;
+    int64_t skip_tile;  // fault injection: never publish this tile (-1: off)
+    int32_t inclusive;
+    int32_t chained;    // 1: wait for the left neighbour's inclusive only
+};
+
+// Per-launch constants the wait loops need.
+struct WaitCtx {
+    uint32_t *ctl;
+    uint64_t limit_ns;
+    uint32_t epoch;
+};
+
+}  // namespace lscan

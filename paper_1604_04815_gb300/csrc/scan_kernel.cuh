@@ -1,0 +1,727 @@
+// scan_kernel.cuh -- persistent single-pass scan kernel for sm_103a.
+//
+// Structure (LightScan Section 4, re-designed for GB300):
+//  * Work decomposition (Section 4 intro, Algorithm 1).  x is cut into tiles
+//    of L = ITEMS * CTHREADS elements.  A persistent grid of CTAs takes tiles
+//    in ascending order from an atomic ticket (the paper deals them
+//    cyclically to exactly #SM blocks, which deadlocks when not every block
+//    is resident; the ticket keeps the "earlier tiles are owned by running
+//    blocks" property under any residency, e.g. beside concurrent kernels).
+//  * Loads (Section 4.1 step 1, Section 4.5).  One producer warp per CTA
+//    issues cp.async.bulk copies of whole tiles into a STAGES-deep shared
+//    memory ring, up to STAGES-1 tiles ahead, so HBM reads stay in flight
+//    while the consumer warps wait on a carry.  x is read exactly once.
+//  * Intra-warp local scan (Section 4.1, Algorithm 2).  Each thread holds
+//    ITEMS consecutive elements (read from shared memory as 16-byte vectors,
+//    XOR-rotated so that each quarter-warp touches 32 distinct banks), scans
+//    them sequentially (the matrix-scan row of Section 2.3), then the warp
+//    runs the Hillis-Steele shuffle scan of Section 2.1 on the 32 thread
+//    totals (5 rounds of shfl.up).
+//  * Intra-block local scan (Section 4.2, Algorithm 3).  Lane 31 of each warp
+//    writes the warp total to a <=32-entry shared array; every warp scans that
+//    array with shuffles (redundantly, which saves the second barrier of
+//    Algorithm 3) and takes its own offset and the tile aggregate.
+//  * Inter-block communication (Section 4.3, Algorithm 4).  One status word
+//    per tile in L2 carries payload and flag in a single 64-bit relaxed
+//    gpu-scope access (the paper's single-transaction (u, v) pair).  Two
+//    protocols: CHAINED waits for tile t-1's inclusive prefix only
+//    (Algorithm 4); LOOK-BACK publishes the tile aggregate first and lets a
+//    warp combine predecessors' aggregates 32 at a time until it meets an
+//    inclusive prefix.  Every wait is bounded by a %globaltimer limit and
+//    reports DEV_ERR_CARRY_WAIT instead of hanging.
+//  * Intra-block global scan (Section 4.4, Algorithm 5).  Each element gets
+//    carry (+) block offset (+) lane offset (+) own prefix, and y is written
+//    exactly once: staged per warp in shared memory and stored with
+//    cp.async.bulk (full tiles), or with plain stores (ragged last tile and
+//    unaligned pointers).
+//  * Batched mode (MODE_SEGMENTED, not in the paper).  The producer warp
+//    marks segment heads of its tile in a bitmap (warp-parallel lower_bound
+//    on the offsets); the scan operator is lifted to (head flag, value); a
+//    tile that contains a head publishes its inclusive status immediately.
+#pragma once
+#include <cstdint>
+
+#include "kinds.cuh"
+#include "ptx.cuh"
+#include "scan_common.h"
+
+namespace lscan {
+
+template <int ITEMS_, int CWARPS_, int STAGES_>
+struct TileCfg {
+    static constexpr int ITEMS = ITEMS_;
+    static constexpr int CWARPS = CWARPS_;
+    static constexpr int STAGES = STAGES_;
+    static constexpr int CTHREADS = CWARPS * 32;
+    static constexpr int THREADS = CTHREADS + 32;  // + one producer warp
+    static constexpr int TILE = ITEMS * CTHREADS;
+};
+
+constexpr int align_up_c(int v, int a) { return (v + a - 1) / a * a; }
+
+template <class Acc>
+struct alignas(16) WarpTotal {
+    Acc v;
+    uint32_t f;
+};
+
+// Shared-memory layout of one CTA.
+template <class K, class Cfg, int MODE, bool TMA>
+struct Layout {
+    using In = typename K::In;
+    using Out = typename K::Out;
+    static constexpr int kIn = TMA ? Cfg::STAGES * Cfg::TILE * int(sizeof(In)) : 0;
+    static constexpr int kOut = TMA ? 2 * Cfg::TILE * int(sizeof(Out)) : 0;
+    static constexpr int kBits =
+        MODE == MODE_SEGMENTED ? Cfg::STAGES * Cfg::TILE / 8 : 0;
+    static constexpr int off_in = 0;
+    static constexpr int off_out = align_up_c(off_in + kIn, 128);
+    static constexpr int off_bits = align_up_c(off_out + kOut, 128);
+    static constexpr int off_bar = align_up_c(off_bits + kBits, 128);
+    static constexpr int off_tile = off_bar + 16 * Cfg::STAGES;
+    static constexpr int off_wtot = align_up_c(off_tile + 8 * Cfg::STAGES, 16);
+    static constexpr int off_carry = off_wtot + 16 * Cfg::CWARPS;
+    static constexpr int off_abort = off_carry + 16;
+    static constexpr int bytes = align_up_c(off_abort + 16, 128);
+};
+
+// --------------------------------------------------- 32-bit word shuffles
+template <class T>
+__device__ __forceinline__ T shfl_up_any(T v, int d) {
+    static_assert(sizeof(T) % 4 == 0, "word-sized types only");
+    constexpr int W = sizeof(T) / 4;
+    uint32_t w[W];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = __shfl_up_sync(0xffffffffu, w[i], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+template <class T>
+__device__ __forceinline__ T shfl_down_any(T v, int d) {
+    constexpr int W = sizeof(T) / 4;
+    uint32_t w[W];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = __shfl_down_sync(0xffffffffu, w[i], d);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+template <class T>
+__device__ __forceinline__ T shfl_idx_any(T v, int src) {
+    constexpr int W = sizeof(T) / 4;
+    uint32_t w[W];
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = __shfl_sync(0xffffffffu, w[i], src);
+    T r;
+    memcpy(&r, w, sizeof(T));
+    return r;
+}
+
+// ------------------------------------------ element <-> 16-byte chunk packs
+template <class T>
+__device__ __forceinline__ T word_to(uint32_t w) {
+    T r;
+    memcpy(&r, &w, sizeof(T));
+    return r;
+}
+template <class T>
+__device__ __forceinline__ uint32_t to_word(T v) {
+    uint32_t w;
+    memcpy(&w, &v, sizeof(T));
+    return w;
+}
+
+template <class E, int ITEMS, int C>
+__device__ __forceinline__ void unpack_chunks(const uint4 (&t)[C], E (&e)[ITEMS]) {
+    static_assert(ITEMS * sizeof(E) == 16 * C, "chunk size mismatch");
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        const uint32_t w[4] = {t[c].x, t[c].y, t[c].z, t[c].w};
+        if constexpr (sizeof(E) == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) e[4 * c + q] = word_to<E>(w[q]);
+        } else {
+            static_assert(sizeof(E) == 2, "2- or 4-byte elements");
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                e[8 * c + 2 * q] = static_cast<E>(w[q] & 0xffffu);
+                e[8 * c + 2 * q + 1] = static_cast<E>(w[q] >> 16);
+            }
+        }
+    }
+}
+
+template <class E, int ITEMS, int C>
+__device__ __forceinline__ void pack_chunks(const E (&e)[ITEMS], uint4 (&t)[C]) {
+    static_assert(ITEMS * sizeof(E) == 16 * C, "chunk size mismatch");
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        uint32_t w[4];
+        if constexpr (sizeof(E) == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) w[q] = to_word(e[4 * c + q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                w[q] = static_cast<uint32_t>(e[8 * c + 2 * q]) |
+                       (static_cast<uint32_t>(e[8 * c + 2 * q + 1]) << 16);
+        }
+        t[c] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// t[j] <- t[j ^ xr] for all j (an involution), done with selects.
+template <int C>
+__device__ __forceinline__ void xor_permute(uint4 (&t)[C], uint32_t xr) {
+#pragma unroll
+    for (int b = 1; b < C; b <<= 1) {
+        const bool sw = (xr & b) != 0;
+#pragma unroll
+        for (int j = 0; j < C; ++j) {
+            if (!(j & b)) {
+                uint4 a = t[j], c = t[j | b];
+                t[j] = sw ? c : a;
+                t[j | b] = sw ? a : c;
+            }
+        }
+    }
+}
+
+// Rotation that makes each quarter-warp's 16-byte accesses hit 8 distinct
+// 16-byte bank groups when every lane owns C consecutive chunks.
+template <int C>
+__device__ __forceinline__ uint32_t chunk_rot(int lane) {
+    if constexpr (C == 1) {
+        return 0u;
+    } else {
+        return static_cast<uint32_t>((lane / (8 / C)) % C);
+    }
+}
+
+// Thread-blocked load of ITEMS elements from a shared-memory tile.
+template <class E, int ITEMS>
+__device__ __forceinline__ void lds_blocked(const uint8_t *tile_smem, int tid,
+                                            int lane, E (&e)[ITEMS]) {
+    constexpr int BYTES = ITEMS * int(sizeof(E));
+    constexpr int C = BYTES / 16;
+    static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
+    const uint8_t *p = tile_smem + tid * BYTES;
+    const uint32_t xr = chunk_rot<C>(lane);
+    uint4 t[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+        t[j] = *reinterpret_cast<const uint4 *>(p + 16 * (j ^ xr));
+    xor_permute<C>(t, xr);
+    unpack_chunks<E, ITEMS, C>(t, e);
+}
+
+// Thread-blocked store of ITEMS elements into a shared-memory region.
+template <class E, int ITEMS>
+__device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
+                                            const E (&e)[ITEMS]) {
+    constexpr int BYTES = ITEMS * int(sizeof(E));
+    constexpr int C = BYTES / 16;
+    static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
+    uint8_t *p = region + idx * BYTES;
+    const uint32_t xr = chunk_rot<C>(lane);
+    uint4 t[C];
+    pack_chunks<E, ITEMS, C>(e, t);
+    xor_permute<C>(t, xr);
+#pragma unroll
+    for (int j = 0; j < C; ++j)
+        *reinterpret_cast<uint4 *>(p + 16 * (j ^ xr)) = t[j];
+}
+
+// ------------------------------------------------------------ status words
+template <class K>
+struct StatusIO {
+    using Car = typename K::Car;
+    static constexpr int W = int(sizeof(Car) / 4);
+
+    __device__ static void publish(uint64_t *status, int64_t t, uint32_t tag,
+                                   Car c) {
+        uint32_t w[W];
+        memcpy(w, &c, sizeof(Car));
+#pragma unroll
+        for (int i = 0; i < W; ++i)
+            st_relaxed_gpu(status + t * W + i,
+                           (static_cast<uint64_t>(w[i]) << 32) | tag);
+    }
+    // State of tile t for this launch (ST_INVALID if absent or torn).
+    __device__ static uint32_t read(const uint64_t *status, int64_t t,
+                                    uint32_t ebase, Car &c) {
+        uint32_t w[W];
+        const uint64_t r0 = ld_relaxed_gpu(status + t * W);
+        const uint32_t tag0 = static_cast<uint32_t>(r0);
+        w[0] = static_cast<uint32_t>(r0 >> 32);
+        bool same = true;
+#pragma unroll
+        for (int i = 1; i < W; ++i) {
+            const uint64_t r = ld_relaxed_gpu(status + t * W + i);
+            same = same && (static_cast<uint32_t>(r) == tag0);
+            w[i] = static_cast<uint32_t>(r >> 32);
+        }
+        if (!same || (tag0 & ~3u) != ebase) return ST_INVALID;
+        const uint32_t st = tag0 & 3u;
+        if (st != ST_AGGREGATE && st != ST_INCLUSIVE) return ST_INVALID;
+        memcpy(&c, w, sizeof(Car));
+        return st;
+    }
+};
+
+// Records that a wait of this launch gave up; later waits of the same launch
+// then give up at once, so a launch never takes much more than one limit.
+__device__ __forceinline__ void note_gave_up(const WaitCtx &w, uint32_t bit) {
+    atomicOr(w.ctl + CTL_ERROR, bit);
+    atomicExch(w.ctl + CTL_ERR_EPOCH, w.epoch + 1u);
+}
+__device__ __forceinline__ bool launch_gave_up(const WaitCtx &w) {
+    return *reinterpret_cast<volatile uint32_t *>(w.ctl + CTL_ERR_EPOCH) ==
+           w.epoch + 1u;
+}
+
+// Bounded wait on an mbarrier phase; false (and a device error bit) if the
+// limit ran out.
+__device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
+                                           const WaitCtx &w) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > w.limit_ns || launch_gave_up(w)) {
+            note_gave_up(w, DEV_ERR_BARRIER_WAIT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Decoupled look-back, run by one full warp: exclusive prefix of tile t.
+template <class K>
+__device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
+                                    int64_t t, uint32_t ebase, int lane) {
+    using Car = typename K::Car;
+    Car excl = K::cident();
+    int64_t base = t - 1;
+    uint64_t t0 = 0;
+    bool started = false, gave_up = false;
+    while (true) {
+        const int64_t idx = base - lane;
+        Car val = K::cident();
+        uint32_t need;
+        uint32_t inc;
+        while (true) {
+            uint32_t st = ST_INCLUSIVE;  // before tile 0: identity, inclusive
+            val = K::cident();
+            if (idx >= 0) st = StatusIO<K>::read(p.status, idx, ebase, val);
+            if (gave_up && st == ST_INVALID) {
+                st = ST_INCLUSIVE;
+                val = K::cident();
+            }
+            inc = __ballot_sync(0xffffffffu, st == ST_INCLUSIVE);
+            const uint32_t bad = __ballot_sync(0xffffffffu, st == ST_INVALID);
+            // lanes 0..(first inclusive lane), or all 32 if none is inclusive
+            need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
+            if ((bad & need) == 0) break;
+            if (!started) {
+                t0 = global_timer_ns();
+                started = true;
+            } else {
+                bool over = (global_timer_ns() - t0) > wc.limit_ns ||
+                            launch_gave_up(wc);
+                over = __shfl_sync(0xffffffffu, over, 0);
+                if (over && !gave_up) {
+                    gave_up = true;
+                    if (lane == 0) note_gave_up(wc, DEV_ERR_CARRY_WAIT);
+                }
+            }
+        }
+        // ordered reduction: higher lanes hold earlier tiles
+        Car agg = ((need >> lane) & 1u) ? val : K::cident();
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const Car o = shfl_down_any(agg, off);
+            if (lane + off < 32) agg = K::cop(o, agg);
+        }
+        const Car win = shfl_idx_any(agg, 0);
+        excl = K::cop(win, excl);
+        if (inc) break;
+        base -= 32;
+    }
+    return excl;
+}
+
+// Chained hand-off (Algorithm 4): wait for tile t-1's inclusive prefix.
+template <class K>
+__device__ typename K::Car chained_wait(const ScanParams &p, const WaitCtx &wc,
+                                        int64_t t, uint32_t ebase, int lane) {
+    using Car = typename K::Car;
+    Car v = K::cident();
+    if (lane == 0) {
+        uint32_t st = StatusIO<K>::read(p.status, t - 1, ebase, v);
+        if (st != ST_INCLUSIVE) {
+            const uint64_t t0 = global_timer_ns();
+            while (true) {
+                st = StatusIO<K>::read(p.status, t - 1, ebase, v);
+                if (st == ST_INCLUSIVE) break;
+                if (global_timer_ns() - t0 > wc.limit_ns || launch_gave_up(wc)) {
+                    note_gave_up(wc, DEV_ERR_CARRY_WAIT);
+                    v = K::cident();
+                    break;
+                }
+            }
+        }
+    }
+    return shfl_idx_any(v, 0);
+}
+
+// First index i in [0, cnt) with a[i] >= key (cnt if none); whole warp.
+__device__ __forceinline__ int64_t warp_lower_bound(const int64_t *a,
+                                                    int64_t cnt, int64_t key,
+                                                    int lane) {
+    int64_t lo = 0, hi = cnt;
+    while (hi - lo > 32) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t probe = lo + static_cast<int64_t>(lane + 1) * step - 1;
+        const bool ge = probe >= hi ? true : (a[probe] >= key);
+        const uint32_t m = __ballot_sync(0xffffffffu, ge);
+        if (m == 0) return hi;
+        const int b = __ffs(m) - 1;
+        const int64_t nlo = lo + static_cast<int64_t>(b) * step;
+        const int64_t nhi = lo + static_cast<int64_t>(b + 1) * step;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    if (lo >= hi) return hi;
+    const int64_t i = lo + lane;
+    const bool ge = i >= hi ? true : (a[i] >= key);
+    const uint32_t m = __ballot_sync(0xffffffffu, ge);
+    if (m == 0) return hi;
+    const int64_t r = lo + (__ffs(m) - 1);
+    return r < hi ? r : hi;
+}
+
+// ------------------------------------------------------------------ kernel
+template <class K, class Cfg, int MODE, bool TMA>
+__global__ void __launch_bounds__(Cfg::THREADS)
+    lscan_kernel(const ScanParams p) {
+    using In = typename K::In;
+    using Out = typename K::Out;
+    using Acc = typename K::Acc;
+    using Car = typename K::Car;
+    using CarA = typename K::CarA;
+    using L = Layout<K, Cfg, MODE, TMA>;
+    constexpr int ITEMS = Cfg::ITEMS;
+    constexpr int CW = Cfg::CWARPS;
+    constexpr int CT = Cfg::CTHREADS;
+    constexpr int TILE = Cfg::TILE;
+    constexpr int ST = Cfg::STAGES;
+    constexpr bool SEG = MODE == MODE_SEGMENTED;
+    static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
+
+    extern __shared__ __align__(128) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::off_bar);
+    uint64_t *empty = full + ST;
+    volatile int64_t *tile_of = reinterpret_cast<int64_t *>(smem + L::off_tile);
+    WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
+    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);
+    volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
+    volatile uint32_t *stop_s = abort_s + 1;
+    uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+
+    if (tid == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+            tile_of[s] = INT64_MAX;
+        }
+        *abort_s = 0;
+        *stop_s = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const uint32_t epoch = *reinterpret_cast<volatile uint32_t *>(p.ctl + CTL_EPOCH);
+    const uint32_t ebase = (epoch & kEpochMask) << 2;
+    const WaitCtx wc{p.ctl, p.wait_limit_ns, epoch};
+    const In *__restrict__ x = static_cast<const In *>(p.x);
+    Out *__restrict__ y = static_cast<Out *>(p.y);
+
+    if (warp == CW) {
+        // ============================ producer warp ============================
+        uint32_t armed_mask = 0;  // slots that ever got a bulk copy
+        uint32_t par_mask = 0;    // parity of each slot's last bulk copy
+        for (int64_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % ST);
+            if (k >= ST) {
+                // lane 0 waits; the decision is made warp-uniform
+                bool ok = true;
+                if (lane == 0)
+                    ok = wait_phase(&empty[s], static_cast<uint32_t>(((k / ST) - 1) & 1), wc);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                __syncwarp();
+                if (!ok) {
+                    if (lane == 0) *abort_s = 1;
+                    break;
+                }
+            }
+            int64_t t = 0;
+            if (lane == 0) t = static_cast<int64_t>(atomicAdd(p.ctl + CTL_TICKET, 1u));
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (lane == 0) tile_of[s] = t;
+            if (t >= p.n_tiles) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+                break;
+            }
+            const int64_t ts = t * TILE;
+            const int64_t te = (ts + TILE < p.n) ? ts + TILE : p.n;
+            if constexpr (SEG) {
+                uint32_t *bm = bits + s * (TILE / 32);
+                for (int i = lane; i < TILE / 32; i += 32) bm[i] = 0u;
+                __syncwarp();
+                const int64_t sa = warp_lower_bound(p.offsets, p.n_seg + 1, ts, lane);
+                for (int64_t i0 = sa; i0 <= p.n_seg; i0 += 32) {
+                    const int64_t i = i0 + lane;
+                    const int64_t o = (i <= p.n_seg) ? p.offsets[i] : te;
+                    if (o >= ts && o < te) {
+                        const int64_t r = o - ts;
+                        atomicOr(&bm[r >> 5], 1u << (r & 31));
+                    }
+                    if (__ballot_sync(0xffffffffu, o < te) != 0xffffffffu) break;
+                }
+                __threadfence_block();
+            }
+            __syncwarp();
+            if (lane == 0) {
+                const bool full_tile = (te - ts) == TILE;
+                if (TMA && full_tile) {
+                    constexpr uint32_t bytes = TILE * sizeof(In);
+                    mbar_arrive_expect_tx(&full[s], bytes);
+                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), x + ts,
+                             bytes, &full[s]);
+                    armed_mask |= 1u << s;
+                    par_mask = (par_mask & ~(1u << s)) |
+                               (static_cast<uint32_t>((k / ST) & 1) << s);
+                } else {
+                    mbar_arrive(&full[s]);
+                }
+            }
+        }
+        // never leave the CTA with a bulk copy still writing its shared memory
+        if (lane == 0) {
+#pragma unroll
+            for (int s = 0; s < ST; ++s)
+                if (armed_mask & (1u << s))
+                    (void)wait_phase(&full[s], (par_mask >> s) & 1u, wc);
+        }
+    } else {
+        // ============================ consumer warps ===========================
+        const int e0 = tid * ITEMS;  // first element of this thread in a tile
+        for (int64_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % ST);
+            const bool ok = wait_phase(&full[s], static_cast<uint32_t>((k / ST) & 1), wc);
+            if (!__all_sync(0xffffffffu, ok) && lane == 0) *abort_s = 1;
+            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
+            if (t >= p.n_tiles) break;
+            const int64_t ts = t * TILE;
+            const int64_t rem = p.n - ts;
+            const int nt = rem < TILE ? static_cast<int>(rem) : TILE;
+            const bool full_tile = nt == TILE;
+
+            // ---- load (Section 4.1 step 1) ----
+            Acc v[ITEMS];
+            if (TMA && full_tile) {
+                In xv[ITEMS];
+                lds_blocked<In, ITEMS>(smem + L::off_in + s * TILE * sizeof(In),
+                                       tid, lane, xv);
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) v[i] = K::load(xv[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i)
+                    v[i] = (e0 + i < nt) ? K::load(x[ts + e0 + i]) : K::ident();
+            }
+            uint32_t hb = 0;  // head bits of my ITEMS elements
+            if constexpr (SEG) {
+                const uint32_t w = bits[s * (TILE / 32) + (e0 >> 5)];
+                hb = (w >> (e0 & 31)) & (ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+
+            // ---- thread-serial scan ----
+#pragma unroll
+            for (int i = 1; i < ITEMS; ++i) {
+                if (SEG && ((hb >> i) & 1u)) continue;
+                v[i] = K::op(v[i - 1], v[i]);
+            }
+            // ---- warp scan of thread totals (Hillis-Steele, 5 rounds) ----
+            Acc wv = v[ITEMS - 1];
+            uint32_t wf = SEG ? (hb != 0u) : 0u;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const Acc ov = shfl_up_any(wv, d);
+                const uint32_t of = SEG ? __shfl_up_sync(0xffffffffu, wf, d) : 0u;
+                if (lane >= d) {
+                    if (!(SEG && wf)) wv = K::op(ov, wv);
+                    wf |= of;
+                }
+            }
+            // exclusive lane prefix
+            Acc lv = shfl_up_any(wv, 1);
+            uint32_t lf = SEG ? __shfl_up_sync(0xffffffffu, wf, 1) : 0u;
+            if (lane == 0) {
+                lv = K::ident();
+                lf = 0u;
+            }
+            // ---- block scan of warp totals (Algorithm 3) ----
+            if (lane == 31) {
+                wtot[warp].v = wv;
+                wtot[warp].f = wf;
+            }
+            named_bar_sync(1, CT);
+            Acc bv = K::ident();
+            uint32_t bf = 0u;
+            if (lane < CW) {
+                bv = wtot[lane].v;
+                bf = SEG ? wtot[lane].f : 0u;
+            }
+#pragma unroll
+            for (int d = 1; d < CW; d <<= 1) {
+                const Acc ov = shfl_up_any(bv, d);
+                const uint32_t of = SEG ? __shfl_up_sync(0xffffffffu, bf, d) : 0u;
+                if (lane >= d) {
+                    if (!(SEG && bf)) bv = K::op(ov, bv);
+                    bf |= of;
+                }
+            }
+            const Acc tile_agg = shfl_idx_any(bv, CW - 1);
+            const uint32_t tile_f = SEG ? __shfl_sync(0xffffffffu, bf, CW - 1) : 0u;
+            Acc wev = shfl_idx_any(bv, warp > 0 ? warp - 1 : 0);
+            uint32_t wef = SEG ? __shfl_sync(0xffffffffu, bf, warp > 0 ? warp - 1 : 0) : 0u;
+            if (warp == 0) {
+                wev = K::ident();
+                wef = 0u;
+            }
+            // thread base = warp offset (+) lane offset
+            Acc tbv;
+            uint32_t tbf;
+            if (SEG && lf) {
+                tbv = lv;
+            } else {
+                tbv = K::op(wev, lv);
+            }
+            tbf = SEG ? (wef | lf) : 0u;
+
+            // ---- inter-tile carry (Section 4.3) ----
+            if (warp == 0) {
+                const bool skip = (t == p.skip_tile);
+                const Car agg_c = K::to_car(tile_agg);
+                Car excl = K::cident();
+                const bool head0 = SEG ? ((__shfl_sync(0xffffffffu, hb, 0) & 1u) != 0u) : false;
+                if (t == 0) {
+                    if (lane == 0 && !skip)
+                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE, agg_c);
+                } else if (SEG && tile_f) {
+                    // the prefix after the last head does not depend on earlier tiles
+                    if (lane == 0 && !skip)
+                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE, agg_c);
+                    if (!head0) {
+                        excl = p.chained ? chained_wait<K>(p, wc, t, ebase, lane)
+                                         : lookback<K>(p, wc, t, ebase, lane);
+                    }
+                } else {
+                    if (!p.chained && lane == 0 && !skip)
+                        StatusIO<K>::publish(p.status, t, ebase | ST_AGGREGATE, agg_c);
+                    excl = p.chained ? chained_wait<K>(p, wc, t, ebase, lane)
+                                     : lookback<K>(p, wc, t, ebase, lane);
+                    if (lane == 0 && !skip)
+                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
+                                             K::cop(excl, agg_c));
+                }
+                if (lane == 0) {
+                    *carry_s = K::to_apply(excl);
+                    *stop_s = *abort_s;  // one snapshot, read by every warp
+                }
+            }
+            named_bar_sync(1, CT);
+            const CarA cin = *carry_s;
+            const bool stop = *stop_s != 0u;
+
+            // ---- apply carry and write y once (Section 4.4) ----
+            const CarA B = K::base(cin, tbv);            // carry (+) thread base
+            const CarA BL = K::base_local(tbv);          // head earlier in tile
+            const CarA BI = K::base_local(K::ident());   // head earlier in thread
+            Out o[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                Acc pv;
+                bool pf;  // a head at or before the contributing prefix, in thread
+                bool is_ident = false;
+                if (p.inclusive) {
+                    pv = v[i];
+                    pf = SEG && ((hb & ((2u << i) - 1u)) != 0u);
+                } else {
+                    if (SEG && ((hb >> i) & 1u)) {
+                        is_ident = true;
+                        pv = K::ident();
+                        pf = true;
+                    } else if (i == 0) {
+                        pv = K::ident();
+                        pf = false;
+                    } else {
+                        pv = v[i - 1];
+                        pf = SEG && ((hb & ((1u << i) - 1u)) != 0u);
+                    }
+                }
+                (void)is_ident;
+                const CarA b = pf ? BI : ((SEG && tbf) ? BL : B);
+                o[i] = K::fin(b, pv);
+            }
+            if (TMA && full_tile) {
+                constexpr int WBYTES = 32 * ITEMS * int(sizeof(Out));
+                uint8_t *region = smem + L::off_out + (k & 1) * (TILE * sizeof(Out)) +
+                                  warp * WBYTES;
+                if (lane == 0) bulk_wait_read<1>();
+                __syncwarp();
+                sts_blocked<Out, ITEMS>(region, lane, lane, o);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_s2g(y + ts + warp * 32 * ITEMS, region, WBYTES);
+                    bulk_commit();
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i)
+                    if (e0 + i < nt) y[ts + e0 + i] = o[i];
+            }
+            if (stop) break;
+        }
+        if (lane == 0) bulk_wait_all<0>();
+    }
+
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const uint32_t prev = atomicAdd(p.ctl + CTL_DONE, 1u);
+        if (prev == gridDim.x - 1) {
+            // last CTA of this launch: re-arm the scratch for the next launch
+            volatile uint32_t *c = p.ctl;
+            c[CTL_TICKET] = 0u;
+            c[CTL_DONE] = 0u;
+            c[CTL_EPOCH] = epoch + 1u;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace lscan

@@ -1,0 +1,97 @@
+"""C-ABI library checks that need no GPU: it builds, loads, exports every
+symbol include/lscan.h declares, and rejects bad arguments on the host before
+any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1604_04815_gb300 import build
+    build.build()
+    from paper_1604_04815_gb300 import _lib
+    return _lib
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lscan.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lscan_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_expected_symbols(lib):
+    assert _declared_symbols() == sorted(lib.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in _declared_symbols():
+        assert hasattr(so, name), name
+
+
+def test_version_and_configs(lib):
+    assert "sm_103a" in lib.lscan_version()
+    assert lib.lscan_num_configs() == 3
+    for c in range(1, 4):
+        for dt in (lib.LSCAN_I32, lib.LSCAN_F32, lib.LSCAN_BF16):
+            info = lib.lscan_config_info(c, dt)
+            assert info["tile"] == info["items"] * info["threads"]
+            assert info["stages"] >= 2
+    # bulk-copy tiles are 8, 16 and 32 KiB of input
+    assert [lib.lscan_config_info(c, lib.LSCAN_I32)["tile"] * 4
+            for c in (1, 2, 3)] == [8192, 16384, 32768]
+    assert [lib.lscan_config_info(c, lib.LSCAN_BF16)["tile"] * 2
+            for c in (1, 2, 3)] == [8192, 16384, 32768]
+
+
+def test_host_argument_checks(lib):
+    L = lib
+    assert L.lscan_inclusive(L.LSCAN_ADD, L.LSCAN_I32, 16, 32, -1) == \
+        L.LSCAN_ERR_INVALID
+    assert L.lscan_inclusive(L.LSCAN_ADD, L.LSCAN_I32, None, None, 5) == \
+        L.LSCAN_ERR_INVALID
+    assert L.lscan_inclusive(L.LSCAN_ADD, 7, 16, 64, 5) == L.LSCAN_ERR_INVALID
+    assert L.lscan_inclusive(9, L.LSCAN_I32, 16, 64, 5) == L.LSCAN_ERR_INVALID
+    # misaligned element pointers
+    assert L.lscan_inclusive(L.LSCAN_ADD, L.LSCAN_I32, 18, 4096, 5) == \
+        L.LSCAN_ERR_INVALID
+    # partial overlap is rejected; identical ranges are the in-place case
+    base = 1 << 20
+    assert L.lscan_inclusive(L.LSCAN_ADD, L.LSCAN_I32, base, base + 4, 100) == \
+        L.LSCAN_ERR_INVALID
+    # bf16 add writes fp32 by default: same start is an overlap, not in-place
+    assert L.lscan_inclusive(L.LSCAN_ADD, L.LSCAN_BF16, base, base, 100) == \
+        L.LSCAN_ERR_INVALID
+    # unsupported output dtype / precision
+    o = L.make_options(out_dtype=L.LSCAN_BF16)
+    assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, 10, o) == \
+        L.LSCAN_ERR_UNSUPPORTED
+    o = L.make_options(precision=9)
+    assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
+        L.LSCAN_ERR_UNSUPPORTED
+    o = L.make_options(config=7)
+    assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
+        L.LSCAN_ERR_INVALID
+    o = L.make_options(carry=5)
+    assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
+        L.LSCAN_ERR_INVALID
+    # batched: negative counts, missing offsets
+    assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, None,
+                           3, 10) == L.LSCAN_ERR_INVALID
+    assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, base * 4,
+                           -1, 10) == L.LSCAN_ERR_INVALID
+    assert L.lscan_set_wait_limit_ns(0) == L.LSCAN_ERR_INVALID
+    assert L.strerror(L.LSCAN_ERR_TIMEOUT) == "device wait ran out of time"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_1604_04815_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no fallback"):
+        _lib.load()

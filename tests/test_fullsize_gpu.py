@@ -1,0 +1,34 @@
+"""Parity at the full single-array sizes (N = 2^28) in the launch
+configuration bench.py times (default tuned tile configuration, decoupled
+look-back, FP64 carry for fp32 add): every output element is compared with the
+oracle, which finishes a 2^28 scan in about a second."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import assert_matches, run_c_abi, to_device, to_host
+from paper_1604_04815_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+N = 1 << 28
+
+
+@pytest.mark.parametrize("case", ["i32_add", "i32_max", "f32_add"])
+def test_full_size(case):
+    from paper_1604_04815_gb300 import build
+    build.build()
+    if case == "i32_add":
+        op, dtype, x = "add", "i32", workloads.large_i32_add(N)
+    elif case == "i32_max":
+        op, dtype, x = "max", "i32", workloads.large_i32_max(N)
+    else:
+        op, dtype, x = "add", "f32", workloads.large_f32_add(N)
+    xd = to_device(x, dtype)
+    y = run_c_abi(op, dtype, xd, True)
+    got = to_host(y)
+    del xd, y
+    torch.cuda.empty_cache()
+    ratio = assert_matches(op, dtype, x, got, True, "f64")
+    if op == "add" and dtype == "f32":
+        print(f"fp32 add N=2^28 max err/S_j = {ratio:.3e}")

@@ -1,0 +1,337 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element, over every kind, tile configuration, inclusive/exclusive,
+ragged sizes, unaligned and in-place buffers, both carry protocols and the
+batched (segmented) mode.  Integer and max scans must be bit-exact; float add
+must stay within |err_j| <= c * S_j (c = 1e-5 for the fp32/FP64 carry paths,
+2.5e-7 for the compensated path)."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import (assert_matches, run_c_abi, to_device, to_host, LDT, LOP,
+                      PREC_CODE, TEST_WAIT_NS)
+from paper_1604_04815_gb300 import _lib
+from paper_1604_04815_gb300.workloads import (random_array, batched_lengths,
+                                              offsets_from_lengths)
+
+pytestmark = pytest.mark.gpu
+
+# (op, dtype, precision, bf16 output)
+KINDS = [
+    ("add", "i32", None, False),
+    ("max", "i32", None, False),
+    ("max", "f32", None, False),
+    ("max", "bf16", None, False),
+    ("add", "f32", "plain", False),
+    ("add", "f32", "f64", False),
+    ("add", "f32", "comp", False),
+    ("add", "bf16", "plain", False),
+    ("add", "bf16", "f64", False),
+    ("add", "bf16", "comp", False),
+    ("add", "bf16", "plain", True),
+    ("add", "bf16", "f64", True),
+    ("add", "bf16", "comp", True),
+]
+KIND_IDS = [f"{o}-{d}-{p or 'exact'}{'-bf16out' if b else ''}"
+            for o, d, p, b in KINDS]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1604_04815_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+    _lib.load()
+    _lib.lscan_set_wait_limit_ns(TEST_WAIT_NS)
+    yield
+
+
+def _input(op, dtype, n, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == "i32":
+        return random_array("i32", n, rng, kind="full" if op == "max" or
+                            seed % 2 else "uniform")
+    return random_array(dtype, n, rng, kind="signed")
+
+
+def _tile(config, dtype):
+    return _lib.lscan_config_info(config, LDT[dtype])["tile"]
+
+
+def _sizes(tile):
+    return [1, 2, 31, 33, 1000, tile - 1, tile, tile + 1, 7 * tile + 123]
+
+
+@pytest.mark.parametrize("config", [1, 2, 3])
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
+def test_sizes_configs(kind, inclusive, config):
+    op, dtype, prec, ob = kind
+    for i, n in enumerate(_sizes(_tile(config, dtype))):
+        x = _input(op, dtype, n, seed=1000 * config + i)
+        y = run_c_abi(op, dtype, to_device(x, dtype), inclusive, prec=prec,
+                      config=config, out_bf16=ob)
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       out_bf16=ob)
+
+
+def test_empty_input_launches_nothing():
+    before = _lib.lscan_launch_count()
+    x = torch.empty(0, dtype=torch.int32, device="cuda")
+    y = torch.empty(0, dtype=torch.int32, device="cuda")
+    st = _lib.lscan_inclusive(_lib.LSCAN_ADD, _lib.LSCAN_I32, x.data_ptr(),
+                              y.data_ptr(), 0,
+                              torch.cuda.current_stream().cuda_stream)
+    assert st == _lib.LSCAN_OK
+    assert _lib.lscan_launch_count() == before
+
+
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
+def test_unaligned_pointers(kind, inclusive):
+    """x and/or y not 16-byte aligned: the plain-load path."""
+    op, dtype, prec, ob = kind
+    for (px, py), n in (((1, 0), 5000), ((0, 1), 70001), ((3, 1), 1)):
+        x = _input(op, dtype, n, seed=77 + n)
+        xd = to_device(x, dtype, pad_front=px)
+        odt = (torch.bfloat16 if ob else torch.float32) if (
+            op == "add" and dtype == "bf16") else xd.dtype
+        yb = torch.empty(n + py, dtype=odt, device="cuda")
+        y = run_c_abi(op, dtype, xd, inclusive, prec=prec, out_bf16=ob,
+                      y_dev=yb[py:])
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       out_bf16=ob)
+
+
+@pytest.mark.parametrize("config", [1, 3])
+@pytest.mark.parametrize("kind", [k for k in KINDS
+                                  if not (k[0] == "add" and k[1] == "bf16")],
+                         ids=[i for k, i in zip(KINDS, KIND_IDS)
+                              if not (k[0] == "add" and k[1] == "bf16")])
+def test_in_place(kind, config):
+    """y == x (Section 4.5): every element is read before it is written."""
+    op, dtype, prec, ob = kind
+    n = 9 * _tile(config, dtype) + 5
+    x = _input(op, dtype, n, seed=5)
+    xd = to_device(x, dtype)
+    y = run_c_abi(op, dtype, xd, True, prec=prec, config=config, y_dev=xd)
+    assert y.data_ptr() == xd.data_ptr()
+    assert_matches(op, dtype, x, to_host(y), True, prec or "f64")
+
+
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", [KINDS[0], KINDS[1], KINDS[5], KINDS[9]],
+                         ids=[KIND_IDS[0], KIND_IDS[1], KIND_IDS[5],
+                              KIND_IDS[9]])
+def test_chained_carry(kind, inclusive):
+    """The paper's neighbour-to-neighbour hand-off (Algorithm 4)."""
+    op, dtype, prec, ob = kind
+    for n in (1, 4096 * 3 + 1, (1 << 20) + 7):
+        x = _input(op, dtype, n, seed=n)
+        y = run_c_abi(op, dtype, to_device(x, dtype), inclusive, prec=prec,
+                      carry=_lib.LSCAN_CARRY_CHAINED, out_bf16=ob)
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       out_bf16=ob)
+
+
+@pytest.mark.parametrize("prec", ["plain", "f64", "comp"])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_float_integer_values_bit_exact(dtype, prec):
+    """Integer-valued inputs keep every fp32 prefix exact (< 2^24), so every
+    float path must reproduce the oracle bit for bit."""
+    rng = np.random.default_rng(12)
+    n = (1 << 20) + 3
+    x = random_array(dtype, n, rng, kind="intval")
+    y = run_c_abi("add", dtype, to_device(x, dtype), True, prec=prec)
+    got = to_host(y).astype(np.float64)
+    want = __import__("oracle").scan("add", dtype, x, True)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
+def test_one_mebi(kind):
+    op, dtype, prec, ob = kind
+    n = (1 << 20) + 7
+    x = _input(op, dtype, n, seed=3)
+    for inclusive in (True, False):
+        y = run_c_abi(op, dtype, to_device(x, dtype), inclusive, prec=prec,
+                      out_bf16=ob)
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       out_bf16=ob)
+
+
+def test_small_i32_workload_bit_exact():
+    """The 2^20 int32 workload (uniform [-1000, 1000], seed 0)."""
+    from paper_1604_04815_gb300.workloads import small_i32
+    x = small_i32()
+    y = run_c_abi("add", "i32", to_device(x, "i32"), True)
+    assert_matches("add", "i32", x, to_host(y), True)
+
+
+# ------------------------------------------------------------ batched mode
+def _offsets(kind, rng):
+    if kind == "mixed":
+        lens = [0, 1, 0, 5, 2048, 0, 2, 4095, 4096, 4097, 1, 30000, 0, 3]
+    elif kind == "tiny":
+        lens = [1] * 4096
+    elif kind == "huge_plus_tiny":
+        lens = [300001] + [1, 2, 0, 3] * 500
+    elif kind == "empty_tail":
+        lens = [10, 0, 0, 0]
+    else:  # log-uniform like the batched workload, smaller
+        lens = batched_lengths(300, max_log2=14, seed=int(rng.integers(1e6)))
+    return offsets_from_lengths(lens)
+
+
+@pytest.mark.parametrize("pattern", ["mixed", "tiny", "huge_plus_tiny",
+                                     "empty_tail", "loguniform"])
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", [KINDS[0], KINDS[1], KINDS[2], KINDS[3],
+                                  KINDS[5], KINDS[6], KINDS[8]],
+                         ids=[KIND_IDS[i] for i in (0, 1, 2, 3, 5, 6, 8)])
+def test_batched(kind, inclusive, pattern):
+    op, dtype, prec, ob = kind
+    rng = np.random.default_rng(sum(map(ord, pattern)))
+    off = _offsets(pattern, rng)
+    n = int(off[-1])
+    x = _input(op, dtype, n, seed=9)
+    for config in (1, 2, 3):
+        xd = to_device(x, dtype)
+        od = torch.from_numpy(off).cuda()
+        y = torch.empty(n, dtype=torch.float32 if (op == "add" and
+                        dtype == "bf16") else xd.dtype, device="cuda")
+        opts = _lib.make_options(precision=PREC_CODE[prec] if prec else 0,
+                                 config=config)
+        s = torch.cuda.current_stream().cuda_stream
+        st = _lib.lscan_batched(LOP[op], LDT[dtype], int(inclusive),
+                                xd.data_ptr(), y.data_ptr(), od.data_ptr(),
+                                len(off) - 1, n, opts, s)
+        assert st == _lib.LSCAN_OK
+        assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       offsets=off)
+
+
+def test_batched_unaligned_and_chained():
+    off = _offsets("mixed", None)
+    n = int(off[-1])
+    x = _input("add", "i32", n, seed=4)
+    xd = to_device(x, "i32", pad_front=1)
+    od = torch.from_numpy(off).cuda()
+    for carry in (_lib.LSCAN_CARRY_LOOKBACK, _lib.LSCAN_CARRY_CHAINED):
+        y = torch.empty(n, dtype=torch.int32, device="cuda")
+        opts = _lib.make_options(carry=carry)
+        s = torch.cuda.current_stream().cuda_stream
+        st = _lib.lscan_batched(LOP["add"], LDT["i32"], 1, xd.data_ptr(),
+                                y.data_ptr(), od.data_ptr(), len(off) - 1, n,
+                                opts, s)
+        assert st == _lib.LSCAN_OK
+        assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
+        assert_matches("add", "i32", x, to_host(y), True, offsets=off)
+
+
+# -------------------------------------------------- robustness of the carry
+def test_many_launches_epoch_and_ticket_rearm():
+    """Hundreds of back-to-back launches of varying size on one stream: the
+    kernel re-arms the ticket and advances the epoch itself."""
+    rng = np.random.default_rng(21)
+    xs = [random_array("i32", int(n), rng, kind="full")
+          for n in rng.integers(1, 200000, size=40)]
+    devs = [to_device(x, "i32") for x in xs]
+    outs = []
+    for rep in range(5):
+        for xd in devs:
+            outs.append(run_c_abi("add", "i32", xd, True, config=1,
+                                  check_status=False))
+    assert _lib.lscan_stream_status(
+        torch.cuda.current_stream().cuda_stream) == _lib.LSCAN_OK
+    for rep in range(5):
+        for i, x in enumerate(xs):
+            assert_matches("add", "i32", x, to_host(outs[rep * len(xs) + i]))
+
+
+def test_concurrent_streams_independent_scratch():
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    rng = np.random.default_rng(5)
+    xs = [random_array("i32", 3_000_000 + 17 * i, rng, kind="full")
+          for i in range(4)]
+    devs = [to_device(x, "i32") for x in xs]
+    torch.cuda.synchronize()
+    ys = []
+    for s, xd in zip(streams, devs):
+        with torch.cuda.stream(s):
+            ys.append(run_c_abi("add", "i32", xd, True, check_status=False))
+    for s in streams:
+        assert _lib.lscan_stream_status(s.cuda_stream) == _lib.LSCAN_OK
+    for x, y in zip(xs, ys):
+        assert_matches("add", "i32", x, to_host(y))
+
+
+def test_wait_timeout_reports_and_recovers():
+    """A tile that never publishes (host-injected): its successors' bounded
+    waits run out, the launch finishes, the host gets LSCAN_ERR_TIMEOUT, and
+    the next launch on the same stream is correct."""
+    s = torch.cuda.current_stream().cuda_stream
+    x = random_array("i32", 64 * 4096, np.random.default_rng(1))
+    xd = to_device(x, "i32")
+    assert _lib.lscan_set_wait_limit_ns(20_000_000) == _lib.LSCAN_OK
+    try:
+        for carry in (_lib.LSCAN_CARRY_LOOKBACK, _lib.LSCAN_CARRY_CHAINED):
+            _lib.lscan_debug_skip_publish(3)
+            run_c_abi("add", "i32", xd, True, carry=carry, config=2,
+                      check_status=False)
+            assert _lib.lscan_stream_status(s) == _lib.LSCAN_ERR_TIMEOUT
+            y = run_c_abi("add", "i32", xd, True, carry=carry, config=2)
+            assert_matches("add", "i32", x, to_host(y))
+    finally:
+        _lib.lscan_set_wait_limit_ns(TEST_WAIT_NS)
+        _lib.lscan_debug_skip_publish(-1)
+
+
+def test_graph_replay_batched():
+    import paper_1604_04815_gb300 as lscan
+    off = _offsets("loguniform", np.random.default_rng(3))
+    n = int(off[-1])
+    rng = np.random.default_rng(8)
+    x = random_array("i32", n, rng, kind="full")
+    xd = to_device(x, "i32")
+    od = torch.from_numpy(off).cuda()
+    y = torch.empty_like(xd)
+    g = lscan.Graph.batched(xd, od, y)
+    try:
+        for rep in range(3):
+            x = random_array("i32", n, rng, kind="full")
+            xd.copy_(torch.from_numpy(x))
+            g.launch()
+            g.status()
+            assert_matches("add", "i32", x, to_host(y), offsets=off)
+    finally:
+        g.close()
+
+
+def test_graph_replay_single():
+    import paper_1604_04815_gb300 as lscan
+    rng = np.random.default_rng(9)
+    n = 5_000_001
+    x = random_array("f32", n, rng, kind="signed")
+    xd = to_device(x, "f32")
+    y = torch.empty_like(xd)
+    g = lscan.Graph.scan(xd, y)
+    try:
+        for _ in range(3):
+            g.launch()
+            g.status()
+            assert_matches("add", "f32", x, to_host(y))
+    finally:
+        g.close()
+
+
+def test_torch_front_matches_c_abi():
+    import paper_1604_04815_gb300 as lscan
+    x = random_array("bf16", 123457, np.random.default_rng(2), kind="signed")
+    xd = to_device(x, "bf16")
+    a = lscan.inclusive(xd)
+    b = run_c_abi("add", "bf16", xd, True)
+    lscan.stream_status()
+    assert torch.equal(a, b)
+    assert a.dtype == torch.float32
