@@ -1,0 +1,484 @@
+"""Benchmark: single-pass scan throughput on one GB300 (and N replicas).
+
+One step = one pass of the scan path over the single-array workload: an
+inclusive int32 add-scan (uniform [-2^15, 2^15]), an inclusive int32
+max-scan (full int32 range) and an inclusive fp32 add-scan (uniform [0, 1),
+FP64 carry), each over N = 2^28 elements already resident in HBM.
+value = bytes moved (each element read once and written once) / time, summed
+over ranks.  Inputs are 1 GiB per array, far above the 129 MB L2, so no L2
+flush is needed between steps.
+
+Also reported on the same line:
+  roofline     dominant kernel's algorithmic GB/s vs the measured HBM copy peak
+  e2e          the same scans through the C ABI from pinned HOST buffers,
+               with the host->device and device->host copies timed
+  batched      4096 log-uniform arrays (lengths 1..2^20) in one persistent
+               launch replayed from a CUDA graph, vs 4096 plain launches
+  cpu_baseline the sequential CPU oracle timed on a bounded sample
+  clocks       nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle (the slow reference program) on the
+same workload, one bounded sample per step.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 1 << 28
+METRIC = ("scan GB/s & % of HBM peak, batched vs per-array; "
+          "p50/p99 served latency")
+CASES = [  # (name, op, dtype)
+    ("i32_add", "add", "i32"),
+    ("i32_max", "max", "i32"),
+    ("f32_add", "add", "f32"),
+]
+ELEM_BYTES = {"i32": 4, "f32": 4, "bf16": 2}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _inputs(case, n):
+    from paper_1604_04815_gb300 import workloads
+    if case == "i32_add":
+        return workloads.large_i32_add(n)
+    if case == "i32_max":
+        return workloads.large_i32_max(n)
+    return workloads.large_f32_add(n)
+
+
+def _kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1604_04815_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cuh", ".cu", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel_case):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") != _kernel_source_hash():
+            return None
+        return d.get("bytes_per_launch", {}).get(kernel_case)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _reduce_max(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(budget_s=12.0, n=N):
+    """Times the sequential oracle on the step's three arrays (bounded)."""
+    import oracle
+    arrays = [(_inputs(c, n), op, dt) for c, op, dt in CASES]
+    total_bytes, total_t, reps = 0, 0.0, 0
+    while reps < 1 or (total_t < budget_s and reps < 5):
+        for x, op, dt in arrays:
+            t0 = time.perf_counter()
+            oracle.scan(op, dt, x, True)
+            total_t += time.perf_counter() - t0
+            total_bytes += 2 * x.nbytes
+        reps += 1
+    return {"value": total_bytes / total_t / 1e9, "unit": "GB/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{reps} pass(es) of the step's three 2^{n.bit_length()-1}"
+                      f"-element arrays through the sequential C oracle"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    n = N
+    arrays = [(_inputs(c, n), op, dt) for c, op, dt in CASES]
+    # each step: one bounded sample = the three arrays' first 2^26 elements
+    m = 1 << 26
+    samples = [(x[:m].copy(), op, dt) for x, op, dt in arrays]
+    for _ in range(args.warmup):
+        for x, op, dt in samples:
+            oracle.scan(op, dt, x, True)
+    times = []
+    nbytes = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        for x, op, dt in samples:
+            oracle.scan(op, dt, x, True)
+        times.append(time.perf_counter() - t0)
+    nbytes = sum(2 * x.nbytes for x, _, _ in samples)
+    tot = sum(times)
+    value = nbytes * args.steps / tot / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32",
+        "data": "synthetic",
+        "config": {"workload": "single-array inclusive scans, N=2^28: int32 "
+                   "add, int32 max, fp32 add", "sample": "first 2^26 elements "
+                   "of each array per step"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1,
+                         "kind": "oracle",
+                         "sample": "first 2^26 elements of each of the three "
+                                   "2^28 arrays, per step"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU path
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    from paper_1604_04815_gb300 import _lib, build
+
+    if ws > 1:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+    _lib.load()
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    peak, peak_src = _peaks()
+
+    host = {c: _inputs(c, N) for c, _, _ in CASES}
+    xs = {c: torch.from_numpy(host[c]).to(dev) for c in host}
+    ys = {c: torch.empty_like(xs[c]) for c in host}
+    torch.cuda.synchronize()
+    step_bytes = sum(2 * N * ELEM_BYTES[dt] for _, _, dt in CASES)
+
+    def launch(case, op, dt):
+        st = _lib.lscan_scan(_lib.LSCAN_ADD if op == "add" else _lib.LSCAN_MAX,
+                             _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32,
+                             1, xs[case].data_ptr(), ys[case].data_ptr(), N,
+                             _lib.make_options(config=args.config,
+                                               carry=args.carry), sp)
+        if st != _lib.LSCAN_OK:
+            raise RuntimeError(_lib.strerror(st))
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            for c, op, dt in CASES:
+                launch(c, op, dt)
+    _lib.check(_lib.lscan_stream_status(sp), "warm-up")
+
+    ev = {c: [(torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)] for c, _, _ in CASES}
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index) if rank == 0 else None
+    _barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    launches0 = _lib.lscan_launch_count()
+    with torch.cuda.stream(stream):
+        t_start.record(stream)
+        for k in range(args.steps):
+            for c, op, dt in CASES:
+                ev[c][k][0].record(stream)
+                launch(c, op, dt)
+                ev[c][k][1].record(stream)
+        t_end.record(stream)
+    stream.synchronize()
+    launches = _lib.lscan_launch_count() - launches0
+    torch.cuda.synchronize()
+    _barrier(ws)
+    clk = clocks.stop() if clocks else None
+    _lib.check(_lib.lscan_stream_status(sp), "timed region")
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    elapsed_max = _reduce_max(elapsed, ws)
+    value = step_bytes * args.steps * ws / elapsed_max / 1e9
+
+    per_kernel = {}
+    for c, op, dt in CASES:
+        ms = [a.elapsed_time(b) for a, b in ev[c]]
+        avg = sum(ms) / len(ms) / 1e3
+        per_kernel[c] = {"avg_us": avg * 1e6,
+                         "gbs": 2 * N * ELEM_BYTES[dt] / avg / 1e9}
+    dom = max(per_kernel, key=lambda c: per_kernel[c]["avg_us"])
+    achieved = per_kernel[dom]["gbs"]
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": _traffic_for(dom), "kernel": dom,
+                "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": 2 * N * 4}
+
+    # ---- e2e: pinned host buffers, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        hx = {c: torch.from_numpy(host[c]).pin_memory() for c in host}
+        hy = {c: torch.empty_like(hx[c]).pin_memory() for c in host}
+        torch.cuda.synchronize()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for c, op, dt in CASES:
+                    xs[c].copy_(hx[c], non_blocking=True)
+                    launch(c, op, dt)
+                    hy[c].copy_(ys[c], non_blocking=True)
+        for _ in range(max(1, args.warmup // 2)):
+            e2e_step()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 5))
+        _barrier(ws)
+        e0.record(stream)
+        for _ in range(ksteps):
+            e2e_step()
+        e1.record(stream)
+        stream.synchronize()
+        et = _reduce_max(e0.elapsed_time(e1) / 1e3, ws)
+        ok = all(np.array_equal(hy[c][:1024].numpy(),
+                                ys[c][:1024].cpu().numpy()) for c in host)
+        e2e = {"value": step_bytes * ksteps * ws / et / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": sum(x.nbytes for x in host.values()),
+               "d2h_bytes_per_step": sum(x.nbytes for x in host.values()),
+               "steps": ksteps, "result_check": bool(ok)}
+        del hx, hy
+
+    # ---- batched: one graph-replayed persistent launch vs 4096 launches ----
+    batched = None
+    if not args.no_batched:
+        batched = bench_batched(args, dev, stream, peak)
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "GB/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * elapsed_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32/f32", "data": "synthetic",
+        "config": {"workload": "single-array inclusive scans, N=2^28 each: "
+                   "int32 add (uniform [-2^15,2^15]), int32 max (full int32 "
+                   "range), fp32 add (uniform [0,1), FP64 carry)",
+                   "n": N, "tile_config": args.config or "tuned",
+                   "carry": ["auto", "lookback", "chained"][args.carry],
+                   "l2": "inputs 1 GiB per array > 129 MB L2; no flush",
+                   "parallelism": f"replicas x{ws}"},
+        "hbm_frac_measured": round(value / ws / peak, 4),
+        "geps": round(N * len(CASES) * args.steps * ws / elapsed_max / 1e9, 2),
+        "kernels": {c: {k: round(v, 2) for k, v in d.items()}
+                    for c, d in per_kernel.items()},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "batched": batched,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget, n=N)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def bench_batched(args, dev, stream, peak):
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    from paper_1604_04815_gb300 import _lib, workloads
+    out = {}
+    sp = stream.cuda_stream
+    for dt in ("i32", "f32"):
+        x, off = workloads.batched(dt)
+        total = int(off[-1])
+        xd = torch.from_numpy(x).to(dev)
+        yd = torch.empty_like(xd)
+        od = torch.from_numpy(off).to(dev)
+        g = lscan.Graph.batched(xd, od, yd)
+        reps = max(3, args.steps)
+        for _ in range(3):
+            g.launch(stream)
+        stream.synchronize()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        for _ in range(reps):
+            g.launch(stream)
+        e1.record(stream)
+        stream.synchronize()
+        g.status()
+        tg = e0.elapsed_time(e1) / 1e3 / reps
+        # per-array: one plain launch per segment
+        opcode = _lib.LSCAN_ADD
+        dcode = _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32
+        es = 4
+        starts = off[:-1].tolist()
+        lens = np.diff(off).tolist()
+        xp, yp = xd.data_ptr(), yd.data_ptr()
+
+        def per_array():
+            for a, ln in zip(starts, lens):
+                st = _lib.lscan_inclusive(opcode, dcode, xp + a * es,
+                                          yp + a * es, ln, sp)
+                if st:
+                    raise RuntimeError(_lib.strerror(st))
+        per_array()
+        stream.synchronize()
+        e0.record(stream)
+        per_array()
+        e1.record(stream)
+        stream.synchronize()
+        tp = e0.elapsed_time(e1) / 1e3
+        _lib.check(_lib.lscan_stream_status(sp), "batched")
+        nbytes = 2 * total * es
+        out[dt] = {"segments": len(lens), "elements": total,
+                   "graph_gbs": round(nbytes / tg / 1e9, 1),
+                   "graph_frac_measured": round(nbytes / tg / 1e9 / peak, 4),
+                   "per_array_gbs": round(nbytes / tp / 1e9, 1),
+                   "speedup_vs_per_array": round(tp / tg, 2)}
+        g.close()
+        del xd, yd, od
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lscan", choices=["lscan", "reference"])
+    ap.add_argument("--config", type=int, default=0)
+    ap.add_argument("--carry", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--log2n", type=int, default=28,
+                    help="array size 2^k (28 = the benchmarked workload; "
+                         "smaller only for profiler captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    global N
+    N = 1 << args.log2n
+    ws, rank, local = _dist()
+    if ws > 1 and args.impl != "reference":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    try:
+        if args.impl == "reference":
+            return run_reference(args, ws, rank)
+        return run_gpu(args, ws, rank, local)
+    finally:
+        if ws > 1 and args.impl != "reference":
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())
