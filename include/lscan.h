@@ -105,6 +105,32 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
                         const void *x, void *y, int64_t n,
                         const lscan_options *opts, void *stream);
 
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory when they scan: a memory-pool or
+ * allocator implementation that is itself servicing an allocation, code under
+ * a framework that forbids allocations outside its own pool, or a latency-
+ * critical path where cudaMalloc (which may synchronise or fail) is not
+ * acceptable.  It runs the same single-array scan as lscan_scan with default
+ * options, but its scratch (control block + per-tile status words) is a
+ * fixed array compiled into the library: 1 MiB + 512 B that every GPU which
+ * loads the library keeps until the process exits.
+ *  - n is limited by that array: at most 131072 status words, one per tile
+ *    for int32, max and plain-carry scans, two per tile for FP64-carry and
+ *    compensated float adds; with the default 4096-element tile that is
+ *    2^29 and 2^28 elements.  Larger n returns LSCAN_ERR_INVALID without
+ *    launching.
+ *  - The first call on a device looks up the array and clears it with
+ *    cudaMemsetAsync on `stream`; make that first call before any capture.
+ *  - Every call shares the array (it keeps the last call's contents; each
+ *    launch re-arms it for the next one).  Calls that overlap on the GPU race
+ *    on it: keep them on one stream or synchronise between them.
+ *  - It allocates nothing (no cudaMalloc, cudaFree or allocating library
+ *    call).  Device-side wait timeouts are not reported, but every wait is
+ *    bounded, so a call cannot hang. */
+lscan_status lscan_scan_noalloc(lscan_op op, lscan_dtype dtype, int inclusive,
+                                const void *x, void *y, int64_t n,
+                                void *stream);
+
 /* Batched scan of n_seg independent arrays stored back to back in x (and y):
  * segment s is elements [offsets[s], offsets[s+1]).  d_offsets is a DEVICE
  * array of n_seg+1 int64, non-decreasing, offsets[0] = 0 and

@@ -32,7 +32,7 @@ EXPORTED = [
     "lscan_stream_status", "lscan_reserve", "lscan_shutdown",
     "lscan_strerror", "lscan_version", "lscan_launch_count",
     "lscan_set_wait_limit_ns", "lscan_debug_skip_publish",
-    "lscan_config_info", "lscan_num_configs",
+    "lscan_config_info", "lscan_num_configs", "lscan_scan_noalloc",
 ]
 
 
@@ -74,6 +74,7 @@ def load():
                                     ctypes.POINTER(vp)],
         "lscan_graph_create_batched": [i32, i32, i32, vp, vp, vp, i64, i64,
                                        optp, ctypes.POINTER(vp)],
+        "lscan_scan_noalloc": [i32, i32, i32, vp, vp, i64, vp],
         "lscan_graph_launch": [vp, vp],
         "lscan_graph_status": [vp],
         "lscan_stream_status": [vp],
@@ -135,6 +136,10 @@ def lscan_scan(op, dtype, inclusive, x, y, n, opts=None, stream=None):
     return load().lscan_scan(op, dtype, inclusive, x, y, n,
                              ctypes.byref(opts) if opts is not None else None,
                              stream)
+
+
+def lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream=None):
+    return load().lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream)
 
 
 def lscan_batched(op, dtype, inclusive, x, y, d_offsets, n_seg, n_total,
