@@ -478,7 +478,10 @@ __global__ void __launch_bounds__(Cfg::THREADS)
             if (lane == 0) tile_of[s] = t;
             if (t >= p.n_tiles) {
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&full[s]);
+                if (lane == 0) {
+                    mbar_arrive(&full[s]);
+                    armed_mask &= ~(1u << s);  // this slot's last phase is plain
+                }
                 break;
             }
             const int64_t ts = t * TILE;
@@ -512,10 +515,14 @@ __global__ void __launch_bounds__(Cfg::THREADS)
                                (static_cast<uint32_t>((k / ST) & 1) << s);
                 } else {
                     mbar_arrive(&full[s]);
+                    armed_mask &= ~(1u << s);
                 }
             }
         }
-        // never leave the CTA with a bulk copy still writing its shared memory
+        // Never leave the CTA with a bulk copy still writing its shared memory:
+        // wait for every slot whose LAST phase was a bulk copy.  (A slot re-armed
+        // by a plain arrive afterwards has had its copy consumed already, and its
+        // barrier has moved two phases on, so its old parity must not be tested.)
         if (lane == 0) {
 #pragma unroll
             for (int s = 0; s < ST; ++s)
