@@ -76,9 +76,11 @@ typedef enum {
 
 /* Inter-tile carry protocol (Section 4.3). */
 typedef enum {
-    LSCAN_CARRY_AUTO = 0,     /* the tuned choice (decoupled look-back) */
-    LSCAN_CARRY_LOOKBACK = 1, /* decoupled look-back over a 32-tile window */
-    LSCAN_CARRY_CHAINED = 2   /* wait for the left neighbour only (Alg. 4) */
+    LSCAN_CARRY_AUTO = 0,     /* the measured best (= LSCAN_CARRY_LOOKBACK) */
+    LSCAN_CARRY_LOOKBACK = 1, /* a tile combines its predecessors' published */
+                              /* aggregates until it meets an inclusive prefix */
+    LSCAN_CARRY_CHAINED = 2   /* a tile waits for its left neighbour's */
+                              /* inclusive prefix and passes on its own (Alg. 4) */
 } lscan_carry;
 
 /* Optional per-call settings; pass NULL for all defaults.  Zero in any field

@@ -5,24 +5,25 @@
 
 namespace lscan {
 
-// Tile configurations by input element size.  Variant 0 (G) loads straight
-// from global memory; C1..C3 stream 8, 16 and 32 KiB input tiles through the
-// bulk-copy ring.
+// Tile configurations by input element size: <items/thread, consumer warps,
+// ring stages, output staging buffers, CTAs per SM the registers must fit>.
+// Variant 0 (G) loads straight from global memory; C1..C3 stream 8, 16 and
+// 32 KiB input tiles through the bulk-copy ring.
 template <int ISZ>
 struct Cfgs;
 template <>
 struct Cfgs<4> {
-    using G = TileCfg<8, 8, 4>;
-    using C1 = TileCfg<8, 8, 4>;
-    using C2 = TileCfg<16, 8, 4>;
-    using C3 = TileCfg<16, 16, 3>;
+    using G = TileCfg<8, 8, 4, 1, 3>;
+    using C1 = TileCfg<8, 8, 4, 1, 3>;
+    using C2 = TileCfg<16, 8, 3, 1, 3>;
+    using C3 = TileCfg<16, 16, 3, 1, 1>;
 };
 template <>
 struct Cfgs<2> {
-    using G = TileCfg<16, 8, 4>;
-    using C1 = TileCfg<16, 8, 4>;
-    using C2 = TileCfg<32, 8, 4>;
-    using C3 = TileCfg<32, 16, 2>;
+    using G = TileCfg<16, 8, 4, 1, 3>;
+    using C1 = TileCfg<16, 8, 4, 1, 3>;
+    using C2 = TileCfg<32, 8, 3, 1, 2>;
+    using C3 = TileCfg<32, 16, 3, 1, 1>;
 };
 
 template <class K, class Cfg, int MODE, bool TMA>

@@ -75,6 +75,7 @@ __device__ __forceinline__ T max_keep_left(T a, T b) {
 
 // ----------------------------------------------------------------- kinds
 struct KI32Add {
+    static constexpr bool kTieOrdered = false;
     using In = int32_t;
     using Out = int32_t;
     using Acc = uint32_t;
@@ -95,6 +96,7 @@ struct KI32Add {
 };
 
 struct KI32Max {
+    static constexpr bool kTieOrdered = false;  // equal ints have equal bits
     using In = int32_t;
     using Out = int32_t;
     using Acc = int32_t;
@@ -141,6 +143,7 @@ struct FloatOut<uint16_t> {
 // fp32 / bf16 max (InT = float or uint16_t bf16 bits; Out = In)
 template <class InT>
 struct KFMax {
+    static constexpr bool kTieOrdered = true;  // +0 / -0 compare equal
     using In = InT;
     using Out = InT;
     using Acc = float;
@@ -163,6 +166,7 @@ struct KFMax {
 // float add, plain fp32 carry
 template <class InT, class OutT>
 struct KFAddPlain {
+    static constexpr bool kTieOrdered = false;
     using In = InT;
     using Out = OutT;
     using Acc = float;
@@ -185,6 +189,7 @@ struct KFAddPlain {
 // float add, fp32 in tile, FP64 carry applied as an fp32 (hi, lo) pair
 template <class InT, class OutT>
 struct KFAddF64 {
+    static constexpr bool kTieOrdered = false;
     using In = InT;
     using Out = OutT;
     using Acc = float;
@@ -210,6 +215,7 @@ struct KFAddF64 {
 // float add, compensated (hi, lo) in tile, FP64 carry
 template <class InT, class OutT>
 struct KFAddComp {
+    static constexpr bool kTieOrdered = false;
     using In = InT;
     using Out = OutT;
     using Acc = float2;

@@ -235,7 +235,7 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.wait_limit_ns = g_wait_limit_ns.load();
     p.skip_tile = g_skip_tile.exchange(-1);
     p.inclusive = ls.inclusive ? 1 : 0;
-    p.chained = ls.chained ? 1 : 0;
+    p.carry_mode = ls.carry_mode;
     void *args[] = {&p};
     cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
                                       dim3(e.threads), args, e.smem, cs);
@@ -290,7 +290,7 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     ls->offsets = offsets;
     ls->n_seg = n_seg;
     ls->inclusive = inclusive != 0;
-    ls->chained = carry == LSCAN_CARRY_CHAINED;
+    ls->carry_mode = carry == LSCAN_CARRY_CHAINED ? CARRY_CHAINED : CARRY_LOOKBACK;
     ls->max_ctas = opts ? opts->max_ctas : 0;
     ls->status_words = static_cast<size_t>(n_tiles) * e.car_words;
     return LSCAN_OK;

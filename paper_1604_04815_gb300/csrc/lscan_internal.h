@@ -21,7 +21,7 @@ struct LaunchSpec {
     const int64_t *offsets = nullptr;
     int64_t n_seg = 0;
     bool inclusive = true;
-    bool chained = false;
+    int carry_mode = 0;  // CarryMode
     int max_ctas = 0;
     size_t status_words = 0;
 };

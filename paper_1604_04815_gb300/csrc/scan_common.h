@@ -29,6 +29,12 @@ constexpr uint32_t kEpochMask = 0x3fffffffu;
 
 enum ScanMode : int { MODE_SINGLE = 0, MODE_SEGMENTED = 1, MODE_COUNT = 2 };
 
+// How a tile obtains the prefix of everything before it (Section 4.3).
+enum CarryMode : int {
+    CARRY_LOOKBACK = 0,  // decoupled look-back over predecessors' statuses
+    CARRY_CHAINED = 1    // wait for the left neighbour's inclusive prefix
+};
+
 struct ScanParams {
     const void *x;
     void *y;
@@ -41,7 +47,7 @@ struct ScanParams {
     uint64_t wait_limit_ns;
     int64_t skip_tile;  // fault injection: never publish this tile (-1: off)
     int32_t inclusive;
-    int32_t chained;    // 1: wait for the left neighbour's inclusive only
+    int32_t carry_mode;  // CarryMode
 };
 
 // Per-launch constants the wait loops need.

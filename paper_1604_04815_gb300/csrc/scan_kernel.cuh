@@ -47,13 +47,16 @@
 
 namespace lscan {
 
-template <int ITEMS_, int CWARPS_, int STAGES_>
+template <int ITEMS_, int CWARPS_, int STAGES_, int OSTAGES_ = 1, int MINB_ = 1>
 struct TileCfg {
     static constexpr int ITEMS = ITEMS_;
     static constexpr int CWARPS = CWARPS_;
     static constexpr int STAGES = STAGES_;
+    static constexpr int OSTAGES = OSTAGES_;  // output staging buffers (1 or 2)
+    static constexpr int MINB = MINB_;        // CTAs per SM the registers must fit
     static constexpr int CTHREADS = CWARPS * 32;
-    static constexpr int THREADS = CTHREADS + 32;  // + one producer warp
+    // + producer, reducer and carry warps
+    static constexpr int THREADS = CTHREADS + 96;
     static constexpr int TILE = ITEMS * CTHREADS;
 };
 
@@ -71,17 +74,21 @@ struct Layout {
     using In = typename K::In;
     using Out = typename K::Out;
     static constexpr int kIn = TMA ? Cfg::STAGES * Cfg::TILE * int(sizeof(In)) : 0;
-    static constexpr int kOut = TMA ? 2 * Cfg::TILE * int(sizeof(Out)) : 0;
+    static constexpr int kOut = TMA ? Cfg::OSTAGES * Cfg::TILE * int(sizeof(Out)) : 0;
     static constexpr int kBits =
         MODE == MODE_SEGMENTED ? Cfg::STAGES * Cfg::TILE / 8 : 0;
     static constexpr int off_in = 0;
     static constexpr int off_out = align_up_c(off_in + kIn, 128);
     static constexpr int off_bits = align_up_c(off_out + kOut, 128);
+    // mbarriers full[ST], empty[ST], reduced[ST], carried[ST]
     static constexpr int off_bar = align_up_c(off_bits + kBits, 128);
-    static constexpr int off_tile = off_bar + 16 * Cfg::STAGES;
-    static constexpr int off_wtot = align_up_c(off_tile + 8 * Cfg::STAGES, 16);
-    static constexpr int off_carry = off_wtot + 16 * Cfg::CWARPS;
-    static constexpr int off_abort = off_carry + 16;
+    static constexpr int off_tile = off_bar + 8 * 4 * Cfg::STAGES;  // int64[ST]
+    static constexpr int off_agg = off_tile + 8 * Cfg::STAGES;      // Car[ST]
+    static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[ST]
+    static constexpr int off_flags = off_carry + 8 * Cfg::STAGES;   // u32[ST] x2
+    static constexpr int off_wtot = align_up_c(off_flags + 8 * Cfg::STAGES, 16);
+    // warp totals, double-buffered by tile parity (one barrier per tile)
+    static constexpr int off_abort = off_wtot + 2 * 16 * Cfg::CWARPS;
     static constexpr int bytes = align_up_c(off_abort + 16, 128);
 };
 
@@ -300,32 +307,63 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
 }
 
 // Decoupled look-back, run by one full warp: exclusive prefix of tile t.
+//
+// Inclusive prefixes can only advance as fast as one look-back round trip
+// covers tiles, so each round issues the status loads of kLookbackWindows
+// 32-tile sub-windows at once (lane l of sub-window j reads tile
+// base - 32 j - l) and resolves them nearest-first; only the sub-windows
+// still needed are re-polled.
+constexpr int kLookbackWindows = 2;
+
 template <class K>
 __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
                                     int64_t t, uint32_t ebase, int lane) {
     using Car = typename K::Car;
+    constexpr int P = kLookbackWindows;
     Car excl = K::cident();
-    int64_t base = t - 1;
+    int64_t base = t - 1;  // tile seen by lane 0 of sub-window 0
     uint64_t t0 = 0;
     bool started = false, gave_up = false;
     while (true) {
-        const int64_t idx = base - lane;
-        Car val = K::cident();
-        uint32_t need;
-        uint32_t inc;
-        while (true) {
-            uint32_t st = ST_INCLUSIVE;  // before tile 0: identity, inclusive
-            val = K::cident();
-            if (idx >= 0) st = StatusIO<K>::read(p.status, idx, ebase, val);
-            if (gave_up && st == ST_INVALID) {
-                st = ST_INCLUSIVE;
-                val = K::cident();
+        uint32_t st[P];
+        Car val[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int64_t idx = base - 32 * j - lane;
+            st[j] = ST_INCLUSIVE;  // before tile 0: identity, inclusive
+            val[j] = K::cident();
+            if (idx >= 0) st[j] = StatusIO<K>::read(p.status, idx, ebase, val[j]);
+        }
+        bool done = false;
+        int consumed = 0;  // sub-windows folded into excl this round
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            if (done || consumed != j) continue;
+            uint32_t sj = st[j];
+            Car vj = val[j];
+            if (gave_up && sj == ST_INVALID) {
+                sj = ST_INCLUSIVE;
+                vj = K::cident();
             }
-            inc = __ballot_sync(0xffffffffu, st == ST_INCLUSIVE);
-            const uint32_t bad = __ballot_sync(0xffffffffu, st == ST_INVALID);
+            const uint32_t inc = __ballot_sync(0xffffffffu, sj == ST_INCLUSIVE);
+            const uint32_t bad = __ballot_sync(0xffffffffu, sj == ST_INVALID);
             // lanes 0..(first inclusive lane), or all 32 if none is inclusive
-            need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
-            if ((bad & need) == 0) break;
+            const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
+            if (bad & need) continue;  // not ready: re-poll from here
+            // ordered reduction: higher lanes hold earlier tiles
+            Car agg = ((need >> lane) & 1u) ? vj : K::cident();
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const Car o = shfl_down_any(agg, off);
+                if (lane + off < 32) agg = K::cop(o, agg);
+            }
+            excl = K::cop(shfl_idx_any(agg, 0), excl);
+            consumed = j + 1;
+            if (inc) done = true;
+        }
+        if (done) break;
+        base -= 32 * consumed;
+        if (consumed == 0) {
             if (!started) {
                 t0 = global_timer_ns();
                 started = true;
@@ -339,17 +377,6 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
                 }
             }
         }
-        // ordered reduction: higher lanes hold earlier tiles
-        Car agg = ((need >> lane) & 1u) ? val : K::cident();
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const Car o = shfl_down_any(agg, off);
-            if (lane + off < 32) agg = K::cop(o, agg);
-        }
-        const Car win = shfl_idx_any(agg, 0);
-        excl = K::cop(win, excl);
-        if (inc) break;
-        base -= 32;
     }
     return excl;
 }
@@ -404,9 +431,40 @@ __device__ __forceinline__ int64_t warp_lower_bound(const int64_t *a,
     return r < hi ? r : hi;
 }
 
+// Reduction of a tile in any order: the operators are commutative (float max
+// keeps the first occurrence through the element index).
+template <class K>
+struct TileReduce {
+    using Acc = typename K::Acc;
+    Acc v;
+    int32_t i;
+    __device__ void init() {
+        v = K::ident();
+        i = INT32_MAX;
+    }
+    __device__ void add(Acc x, int32_t idx) {
+        if constexpr (K::kTieOrdered) {
+            if (x > v || (!(v > x) && idx < i)) {
+                v = x;
+                i = idx;
+            }
+        } else {
+            v = K::op(v, x);
+        }
+    }
+    __device__ void warp_all() {
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const Acc ov = shfl_idx_any(v, (threadIdx.x ^ off) & 31);
+            const int32_t oi = __shfl_xor_sync(0xffffffffu, i, off);
+            add(ov, oi);
+        }
+    }
+};
+
 // ------------------------------------------------------------------ kernel
 template <class K, class Cfg, int MODE, bool TMA>
-__global__ void __launch_bounds__(Cfg::THREADS)
+__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     lscan_kernel(const ScanParams p) {
     using In = typename K::In;
     using Out = typename K::Out;
@@ -419,17 +477,24 @@ __global__ void __launch_bounds__(Cfg::THREADS)
     constexpr int CT = Cfg::CTHREADS;
     constexpr int TILE = Cfg::TILE;
     constexpr int ST = Cfg::STAGES;
+    constexpr int OS = Cfg::OSTAGES;
     constexpr bool SEG = MODE == MODE_SEGMENTED;
+    constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
+    static_assert(OS == 1 || OS == 2, "one or two output staging buffers");
 
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::off_bar);
-    uint64_t *empty = full + ST;
+    uint64_t *empty = full + ST;    // slot consumed: consumers, reducer, carry
+    uint64_t *reduced = empty + ST;  // reducer published the tile's status
+    uint64_t *carried = reduced + ST;  // carry warp stored the tile's carry
     volatile int64_t *tile_of = reinterpret_cast<int64_t *>(smem + L::off_tile);
+    Car *agg_s = reinterpret_cast<Car *>(smem + L::off_agg);        // reducer -> carry
+    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // carry -> consumers
+    volatile uint32_t *head_s = reinterpret_cast<uint32_t *>(smem + L::off_flags);
+    volatile uint32_t *stop_s = head_s + ST;
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
-    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
-    volatile uint32_t *stop_s = abort_s + 1;
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
 
     const int tid = threadIdx.x;
@@ -439,11 +504,14 @@ __global__ void __launch_bounds__(Cfg::THREADS)
     if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW);
+            mbar_init(&empty[s], CW + 2);  // consumer warps + reducer + carry
+            mbar_init(&reduced[s], 1);
+            mbar_init(&carried[s], 1);
             tile_of[s] = INT64_MAX;
+            head_s[s] = 0;
+            stop_s[s] = 0;
         }
         *abort_s = 0;
-        *stop_s = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -454,9 +522,9 @@ __global__ void __launch_bounds__(Cfg::THREADS)
     const In *__restrict__ x = static_cast<const In *>(p.x);
     Out *__restrict__ y = static_cast<Out *>(p.y);
 
-    if (warp == CW) {
+    if (warp == W_PROD) {
         // ============================ producer warp ============================
-        uint32_t armed_mask = 0;  // slots that ever got a bulk copy
+        uint32_t armed_mask = 0;  // slots whose last phase was a bulk copy
         uint32_t par_mask = 0;    // parity of each slot's last bulk copy
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
@@ -529,12 +597,112 @@ __global__ void __launch_bounds__(Cfg::THREADS)
                 if (armed_mask & (1u << s))
                     (void)wait_phase(&full[s], (par_mask >> s) & 1u, wc);
         }
+    } else if (warp == W_RED) {
+        // ======================= reducer warp =========================
+        // Publishes each tile's aggregate as soon as its data lands, so the
+        // carry of later tiles never waits on this CTA's consumer queue.
+        for (int64_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % ST);
+            const bool ok = wait_phase(&full[s], static_cast<uint32_t>((k / ST) & 1), wc);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) *abort_s = 1;
+                break;
+            }
+            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
+            if (t >= p.n_tiles) break;
+            const int64_t ts = t * TILE;
+            const int64_t rem = p.n - ts;
+            const int nt = rem < TILE ? static_cast<int>(rem) : TILE;
+            int start = 0;  // reduce elements [start, nt)
+            bool has_head = false;
+            if constexpr (SEG) {
+                // last segment head in the tile: the aggregate restarts there
+                int last = -1;
+                for (int w = lane; w < TILE / 32; w += 32) {
+                    const uint32_t b = bits[s * (TILE / 32) + w];
+                    if (b) last = w * 32 + 31 - __clz(b);
+                }
+                last = __reduce_max_sync(0xffffffffu, last);
+                has_head = last >= 0;
+                start = has_head ? last : 0;
+            }
+            TileReduce<K> r;
+            r.init();
+            if (TMA && nt == TILE) {
+                constexpr int EPC = 16 / int(sizeof(In));
+                const uint8_t *tsm = smem + L::off_in + s * TILE * sizeof(In);
+                for (int c = lane; c < TILE / EPC; c += 32) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(tsm + 16 * c);
+                    const uint4 qa[1] = {q};
+                    In e[EPC];
+                    unpack_chunks<In, EPC, 1>(qa, e);
+#pragma unroll
+                    for (int u = 0; u < EPC; ++u) {
+                        const int idx = c * EPC + u;
+                        if (!SEG || idx >= start) r.add(K::load(e[u]), idx);
+                    }
+                }
+            } else {
+                for (int i = lane; i < nt; i += 32)
+                    if (!SEG || i >= start) r.add(K::load(x[ts + i]), i);
+            }
+            r.warp_all();
+            if (lane == 0) {
+                const Car agg = K::to_car(r.v);
+                if (t != p.skip_tile)
+                    StatusIO<K>::publish(p.status, t,
+                                         ebase | ((t == 0 || has_head) ? ST_INCLUSIVE
+                                                                        : ST_AGGREGATE),
+                                         agg);
+                agg_s[s] = agg;
+                head_s[s] = has_head ? 1u : 0u;
+                mbar_arrive(&reduced[s]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
+    } else if (warp == W_CARRY) {
+        // ========================= carry warp ==========================
+        // Resolves each tile's exclusive prefix (Section 4.3) as soon as the
+        // reducer has published the tile's status, running ahead of the
+        // consumer warps, and publishes the tile's inclusive prefix.
+        for (int64_t k = 0;; ++k) {
+            const int s = static_cast<int>(k % ST);
+            const uint32_t par = static_cast<uint32_t>((k / ST) & 1);
+            const bool okf = wait_phase(&full[s], par, wc);
+            if (!__all_sync(0xffffffffu, okf)) {
+                if (lane == 0) *abort_s = 1;
+                break;
+            }
+            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
+            if (t >= p.n_tiles) break;
+            const bool okr = wait_phase(&reduced[s], par, wc);
+            if (!__all_sync(0xffffffffu, okr) && lane == 0) *abort_s = 1;
+            const bool has_head = SEG && head_s[s] != 0u;
+            const bool head0 = SEG && ((bits[s * (TILE / 32)] & 1u) != 0u);
+            Car excl = K::cident();
+            if (t > 0 && !head0)
+                excl = p.carry_mode == CARRY_CHAINED ? chained_wait<K>(p, wc, t, ebase, lane)
+                                                     : lookback<K>(p, wc, t, ebase, lane);
+            if (lane == 0) {
+                // tile 0 and tiles holding a head got theirs from the reducer
+                if (t > 0 && !has_head && t != p.skip_tile)
+                    StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
+                                         K::cop(excl, agg_s[s]));
+                carry_s[s] = K::to_apply(excl);
+                stop_s[s] = *abort_s;  // one snapshot for every consumer warp
+                mbar_arrive(&carried[s]);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+        }
     } else {
         // ============================ consumer warps ===========================
         const int e0 = tid * ITEMS;  // first element of this thread in a tile
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
-            const bool ok = wait_phase(&full[s], static_cast<uint32_t>((k / ST) & 1), wc);
+            const uint32_t par = static_cast<uint32_t>((k / ST) & 1);
+            const bool ok = wait_phase(&full[s], par, wc);
             if (!__all_sync(0xffffffffu, ok) && lane == 0) *abort_s = 1;
             const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
             if (t >= p.n_tiles) break;
@@ -561,9 +729,6 @@ __global__ void __launch_bounds__(Cfg::THREADS)
                 const uint32_t w = bits[s * (TILE / 32) + (e0 >> 5)];
                 hb = (w >> (e0 & 31)) & (ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u));
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
-
             // ---- thread-serial scan ----
 #pragma unroll
             for (int i = 1; i < ITEMS; ++i) {
@@ -590,16 +755,20 @@ __global__ void __launch_bounds__(Cfg::THREADS)
                 lf = 0u;
             }
             // ---- block scan of warp totals (Algorithm 3) ----
+            // One barrier per tile: a warp can be at most one tile ahead of the
+            // slowest (it cannot pass the next barrier before it), so two
+            // buffers keep a fast warp from overwriting totals still being read.
+            WarpTotal<Acc> *wt = wtot + (k & 1) * CW;
             if (lane == 31) {
-                wtot[warp].v = wv;
-                wtot[warp].f = wf;
+                wt[warp].v = wv;
+                wt[warp].f = wf;
             }
             named_bar_sync(1, CT);
             Acc bv = K::ident();
             uint32_t bf = 0u;
             if (lane < CW) {
-                bv = wtot[lane].v;
-                bf = SEG ? wtot[lane].f : 0u;
+                bv = wt[lane].v;
+                bf = SEG ? wt[lane].f : 0u;
             }
 #pragma unroll
             for (int d = 1; d < CW; d <<= 1) {
@@ -610,8 +779,6 @@ __global__ void __launch_bounds__(Cfg::THREADS)
                     bf |= of;
                 }
             }
-            const Acc tile_agg = shfl_idx_any(bv, CW - 1);
-            const uint32_t tile_f = SEG ? __shfl_sync(0xffffffffu, bf, CW - 1) : 0u;
             Acc wev = shfl_idx_any(bv, warp > 0 ? warp - 1 : 0);
             uint32_t wef = SEG ? __shfl_sync(0xffffffffu, bf, warp > 0 ? warp - 1 : 0) : 0u;
             if (warp == 0) {
@@ -620,48 +787,20 @@ __global__ void __launch_bounds__(Cfg::THREADS)
             }
             // thread base = warp offset (+) lane offset
             Acc tbv;
-            uint32_t tbf;
             if (SEG && lf) {
                 tbv = lv;
             } else {
                 tbv = K::op(wev, lv);
             }
-            tbf = SEG ? (wef | lf) : 0u;
+            const uint32_t tbf = SEG ? (wef | lf) : 0u;
 
-            // ---- inter-tile carry (Section 4.3) ----
-            if (warp == 0) {
-                const bool skip = (t == p.skip_tile);
-                const Car agg_c = K::to_car(tile_agg);
-                Car excl = K::cident();
-                const bool head0 = SEG ? ((__shfl_sync(0xffffffffu, hb, 0) & 1u) != 0u) : false;
-                if (t == 0) {
-                    if (lane == 0 && !skip)
-                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE, agg_c);
-                } else if (SEG && tile_f) {
-                    // the prefix after the last head does not depend on earlier tiles
-                    if (lane == 0 && !skip)
-                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE, agg_c);
-                    if (!head0) {
-                        excl = p.chained ? chained_wait<K>(p, wc, t, ebase, lane)
-                                         : lookback<K>(p, wc, t, ebase, lane);
-                    }
-                } else {
-                    if (!p.chained && lane == 0 && !skip)
-                        StatusIO<K>::publish(p.status, t, ebase | ST_AGGREGATE, agg_c);
-                    excl = p.chained ? chained_wait<K>(p, wc, t, ebase, lane)
-                                     : lookback<K>(p, wc, t, ebase, lane);
-                    if (lane == 0 && !skip)
-                        StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
-                                             K::cop(excl, agg_c));
-                }
-                if (lane == 0) {
-                    *carry_s = K::to_apply(excl);
-                    *stop_s = *abort_s;  // one snapshot, read by every warp
-                }
-            }
-            named_bar_sync(1, CT);
-            const CarA cin = *carry_s;
-            const bool stop = *stop_s != 0u;
+            // ---- carry from the carry warp (Section 4.3) ----
+            const bool okc = wait_phase(&carried[s], par, wc);
+            if (!__all_sync(0xffffffffu, okc) && lane == 0) *abort_s = 1;
+            const CarA cin = carry_s[s];
+            const bool stop = stop_s[s] != 0u;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
 
             // ---- apply carry and write y once (Section 4.4) ----
             const CarA B = K::base(cin, tbv);            // carry (+) thread base
@@ -672,32 +811,34 @@ __global__ void __launch_bounds__(Cfg::THREADS)
             for (int i = 0; i < ITEMS; ++i) {
                 Acc pv;
                 bool pf;  // a head at or before the contributing prefix, in thread
-                bool is_ident = false;
                 if (p.inclusive) {
                     pv = v[i];
                     pf = SEG && ((hb & ((2u << i) - 1u)) != 0u);
+                } else if (SEG && ((hb >> i) & 1u)) {
+                    pv = K::ident();  // a segment head's exclusive value
+                    pf = true;
+                } else if (i == 0) {
+                    pv = K::ident();
+                    pf = false;
                 } else {
-                    if (SEG && ((hb >> i) & 1u)) {
-                        is_ident = true;
-                        pv = K::ident();
-                        pf = true;
-                    } else if (i == 0) {
-                        pv = K::ident();
-                        pf = false;
-                    } else {
-                        pv = v[i - 1];
-                        pf = SEG && ((hb & ((1u << i) - 1u)) != 0u);
-                    }
+                    pv = v[i - 1];
+                    pf = SEG && ((hb & ((1u << i) - 1u)) != 0u);
                 }
-                (void)is_ident;
                 const CarA b = pf ? BI : ((SEG && tbf) ? BL : B);
                 o[i] = K::fin(b, pv);
             }
             if (TMA && full_tile) {
                 constexpr int WBYTES = 32 * ITEMS * int(sizeof(Out));
-                uint8_t *region = smem + L::off_out + (k & 1) * (TILE * sizeof(Out)) +
+                uint8_t *region = smem + L::off_out +
+                                  (OS == 2 ? (k & 1) : 0) * (TILE * sizeof(Out)) +
                                   warp * WBYTES;
-                if (lane == 0) bulk_wait_read<1>();
+                if (lane == 0) {
+                    if constexpr (OS == 2) {
+                        bulk_wait_read<1>();
+                    } else {
+                        bulk_wait_read<0>();
+                    }
+                }
                 __syncwarp();
                 sts_blocked<Out, ITEMS>(region, lane, lane, o);
                 fence_proxy_async_smem();
