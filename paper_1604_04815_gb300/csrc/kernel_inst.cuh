@@ -16,14 +16,14 @@ struct Cfgs<4> {
     using G = TileCfg<8, 8, 4, 1, 3>;
     using C1 = TileCfg<8, 8, 4, 1, 3>;
     using C2 = TileCfg<16, 8, 3, 1, 3>;
-    using C3 = TileCfg<16, 16, 3, 1, 1>;
+    using C3 = TileCfg<16, 16, 2, 1, 2>;
 };
 template <>
 struct Cfgs<2> {
     using G = TileCfg<16, 8, 4, 1, 3>;
     using C1 = TileCfg<16, 8, 4, 1, 3>;
     using C2 = TileCfg<32, 8, 3, 1, 2>;
-    using C3 = TileCfg<32, 16, 3, 1, 1>;
+    using C3 = TileCfg<32, 16, 2, 1, 1>;
 };
 
 template <class K, class Cfg, int MODE, bool TMA>
