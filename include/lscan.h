@@ -168,6 +168,67 @@ lscan_status lscan_graph_launch(lscan_graph *g, void *stream);
 lscan_status lscan_graph_status(lscan_graph *g);
 void lscan_graph_destroy(lscan_graph *g);
 
+/* ---------------------------------------------------------------- serving
+ * A continuous-batching scan service on the current device (not in the
+ * paper; the serving pattern of this library).  The server owns ONE device
+ * allocation of hbm_budget_bytes: per-stream scratch plus a pool for request
+ * outputs and client buffers, so nothing is allocated while serving.
+ * Requests wait in a FIFO admission queue until the pool can hold their
+ * output; a scheduler thread keeps n_streams launch slots busy, each running
+ * one persistent launch over every admitted request of one (op, dtype,
+ * inclusive) kind, so kinds overlap on the device and later arrivals join
+ * the next launch.  Times are microseconds on the host's steady clock since
+ * server creation; launch and completion times come from CUDA events. */
+typedef struct lscan_server lscan_server;
+typedef struct lscan_req_stats {
+    double submit_us;  /* submit() call (replay: scheduled arrival) */
+    double admit_us;   /* output allocated from the pool */
+    double launch_us;  /* its batch started on the device */
+    double done_us;    /* its batch finished on the device */
+    void *y;           /* output (server-allocated ones: until release) */
+    int64_t n;
+    int32_t status;          /* lscan_status of the request */
+    int32_t batch_requests;  /* requests in the same launch */
+} lscan_req_stats;
+typedef struct lscan_trace_req {
+    int32_t op, dtype, inclusive, reserved;
+    const void *x;      /* device input */
+    int64_t n;
+    double arrival_us;  /* offset from the start of the replay */
+} lscan_trace_req;
+
+/* NULL on failure (bad arguments, budget below the scratch reserve + 1 MiB,
+ * or the allocation failed). */
+lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams);
+/* Finishes in-flight batches, fails never-admitted requests, frees all. */
+void lscan_server_destroy(lscan_server *srv);
+/* Client buffers from the pool (count against the budget); NOMEM if full. */
+lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr);
+lscan_status lscan_server_free(lscan_server *srv, void *dptr);
+/* x: device input (any element-aligned address; 16-byte aligned inputs and
+ * outputs take the bulk-copy path).  y: device output, or NULL to have the
+ * server allocate it from the pool at admission (reported in the stats and
+ * kept until lscan_server_release).  Returns at once with a ticket. */
+lscan_status lscan_server_submit(lscan_server *srv, lscan_op op,
+                                 lscan_dtype dtype, int inclusive,
+                                 const void *x, void *y, int64_t n,
+                                 uint64_t *ticket);
+/* Blocks until the request finished; returns its status. */
+lscan_status lscan_server_wait(lscan_server *srv, uint64_t ticket,
+                               lscan_req_stats *out);
+/* Non-blocking: LSCAN_ERR_BUSY while the request is still pending. */
+lscan_status lscan_server_poll(lscan_server *srv, uint64_t ticket,
+                               lscan_req_stats *out);
+/* Forgets a finished request and frees a server-allocated output. */
+lscan_status lscan_server_release(lscan_server *srv, uint64_t ticket);
+/* Open-loop load replay: a native thread submits trace[i] at its arrival
+ * time (outputs allocated by the server), completions are collected and
+ * released in completion order; out[i] receives each request's stats and
+ * *wall_us the time from the first arrival to the last completion. */
+lscan_status lscan_server_replay(lscan_server *srv,
+                                 const lscan_trace_req *trace, int64_t n_req,
+                                 lscan_req_stats *out, double *wall_us);
+
 /* Waits for the stream, then returns and clears its latched device error:
  * LSCAN_OK or LSCAN_ERR_TIMEOUT (LSCAN_ERR_CUDA if a CUDA call failed). */
 lscan_status lscan_stream_status(void *stream);

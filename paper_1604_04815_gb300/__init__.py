@@ -161,3 +161,79 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching scan service (lscan_server_* of include/lscan.h).
+
+    submit() returns a ticket at once; wait() blocks until the request's batch
+    finished and returns its stats; output() views a server-allocated output;
+    release() frees it.  Requests with out=None get their output from the
+    server's HBM pool and wait in the admission queue until it fits.
+    """
+
+    def __init__(self, budget_bytes=16 << 30, n_streams=4):
+        lib = _lib.load()
+        self._h = lib.lscan_server_create(int(budget_bytes), int(n_streams))
+        if not self._h:
+            raise LscanError(_lib.LSCAN_ERR_NOMEM, "lscan_server_create")
+
+    def submit(self, x, op="add", inclusive=True, out=None):
+        import ctypes
+        _check_input(x)
+        tk = ctypes.c_uint64()
+        st = _lib.load().lscan_server_submit(
+            self._h, _OPS[op], _DT[x.dtype], int(bool(inclusive)),
+            x.data_ptr(), out.data_ptr() if out is not None else None,
+            x.shape[0], ctypes.byref(tk))
+        _lib.check(st, "lscan_server_submit")
+        return tk.value
+
+    def wait(self, ticket):
+        import ctypes
+        s = _lib.lscan_req_stats()
+        st = _lib.load().lscan_server_wait(self._h, ticket, ctypes.byref(s))
+        _lib.check(st, "lscan_server_wait")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def output(self, stats, op, dtype):
+        """View of a server-allocated output (valid until release)."""
+        return _lib.device_view(stats["y"], stats["n"],
+                                out_dtype_for(op, dtype))
+
+    def release(self, ticket):
+        _lib.check(_lib.load().lscan_server_release(self._h, ticket),
+                   "lscan_server_release")
+
+    def replay(self, trace):
+        """trace: list of (op, dtype(torch), inclusive, x_ptr, n, arrival_us).
+        Returns (list of stats dicts, wall_us)."""
+        import ctypes
+        n = len(trace)
+        arr = (_lib.lscan_trace_req * max(n, 1))()
+        for i, (op, dt, incl, xp, nn, at) in enumerate(trace):
+            arr[i].op = _OPS[op]
+            arr[i].dtype = _DT[dt]
+            arr[i].inclusive = int(bool(incl))
+            arr[i].x = xp
+            arr[i].n = nn
+            arr[i].arrival_us = at
+        out = (_lib.lscan_req_stats * max(n, 1))()
+        wall = ctypes.c_double()
+        st = _lib.load().lscan_server_replay(self._h, arr, n, out,
+                                             ctypes.byref(wall))
+        _lib.check(st, "lscan_server_replay")
+        stats = [{k: getattr(out[i], k) for k, _ in out[i]._fields_}
+                 for i in range(n)]
+        return stats, wall.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().lscan_server_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -33,6 +33,9 @@ EXPORTED = [
     "lscan_strerror", "lscan_version", "lscan_launch_count",
     "lscan_set_wait_limit_ns", "lscan_debug_skip_publish",
     "lscan_config_info", "lscan_num_configs", "lscan_scan_noalloc",
+    "lscan_server_create", "lscan_server_destroy", "lscan_server_alloc",
+    "lscan_server_free", "lscan_server_submit", "lscan_server_wait",
+    "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
 ]
 
 
@@ -41,6 +44,20 @@ class lscan_options(ctypes.Structure):
                 ("carry", ctypes.c_int32), ("config", ctypes.c_int32),
                 ("max_ctas", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 3)]
+
+
+class lscan_req_stats(ctypes.Structure):
+    _fields_ = [("submit_us", ctypes.c_double), ("admit_us", ctypes.c_double),
+                ("launch_us", ctypes.c_double), ("done_us", ctypes.c_double),
+                ("y", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("batch_requests", ctypes.c_int32)]
+
+
+class lscan_trace_req(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("inclusive", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("x", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("arrival_us", ctypes.c_double)]
 
 
 class LscanError(RuntimeError):
@@ -83,11 +100,27 @@ def load():
         "lscan_debug_skip_publish": [i64],
         "lscan_config_info": [ctypes.c_int32, i32] +
                              [ctypes.POINTER(ctypes.c_int32)] * 4,
+        "lscan_server_alloc": [vp, ctypes.c_size_t, ctypes.POINTER(vp)],
+        "lscan_server_free": [vp, vp],
+        "lscan_server_submit": [vp, i32, i32, i32, vp, vp, i64,
+                                ctypes.POINTER(ctypes.c_uint64)],
+        "lscan_server_wait": [vp, ctypes.c_uint64,
+                              ctypes.POINTER(lscan_req_stats)],
+        "lscan_server_poll": [vp, ctypes.c_uint64,
+                              ctypes.POINTER(lscan_req_stats)],
+        "lscan_server_release": [vp, ctypes.c_uint64],
+        "lscan_server_replay": [vp, ctypes.POINTER(lscan_trace_req), i64,
+                                ctypes.POINTER(lscan_req_stats),
+                                ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    lib.lscan_server_create.argtypes = [ctypes.c_size_t, i32]
+    lib.lscan_server_create.restype = vp
+    lib.lscan_server_destroy.argtypes = [vp]
+    lib.lscan_server_destroy.restype = None
     lib.lscan_graph_destroy.argtypes = [vp]
     lib.lscan_graph_destroy.restype = None
     lib.lscan_shutdown.argtypes = []
@@ -189,3 +222,21 @@ def lscan_num_configs():
 
 def lscan_version():
     return load().lscan_version().decode()
+
+
+class _CudaArray:
+    """Zero-copy view of device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {
+            "shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+            "version": 3, "strides": None}
+
+
+def device_view(ptr, n, torch_dtype):
+    """torch tensor aliasing n elements at a device pointer (no copy)."""
+    import torch
+    typestr = {torch.int32: "<i4", torch.float32: "<f4",
+               torch.bfloat16: "<i2"}[torch_dtype]
+    t = torch.as_tensor(_CudaArray(ptr, n, typestr), device="cuda")
+    return t.view(torch.bfloat16) if torch_dtype == torch.bfloat16 else t

@@ -55,6 +55,7 @@ template <class K>
 void fill_kind(int kind) {
     fill_mode<K, MODE_SINGLE>(kind);
     fill_mode<K, MODE_SEGMENTED>(kind);
+    fill_mode<K, MODE_LIST>(kind);
 }
 
 }  // namespace lscan

@@ -217,7 +217,8 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     int bps = 1;
     lscan_status st = kernel_prepare(dev, e, &bps);
     if (st != LSCAN_OK) return st;
-    const int64_t n_tiles = (ls.n + e.tile - 1) / e.tile;
+    const int64_t n_tiles =
+        ls.mode == MODE_LIST ? ls.list_tiles : (ls.n + e.tile - 1) / e.tile;
     int64_t grid = static_cast<int64_t>(bps) * sm_count(dev);
     if (ls.max_ctas > 0 && grid > ls.max_ctas) grid = ls.max_ctas;
     if (grid > n_tiles) grid = n_tiles;
@@ -230,6 +231,7 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.n_tiles = n_tiles;
     p.offsets = ls.offsets;
     p.n_seg = ls.n_seg;
+    p.segs = static_cast<const SegDesc *>(ls.segs);
     p.ctl = buf.ctl;
     p.status = buf.status;
     p.wait_limit_ns = g_wait_limit_ns.load();
@@ -310,6 +312,12 @@ lscan_status run_planned(const LaunchSpec &ls, void *stream) {
 }
 
 std::mutex &api_mutex() { return g_mu; }
+
+int planned_tile(const LaunchSpec &ls) {
+    return g_kernels[ls.kind][ls.mode][ls.variant].tile;
+}
+
+int carry_words(int kind) { return g_kernels[kind][MODE_SINGLE][1].car_words; }
 
 void note_launch() { g_launches.fetch_add(1); }
 

@@ -18,8 +18,10 @@ struct LaunchSpec {
     const void *x = nullptr;
     void *y = nullptr;
     int64_t n = 0;
-    const int64_t *offsets = nullptr;
+    const int64_t *offsets = nullptr;  // SEGMENTED offsets / LIST first tiles
     int64_t n_seg = 0;
+    const void *segs = nullptr;        // LIST: device SegDesc[n_seg]
+    int64_t list_tiles = 0;            // LIST: total tiles over all arrays
     bool inclusive = true;
     int carry_mode = 0;  // CarryMode
     int max_ctas = 0;
@@ -38,6 +40,10 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
 lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
                          cudaStream_t cs);
 lscan_status run_planned(const LaunchSpec &ls, void *stream);
+// tile length of the kernel a plan selected
+int planned_tile(const LaunchSpec &ls);
+// number of 64-bit status words per tile of a kind
+int carry_words(int kind);
 
 // tile configuration the tuning table picks for (kind, mode, n); 1..3
 int tuned_variant(int kind, int mode, int64_t n);

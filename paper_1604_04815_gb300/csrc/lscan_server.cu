@@ -1,0 +1,619 @@
+// lscan_server.cu -- continuous-batching scan service on one GPU.
+//
+// Not in the paper (which times one scan at a time, Section 5): this is the
+// serving pattern built on the same single-pass kernel.
+//
+//  * HBM budget.  At creation the server takes one device allocation of the
+//    whole budget: a pool from which request outputs (and client buffers,
+//    lscan_server_alloc) are carved, plus a small reserve for per-stream
+//    scratch (status words, array descriptors).  No cudaMalloc happens while
+//    serving.
+//  * Admission.  A request whose output the server must allocate waits in a
+//    FIFO queue until the pool can hold it; requests are admitted in arrival
+//    order as earlier ones release their outputs.
+//  * Continuous batching.  A scheduler thread keeps n_streams launch slots.
+//    Whenever a slot is idle it takes the oldest admitted request, gathers
+//    every admitted request of the same (op, dtype, inclusive) up to a tile
+//    budget, and issues ONE persistent MODE_LIST launch over them (each array
+//    keeps its own carry chain).  Different kinds run on different streams
+//    and overlap on the device; requests arriving while batches run are
+//    admitted and launched as slots free up.
+//  * Timing.  A batch's completion is signalled by a host callback queued
+//    behind the kernel; completion and launch times are read from CUDA events
+//    and mapped onto the host clock, so latencies are device-accurate.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/lscan.h"
+#include "kernel_table.h"
+#include "lscan_internal.h"
+#include "scan_common.h"
+
+namespace lscan {
+namespace {
+
+constexpr size_t kPoolAlign = 256;
+constexpr int64_t kMaxBatchTiles = 8192;    // ~128 MiB of 16 KiB tiles
+constexpr int64_t kMaxBatchRequests = 4096;
+
+double now_us(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0)
+        .count();
+}
+
+// First-fit allocator over [0, size) with coalescing.
+class PoolAllocator {
+   public:
+    void init(size_t size) {
+        free_.clear();
+        free_[0] = size;
+        used_ = 0;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + kPoolAlign - 1) / kPoolAlign * kPoolAlign;
+        if (bytes == 0) bytes = kPoolAlign;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes;
+                const size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                sizes_[*off] = bytes;
+                used_ += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    bool release(size_t off) {
+        auto s = sizes_.find(off);
+        if (s == sizes_.end()) return false;
+        size_t bytes = s->second;
+        sizes_.erase(s);
+        used_ -= bytes;
+        size_t start = off;
+        auto nx = free_.lower_bound(start);
+        if (nx != free_.end() && nx->first == start + bytes) {
+            bytes += nx->second;
+            free_.erase(nx);
+        }
+        auto pv = free_.lower_bound(start);
+        if (pv != free_.begin()) {
+            --pv;
+            if (pv->first + pv->second == start) {
+                start = pv->first;
+                bytes += pv->second;
+                free_.erase(pv);
+            }
+        }
+        free_[start] = bytes;
+        return true;
+    }
+    size_t used() const { return used_; }
+
+   private:
+    std::map<size_t, size_t> free_;   // offset -> bytes
+    std::map<size_t, size_t> sizes_;  // allocated offset -> bytes
+    size_t used_ = 0;
+};
+
+struct Request {
+    uint64_t id = 0;
+    int op = 0, dtype = 0, inclusive = 1;
+    const void *x = nullptr;
+    void *y = nullptr;
+    bool y_owned = false;  // output allocated by the server
+    int64_t n = 0;
+    lscan_req_stats st{};
+    bool done = false;
+};
+
+struct Batch {
+    std::vector<Request *> reqs;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    uint32_t *ctl = nullptr;
+    uint64_t *status = nullptr;
+    SegDesc *d_desc = nullptr;
+    int64_t *d_first = nullptr;
+    SegDesc *h_desc = nullptr;   // pinned
+    int64_t *h_first = nullptr;  // pinned
+    uint32_t *h_err = nullptr;   // pinned copy of the batch's device error word
+    Batch *inflight = nullptr;
+    uint64_t launches = 0;
+    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+
+}  // namespace
+}  // namespace lscan
+
+namespace lscan {
+struct CallbackArg;
+}
+using namespace lscan;
+
+struct lscan_server {
+    int device = 0;
+    size_t budget = 0;
+    uint8_t *mem = nullptr;  // the one device allocation
+    uint8_t *pool = nullptr;
+    size_t pool_size = 0;
+    PoolAllocator alloc;
+    std::vector<Slot> slots;
+    std::deque<Request *> waiting;   // not admitted yet (output not allocated)
+    std::deque<Request *> admitted;  // ready to launch
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::mutex mu;
+    std::condition_variable cv_sched, cv_done;
+    std::thread sched;
+    bool stop = false;
+    uint64_t next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+    cudaEvent_t ref_ev = nullptr;
+    double ref_us = 0;
+    std::vector<int> completed_slots;  // filled by host callbacks
+    std::vector<lscan::CallbackArg> cb_args;
+};
+
+namespace lscan {
+struct CallbackArg {
+    lscan_server *srv;
+    int slot;
+};
+namespace {
+
+void CUDART_CB batch_done_cb(void *arg) {
+    CallbackArg *a = static_cast<CallbackArg *>(arg);
+    {
+        std::lock_guard<std::mutex> lk(a->srv->mu);
+        a->srv->completed_slots.push_back(a->slot);
+    }
+    a->srv->cv_sched.notify_one();
+}
+
+int out_dtype_of(int op, int dtype) {
+    return (op == LSCAN_ADD && dtype == LSCAN_BF16) ? LSCAN_F32 : dtype;
+}
+
+bool same_kind(const Request *a, const Request *b) {
+    return a->op == b->op && a->dtype == b->dtype && a->inclusive == b->inclusive;
+}
+
+// Try to admit waiting requests (FIFO) into the pool.  Caller holds mu.
+void admit_locked(lscan_server *srv) {
+    while (!srv->waiting.empty()) {
+        Request *r = srv->waiting.front();
+        size_t off = 0;
+        const size_t bytes = static_cast<size_t>(r->n) * dtype_size(out_dtype_of(r->op, r->dtype));
+        if (!srv->alloc.alloc(bytes, &off)) break;  // head-of-line waits
+        r->y = srv->pool + off;
+        r->y_owned = true;
+        r->st.y = r->y;
+        srv->waiting.pop_front();
+        r->st.admit_us = now_us(srv->t0);
+        srv->admitted.push_back(r);
+    }
+}
+
+double event_us(lscan_server *srv, cudaEvent_t ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, srv->ref_ev, ev) != cudaSuccess) return now_us(srv->t0);
+    return srv->ref_us + 1000.0 * ms;
+}
+
+// Finish a slot's batch.  Caller holds mu.
+void retire_locked(lscan_server *srv, int si) {
+    Slot &sl = srv->slots[si];
+    Batch *b = sl.inflight;
+    if (!b) return;
+    const double t_start = event_us(srv, sl.ev_start);
+    const double t_done = event_us(srv, sl.ev_done);
+    const uint32_t err = *reinterpret_cast<volatile uint32_t *>(sl.h_err);
+    for (Request *r : b->reqs) {
+        r->st.launch_us = t_start;
+        r->st.done_us = t_done;
+        r->st.status = err ? LSCAN_ERR_TIMEOUT : LSCAN_OK;
+        r->st.batch_requests = static_cast<int32_t>(b->reqs.size());
+        r->done = true;
+    }
+    delete b;
+    sl.inflight = nullptr;
+    srv->cv_done.notify_all();
+}
+
+// Launch one batch on an idle slot.  Caller holds mu.
+bool launch_batch_locked(lscan_server *srv, int si) {
+    if (srv->admitted.empty()) return false;
+    Slot &sl = srv->slots[si];
+    Request *head = srv->admitted.front();
+    // plan with the head's kind (dummy disjoint aligned pointers, n = 1)
+    LaunchSpec ls;
+    if (plan_scan(head->op, head->dtype, head->inclusive, reinterpret_cast<void *>(256),
+                  reinterpret_cast<void *>(4096), 1, nullptr, MODE_LIST, nullptr, 0,
+                  &ls) != LSCAN_OK) {
+        head->st.status = LSCAN_ERR_UNSUPPORTED;
+        head->done = true;
+        srv->admitted.pop_front();
+        srv->cv_done.notify_all();
+        return true;
+    }
+    const int tile = planned_tile(ls);
+    Batch *b = new Batch();
+    int64_t tiles = 0;
+    bool aligned = true;
+    for (auto it = srv->admitted.begin(); it != srv->admitted.end();) {
+        Request *r = *it;
+        if (!same_kind(r, head)) {
+            ++it;
+            continue;
+        }
+        const int64_t rt = (r->n + tile - 1) / tile;
+        if (!b->reqs.empty() && (tiles + rt > kMaxBatchTiles ||
+                                 static_cast<int64_t>(b->reqs.size()) >= kMaxBatchRequests))
+            break;
+        sl.h_desc[b->reqs.size()] = SegDesc{r->x, r->y, r->n};
+        sl.h_first[b->reqs.size()] = tiles;
+        tiles += rt;
+        aligned = aligned && (reinterpret_cast<uintptr_t>(r->x) % 16 == 0) &&
+                  (reinterpret_cast<uintptr_t>(r->y) % 16 == 0);
+        b->reqs.push_back(r);
+        it = srv->admitted.erase(it);
+    }
+    const int64_t nseg = static_cast<int64_t>(b->reqs.size());
+    sl.h_first[nseg] = tiles;
+    if (!aligned) ls.variant = 0;
+    ls.mode = MODE_LIST;
+    ls.segs = sl.d_desc;
+    ls.offsets = sl.d_first;
+    ls.n_seg = nseg;
+    ls.list_tiles = tiles;
+    ls.n = 0;
+    for (Request *r : b->reqs) {
+        r->st.launch_us = now_us(srv->t0);
+        ls.n += r->n;
+    }
+    sl.inflight = b;
+    if (tiles == 0) {  // only empty requests
+        cudaEventRecord(sl.ev_start, sl.stream);
+        cudaEventRecord(sl.ev_done, sl.stream);
+    } else {
+        cudaMemcpyAsync(sl.d_desc, sl.h_desc, nseg * sizeof(SegDesc), cudaMemcpyHostToDevice,
+                        sl.stream);
+        cudaMemcpyAsync(sl.d_first, sl.h_first, (nseg + 1) * sizeof(int64_t),
+                        cudaMemcpyHostToDevice, sl.stream);
+        if (++sl.launches >= (1ull << 30) - 1) {  // keep the epoch tag from wrapping
+            cudaMemsetAsync(sl.ctl, 0, CTL_WORDS * sizeof(uint32_t), sl.stream);
+            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * 2 * sizeof(uint64_t), sl.stream);
+            sl.launches = 0;
+        }
+        cudaEventRecord(sl.ev_start, sl.stream);
+        DevBuffers db{sl.ctl, sl.status};
+        const lscan_status st = launch_scan(ls, db, sl.stream);
+        cudaEventRecord(sl.ev_done, sl.stream);
+        if (st != LSCAN_OK)
+            for (Request *r : b->reqs) r->st.status = st;
+    }
+    // the batch's error word travels with it; the host callback then wakes
+    // the scheduler (no blocking CUDA call is ever made under the lock)
+    cudaMemcpyAsync(sl.h_err, sl.ctl + CTL_ERROR, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                    sl.stream);
+    cudaMemsetAsync(sl.ctl + CTL_ERROR, 0, sizeof(uint32_t), sl.stream);
+    cudaLaunchHostFunc(sl.stream, batch_done_cb, &srv->cb_args[si]);
+    return true;
+}
+
+void scheduler_main(lscan_server *srv) {
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (true) {
+        for (int si : srv->completed_slots) retire_locked(srv, si);
+        srv->completed_slots.clear();
+        admit_locked(srv);
+        bool launched = false;
+        for (size_t si = 0; si < srv->slots.size(); ++si)
+            if (!srv->slots[si].inflight && launch_batch_locked(srv, static_cast<int>(si)))
+                launched = true;
+        if (launched) continue;
+        bool busy = false;
+        for (auto &sl : srv->slots) busy = busy || sl.inflight;
+        if (srv->stop && !busy && srv->admitted.empty()) break;
+        srv->cv_sched.wait(lk);
+    }
+}
+
+void release_request_locked(lscan_server *srv, Request *r) {
+    if (r->y_owned) srv->alloc.release(static_cast<uint8_t *>(r->y) - srv->pool);
+    srv->reqs.erase(r->id);
+    delete r;
+}
+
+}  // namespace
+}  // namespace lscan
+
+extern "C" {
+
+lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
+    if (n_streams < 1 || n_streams > 64) return nullptr;
+    lscan_server *srv = new lscan_server();
+    srv->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&srv->device) != cudaSuccess) {
+        delete srv;
+        return nullptr;
+    }
+    auto up = [](size_t b) { return (b + kPoolAlign - 1) / kPoolAlign * kPoolAlign; };
+    const size_t ctl_b = up(CTL_WORDS * sizeof(uint32_t));
+    const size_t st_b = up(kMaxBatchTiles * 2 * sizeof(uint64_t));
+    const size_t desc_b = up(kMaxBatchRequests * sizeof(SegDesc));
+    const size_t first_b = up((kMaxBatchRequests + 1) * sizeof(int64_t));
+    const size_t slot_b = ctl_b + st_b + desc_b + first_b;
+    const size_t reserve = slot_b * n_streams;
+    if (hbm_budget_bytes < reserve + (size_t{1} << 20)) {
+        delete srv;
+        return nullptr;
+    }
+    srv->budget = hbm_budget_bytes;
+    if (cudaMalloc(&srv->mem, hbm_budget_bytes) != cudaSuccess) {
+        delete srv;
+        return nullptr;
+    }
+    cudaMemset(srv->mem, 0, reserve);
+    srv->pool = srv->mem + reserve;
+    srv->pool_size = hbm_budget_bytes - reserve;
+    srv->alloc.init(srv->pool_size);
+    srv->slots.resize(n_streams);
+    srv->cb_args.resize(n_streams);
+    for (int i = 0; i < n_streams; ++i) {
+        Slot &sl = srv->slots[i];
+        uint8_t *base = srv->mem + i * slot_b;
+        sl.ctl = reinterpret_cast<uint32_t *>(base);
+        sl.status = reinterpret_cast<uint64_t *>(base + ctl_b);
+        sl.d_desc = reinterpret_cast<SegDesc *>(base + ctl_b + st_b);
+        sl.d_first = reinterpret_cast<int64_t *>(base + ctl_b + st_b + desc_b);
+        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        cudaMallocHost(&sl.h_desc, kMaxBatchRequests * sizeof(SegDesc));
+        cudaMallocHost(&sl.h_first, (kMaxBatchRequests + 1) * sizeof(int64_t));
+        cudaMallocHost(&sl.h_err, sizeof(uint32_t));
+        *sl.h_err = 0;
+        cudaEventCreate(&sl.ev_start);
+        cudaEventCreate(&sl.ev_done);
+        srv->cb_args[i] = CallbackArg{srv, i};
+    }
+    cudaEventCreate(&srv->ref_ev);
+    cudaEventRecord(srv->ref_ev, srv->slots[0].stream);
+    cudaEventSynchronize(srv->ref_ev);
+    srv->ref_us = now_us(srv->t0);
+    if (cudaGetLastError() != cudaSuccess) {
+        lscan_server_destroy(srv);
+        return nullptr;
+    }
+    srv->sched = std::thread(scheduler_main, srv);
+    return srv;
+}
+
+void lscan_server_destroy(lscan_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        // requests that were never admitted cannot run any more
+        for (Request *r : srv->waiting) {
+            r->st.status = LSCAN_ERR_NOMEM;
+            r->done = true;
+        }
+        srv->waiting.clear();
+    }
+    srv->cv_sched.notify_all();
+    if (srv->sched.joinable()) srv->sched.join();
+    cudaSetDevice(srv->device);
+    for (Slot &sl : srv->slots) {
+        if (sl.stream) {
+            cudaStreamSynchronize(sl.stream);
+            cudaStreamDestroy(sl.stream);
+        }
+        if (sl.h_desc) cudaFreeHost(sl.h_desc);
+        if (sl.h_first) cudaFreeHost(sl.h_first);
+        if (sl.h_err) cudaFreeHost(sl.h_err);
+        if (sl.ev_start) cudaEventDestroy(sl.ev_start);
+        if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+        delete sl.inflight;
+    }
+    if (srv->ref_ev) cudaEventDestroy(srv->ref_ev);
+    for (auto &kv : srv->reqs) delete kv.second;
+    if (srv->mem) cudaFree(srv->mem);
+    delete srv;
+}
+
+lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr) {
+    if (!srv || !dptr) return LSCAN_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    size_t off = 0;
+    if (!srv->alloc.alloc(bytes, &off)) return LSCAN_ERR_NOMEM;
+    *dptr = srv->pool + off;
+    return LSCAN_OK;
+}
+
+lscan_status lscan_server_free(lscan_server *srv, void *dptr) {
+    if (!srv || !dptr) return LSCAN_ERR_INVALID;
+    lscan_status st;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        const uint8_t *p = static_cast<uint8_t *>(dptr);
+        if (p < srv->pool || p >= srv->pool + srv->pool_size) return LSCAN_ERR_INVALID;
+        st = srv->alloc.release(p - srv->pool) ? LSCAN_OK : LSCAN_ERR_INVALID;
+    }
+    srv->cv_sched.notify_one();  // waiting requests may now fit
+    return st;
+}
+
+lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dtype,
+                                 int inclusive, const void *x, void *y, int64_t n,
+                                 uint64_t *ticket) {
+    if (!srv || !ticket || n < 0) return LSCAN_ERR_INVALID;
+    if (op != LSCAN_ADD && op != LSCAN_MAX) return LSCAN_ERR_INVALID;
+    const int isz = dtype_size(dtype);
+    if (isz == 0) return LSCAN_ERR_INVALID;
+    const int osz = dtype_size(out_dtype_of(op, dtype));
+    if (n > 0 && (x == nullptr || reinterpret_cast<uintptr_t>(x) % isz != 0))
+        return LSCAN_ERR_INVALID;
+    if (y && reinterpret_cast<uintptr_t>(y) % osz != 0) return LSCAN_ERR_INVALID;
+    if (y && n > 0) {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(x), a1 = a0 + n * isz;
+        const uintptr_t b0 = reinterpret_cast<uintptr_t>(y), b1 = b0 + n * osz;
+        const bool disjoint = a1 <= b0 || b1 <= a0;
+        if (!disjoint && !(a0 == b0 && isz == osz)) return LSCAN_ERR_INVALID;
+    }
+    Request *r = new Request();
+    r->op = op;
+    r->dtype = dtype;
+    r->inclusive = inclusive ? 1 : 0;
+    r->x = x;
+    r->y = y;
+    r->n = n;
+    r->st.n = n;
+    r->st.y = y;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) {
+            delete r;
+            return LSCAN_ERR_INVALID;
+        }
+        const size_t need = y ? 0 : static_cast<size_t>(n) * osz;
+        if (need > srv->pool_size) {
+            delete r;
+            return LSCAN_ERR_NOMEM;  // can never be admitted
+        }
+        r->id = srv->next_id++;
+        r->st.submit_us = now_us(srv->t0);
+        srv->reqs[r->id] = r;
+        if (y) {
+            r->st.admit_us = r->st.submit_us;
+            srv->admitted.push_back(r);
+        } else {
+            srv->waiting.push_back(r);
+        }
+        *ticket = r->id;
+    }
+    srv->cv_sched.notify_one();
+    return LSCAN_OK;
+}
+
+static lscan_status server_get(lscan_server *srv, uint64_t ticket, lscan_req_stats *out,
+                               bool block) {
+    if (!srv) return LSCAN_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end()) return LSCAN_ERR_INVALID;
+    Request *r = it->second;
+    if (!r->done) {
+        if (!block) return LSCAN_ERR_BUSY;
+        srv->cv_done.wait(lk, [&] { return r->done; });
+    }
+    if (out) *out = r->st;
+    return static_cast<lscan_status>(r->st.status);
+}
+
+lscan_status lscan_server_wait(lscan_server *srv, uint64_t ticket, lscan_req_stats *out) {
+    return server_get(srv, ticket, out, true);
+}
+
+lscan_status lscan_server_poll(lscan_server *srv, uint64_t ticket, lscan_req_stats *out) {
+    return server_get(srv, ticket, out, false);
+}
+
+lscan_status lscan_server_release(lscan_server *srv, uint64_t ticket) {
+    if (!srv) return LSCAN_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        auto it = srv->reqs.find(ticket);
+        if (it == srv->reqs.end()) return LSCAN_ERR_INVALID;
+        if (!it->second->done) return LSCAN_ERR_BUSY;
+        release_request_locked(srv, it->second);
+    }
+    srv->cv_sched.notify_one();
+    return LSCAN_OK;
+}
+
+lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace,
+                                 int64_t n_req, lscan_req_stats *out, double *wall_us) {
+    if (!srv || (n_req > 0 && (!trace || !out))) return LSCAN_ERR_INVALID;
+    std::vector<uint64_t> tickets(n_req, 0);
+    std::vector<char> submitted(n_req, 0);
+    std::atomic<int64_t> n_sub{0};
+    const double base = now_us(srv->t0);
+    std::atomic<int> sub_err{LSCAN_OK};
+    // open-loop submitter: each request enters at its arrival time
+    std::thread submitter([&] {
+        for (int64_t i = 0; i < n_req; ++i) {
+            const double due = base + trace[i].arrival_us;
+            while (now_us(srv->t0) < due) {
+                const double left = due - now_us(srv->t0);
+                if (left > 200) std::this_thread::sleep_for(std::chrono::microseconds(100));
+            }
+            uint64_t tk = 0;
+            const lscan_status st = lscan_server_submit(
+                srv, static_cast<lscan_op>(trace[i].op), static_cast<lscan_dtype>(trace[i].dtype),
+                trace[i].inclusive, trace[i].x, nullptr, trace[i].n, &tk);
+            if (st != LSCAN_OK) {
+                sub_err.store(st);
+                break;
+            }
+            {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                srv->reqs[tk]->st.submit_us = due;  // latency counts from arrival
+                tickets[i] = tk;
+                submitted[i] = 1;
+            }
+            n_sub.fetch_add(1);
+        }
+    });
+    // collector: release outputs in completion order so admission never stalls
+    int64_t collected = 0;
+    std::vector<char> got(n_req, 0);
+    double last_done = base;
+    {
+        std::unique_lock<std::mutex> lk(srv->mu);
+        int64_t scan_from = 0;
+        while (collected < n_req) {
+            bool progress = false;
+            for (int64_t i = scan_from; i < n_req; ++i) {
+                if (got[i] || !submitted[i]) continue;
+                auto it = srv->reqs.find(tickets[i]);
+                if (it == srv->reqs.end() || !it->second->done) continue;
+                out[i] = it->second->st;
+                out[i].y = nullptr;  // released below
+                last_done = std::max(last_done, out[i].done_us);
+                release_request_locked(srv, it->second);
+                got[i] = 1;
+                ++collected;
+                progress = true;
+            }
+            while (scan_from < n_req && got[scan_from]) ++scan_from;
+            if (progress) {
+                srv->cv_sched.notify_one();
+                continue;
+            }
+            if (sub_err.load() != LSCAN_OK && collected == n_sub.load()) break;
+            srv->cv_done.wait_for(lk, std::chrono::milliseconds(2));
+        }
+    }
+    submitter.join();
+    if (wall_us) *wall_us = last_done - base;
+    return static_cast<lscan_status>(sub_err.load());
+}
+
+}  // extern "C"

@@ -27,7 +27,22 @@ enum DevError : uint32_t {
 enum TileState : uint32_t { ST_INVALID = 0, ST_AGGREGATE = 1, ST_INCLUSIVE = 2 };
 constexpr uint32_t kEpochMask = 0x3fffffffu;
 
-enum ScanMode : int { MODE_SINGLE = 0, MODE_SEGMENTED = 1, MODE_COUNT = 2 };
+// MODE_SINGLE: one array.  MODE_SEGMENTED: arrays back to back, delimited by
+// offsets; tiles span segment boundaries.  MODE_LIST: arrays anywhere in
+// memory, given as (x, y, n) descriptors; every array starts a new tile.
+enum ScanMode : int {
+    MODE_SINGLE = 0,
+    MODE_SEGMENTED = 1,
+    MODE_LIST = 2,
+    MODE_COUNT = 3
+};
+
+// One array of a MODE_LIST launch.
+struct SegDesc {
+    const void *x;
+    void *y;
+    int64_t n;
+};
 
 // How a tile obtains the prefix of everything before it (Section 4.3).
 enum CarryMode : int {
@@ -40,8 +55,10 @@ struct ScanParams {
     void *y;
     int64_t n;        // elements
     int64_t n_tiles;  // ceil(n / TILE)
-    const int64_t *offsets;  // MODE_SEGMENTED: n_seg + 1 entries
+    const int64_t *offsets;  // MODE_SEGMENTED: n_seg + 1 element offsets;
+                             // MODE_LIST: n_seg + 1 first-tile indices
     int64_t n_seg;
+    const SegDesc *segs;     // MODE_LIST: n_seg descriptors
     uint32_t *ctl;    // CTL_WORDS uint32
     uint64_t *status; // n_tiles * carry words
     uint64_t wait_limit_ns;

@@ -78,7 +78,7 @@ struct Layout {
     static constexpr int kIn = TMA ? Cfg::STAGES * Cfg::TILE * int(sizeof(In)) : 0;
     static constexpr int kOut = TMA ? Cfg::OSTAGES * Cfg::TILE * int(sizeof(Out)) : 0;
     static constexpr int kBits =
-        MODE == MODE_SEGMENTED ? Cfg::STAGES * Cfg::TILE / 8 : 0;
+        MODE != MODE_SINGLE ? Cfg::STAGES * Cfg::TILE / 8 : 0;
     static constexpr int off_in = 0;
     static constexpr int off_out = align_up_c(off_in + kIn, 128);
     static constexpr int off_bits = align_up_c(off_out + kOut, 128);
@@ -88,7 +88,11 @@ struct Layout {
     static constexpr int off_agg = off_tile + 8 * Cfg::STAGES;      // Car[ST]
     static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[ST]
     static constexpr int off_flags = off_carry + 8 * Cfg::STAGES;   // u32[ST] x2
-    static constexpr int off_wtot = align_up_c(off_flags + 8 * Cfg::STAGES, 16);
+    // per-slot tile descriptor: x and y of the tile's first element, count
+    static constexpr int off_sx = off_flags + 8 * Cfg::STAGES;      // ptr[ST]
+    static constexpr int off_sy = off_sx + 8 * Cfg::STAGES;         // ptr[ST]
+    static constexpr int off_snt = off_sy + 8 * Cfg::STAGES;        // i32[ST]
+    static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
     // warp totals, double-buffered by tile parity (one barrier per tile)
     static constexpr int off_abort = off_wtot + 2 * 16 * Cfg::CWARPS;
     static constexpr int bytes = align_up_c(off_abort + 16, 128);
@@ -480,7 +484,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr int TILE = Cfg::TILE;
     constexpr int ST = Cfg::STAGES;
     constexpr int OS = Cfg::OSTAGES;
-    constexpr bool SEG = MODE == MODE_SEGMENTED;
+    constexpr bool SEG = MODE != MODE_SINGLE;  // segment heads exist
     constexpr int NC = Cfg::NCARRY;
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
@@ -503,6 +507,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
+    const In *volatile *slot_x = reinterpret_cast<const In *volatile *>(smem + L::off_sx);
+    Out *volatile *slot_y = reinterpret_cast<Out *volatile *>(smem + L::off_sy);
+    volatile int32_t *slot_nt = reinterpret_cast<int32_t *>(smem + L::off_snt);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -576,9 +583,42 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 }
                 break;
             }
-            const int64_t ts = t * TILE;
-            const int64_t te = (ts + TILE < p.n) ? ts + TILE : p.n;
-            if constexpr (SEG) {
+            // ---- tile descriptor: where the tile's elements live ----
+            const In *tx;
+            Out *ty;
+            int nt;
+            bool list_head = false;
+            int64_t ts = 0, te = 0;
+            if constexpr (MODE == MODE_LIST) {
+                // array holding tile t: last s with first_tile[s] <= t
+                const int64_t seg =
+                    warp_lower_bound(p.offsets, p.n_seg + 1, t + 1, lane) - 1;
+                const int64_t lt = t - p.offsets[seg];
+                const SegDesc d = p.segs[seg];
+                const int64_t left = d.n - lt * TILE;
+                nt = left < TILE ? static_cast<int>(left) : TILE;
+                tx = static_cast<const In *>(d.x) + lt * TILE;
+                ty = static_cast<Out *>(d.y) + lt * TILE;
+                list_head = lt == 0;
+            } else {
+                ts = t * TILE;
+                te = (ts + TILE < p.n) ? ts + TILE : p.n;
+                nt = static_cast<int>(te - ts);
+                tx = x + ts;
+                ty = y + ts;
+            }
+            if (lane == 0) {
+                slot_x[s] = tx;
+                slot_y[s] = ty;
+                slot_nt[s] = nt;
+            }
+            if constexpr (MODE == MODE_LIST) {
+                uint32_t *bm = bits + s * (TILE / 32);
+                for (int i = lane; i < TILE / 32; i += 32) bm[i] = 0u;
+                __syncwarp();
+                if (lane == 0 && list_head) bm[0] = 1u;  // each array starts a chain
+                __threadfence_block();
+            } else if constexpr (SEG) {
                 uint32_t *bm = bits + s * (TILE / 32);
                 for (int i = lane; i < TILE / 32; i += 32) bm[i] = 0u;
                 __syncwarp();
@@ -596,12 +636,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             }
             __syncwarp();
             if (lane == 0) {
-                const bool full_tile = (te - ts) == TILE;
+                const bool full_tile = nt == TILE;
                 if (TMA && full_tile) {
                     constexpr uint32_t bytes = TILE * sizeof(In);
                     mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), x + ts,
-                             bytes, &full[s]);
+                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bytes,
+                             &full[s]);
                     armed_mask |= 1u << s;
                     par_mask = (par_mask & ~(1u << s)) |
                                (static_cast<uint32_t>((k / ST) & 1) << s);
@@ -634,9 +674,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             }
             const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
             if (t >= p.n_tiles) break;
-            const int64_t ts = t * TILE;
-            const int64_t rem = p.n - ts;
-            const int nt = rem < TILE ? static_cast<int>(rem) : TILE;
+            const In *tx = slot_x[s];
+            const int nt = slot_nt[s];
             int start = 0;  // reduce elements [start, nt)
             bool has_head = false;
             if constexpr (SEG) {
@@ -668,7 +707,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 }
             } else {
                 for (int i = lane; i < nt; i += 32)
-                    if (!SEG || i >= start) r.add(K::load(x[ts + i]), i);
+                    if (!SEG || i >= start) r.add(K::load(tx[i]), i);
             }
             r.warp_all();
             if (lane == 0) {
@@ -733,9 +772,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             if (!__all_sync(0xffffffffu, ok) && lane == 0) *abort_s = 1;
             const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
             if (t >= p.n_tiles) break;
-            const int64_t ts = t * TILE;
-            const int64_t rem = p.n - ts;
-            const int nt = rem < TILE ? static_cast<int>(rem) : TILE;
+            const In *tx = slot_x[s];
+            Out *ty = slot_y[s];
+            const int nt = slot_nt[s];
             const bool full_tile = nt == TILE;
 
             // ---- load (Section 4.1 step 1) ----
@@ -749,7 +788,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             } else {
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i)
-                    v[i] = (e0 + i < nt) ? K::load(x[ts + e0 + i]) : K::ident();
+                    v[i] = (e0 + i < nt) ? K::load(tx[e0 + i]) : K::ident();
             }
             uint32_t hb = 0;  // head bits of my ITEMS elements
             if constexpr (SEG) {
@@ -871,13 +910,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    bulk_s2g(y + ts + warp * 32 * ITEMS, region, WBYTES);
+                    bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
                     bulk_commit();
                 }
             } else {
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i)
-                    if (e0 + i < nt) y[ts + e0 + i] = o[i];
+                    if (e0 + i < nt) ty[e0 + i] = o[i];
             }
             if (stop) break;
         }

@@ -95,3 +95,16 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no fallback"):
         _lib.load()
+
+
+def test_server_entry_points_reject_null_handles(lib):
+    import ctypes
+    L = lib.load()
+    tk = ctypes.c_uint64()
+    assert L.lscan_server_submit(None, 0, 0, 1, 16, None, 4,
+                                 ctypes.byref(tk)) == lib.LSCAN_ERR_INVALID
+    assert L.lscan_server_wait(None, 1, None) == lib.LSCAN_ERR_INVALID
+    assert L.lscan_server_release(None, 1) == lib.LSCAN_ERR_INVALID
+    assert L.lscan_server_alloc(None, 16, None) == lib.LSCAN_ERR_INVALID
+    assert not L.lscan_server_create(1 << 20, 0)   # bad stream count
+    L.lscan_server_destroy(None)                   # no-op
