@@ -353,6 +353,13 @@ def run_gpu(args, ws, rank, local):
     if not args.no_batched:
         batched = bench_batched(args, dev, stream, peak)
 
+    # ---- serving: Poisson stream through the continuous-batching server ----
+    serving = None
+    if args.serving_full:
+        serving = bench_serving(args, dev, peak, 20000, [0.5, 0.8, 0.95])
+    elif not args.no_serving:
+        serving = bench_serving(args, dev, peak, args.serving_requests, [0.8])
+
     if rank != 0:
         return 0
     line = {
@@ -376,6 +383,7 @@ def run_gpu(args, ws, rank, local):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "batched": batched,
+        "serving": serving,
         "clocks": clk,
     }
     if not args.no_cpu_baseline:
@@ -444,6 +452,91 @@ def bench_batched(args, dev, stream, peak):
     return out
 
 
+SIZE_CLASSES = [(10, 14), (14, 18), (18, 22), (22, 25)]
+
+
+def bench_serving(args, dev, peak, n_req, fracs, seed=6):
+    """Poisson stream of scan requests through lscan_server_replay.
+
+    Request mix: sizes round(2^(10 + 14 U)), dtype int32/fp32/bf16 at
+    50/35/15 %, op add/max 50/50, inclusive; inputs are slices of a device
+    resident synthetic array per dtype, outputs are allocated by the server
+    from its 16 GiB budget.  First a closed-loop run (every request arrives at
+    t = 0) gives the saturation rate; then open-loop Poisson runs at the given
+    fractions of it.  Latency = completion - scheduled arrival."""
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    from paper_1604_04815_gb300 import workloads
+    rng = np.random.default_rng(seed)
+    lake_n = 1 << 25
+    lakes = {
+        torch.int32: torch.from_numpy(rng.integers(
+            -(1 << 15), (1 << 15) + 1, size=lake_n, dtype=np.int32)).to(dev),
+        torch.float32: torch.from_numpy(rng.random(
+            size=lake_n, dtype=np.float32)).to(dev),
+        torch.bfloat16: torch.from_numpy(workloads.f32_to_bf16_bits(
+            rng.random(size=lake_n, dtype=np.float32)).view(np.int16)).to(
+                dev).view(torch.bfloat16),
+    }
+    mix = workloads.serving_requests(n_req, seed=seed)
+    tdt = {"i32": torch.int32, "f32": torch.float32, "bf16": torch.bfloat16}
+    base = []
+    nbytes = 0
+    for r in mix:
+        t = tdt[r["dtype"]]
+        lk = lakes[t]
+        es = lk.element_size()
+        off = int(rng.integers(0, lake_n - r["n"])) // 8 * 8
+        out_es = 4 if (r["op"] == "add" and r["dtype"] == "bf16") else es
+        nbytes += r["n"] * (es + out_es)
+        base.append([r["op"], t, True, lk.data_ptr() + off * es, r["n"]])
+    srv = lscan.Server(budget_bytes=16 << 30, n_streams=4)
+    out = {"requests": n_req, "budget_gib": 16, "n_streams": 4,
+           "mean_elems": float(np.mean([r["n"] for r in mix]))}
+    try:
+        # warm-up (kernels, scratch, pool) on a short closed-loop burst
+        srv.replay([b + [0.0] for b in base[: min(200, n_req)]])
+        stats, wall = srv.replay([b + [0.0] for b in base])
+        sat_rps = n_req / (wall / 1e6)
+        out["saturation"] = {"gbs": round(nbytes / (wall / 1e6) / 1e9, 1),
+                             "frac_measured": round(
+                                 nbytes / (wall / 1e6) / 1e9 / peak, 4),
+                             "req_per_s": round(sat_rps, 1)}
+        runs = []
+        for f in fracs:
+            rate = f * sat_rps
+            gaps = workloads.poisson_gaps(n_req, rate, seed=seed + 10)
+            arr = np.cumsum(gaps) * 1e6
+            arr -= arr[0]
+            stats, wall = srv.replay([b + [float(a)] for b, a in
+                                      zip(base, arr)])
+            lat = np.array([s["done_us"] - s["submit_us"] for s in stats])
+            ns = np.array([s["n"] for s in stats])
+            ok = all(s["status"] == 0 for s in stats)
+            per = {}
+            for lo, hi in SIZE_CLASSES:
+                m = (ns >= (1 << lo)) & (ns < (1 << hi))
+                if m.any():
+                    per[f"2^{lo}-2^{hi}"] = {
+                        "count": int(m.sum()),
+                        "p50_us": round(float(np.percentile(lat[m], 50)), 1),
+                        "p99_us": round(float(np.percentile(lat[m], 99)), 1)}
+            runs.append({"load": f, "offered_req_per_s": round(rate, 1),
+                         "gbs": round(nbytes / (wall / 1e6) / 1e9, 1),
+                         "p50_us": round(float(np.percentile(lat, 50)), 1),
+                         "p99_us": round(float(np.percentile(lat, 99)), 1),
+                         "mean_batch": round(float(np.mean(
+                             [s["batch_requests"] for s in stats])), 1),
+                         "all_ok": ok, "size_classes": per})
+        out["runs"] = runs
+    finally:
+        srv.close()
+        del lakes
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -456,6 +549,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=3000)
+    ap.add_argument("--serving-full", action="store_true",
+                    help="20000 requests per load level, loads 0.5/0.8/0.95")
     ap.add_argument("--log2n", type=int, default=28,
                     help="array size 2^k (28 = the benchmarked workload; "
                          "smaller only for profiler captures)")

@@ -44,7 +44,8 @@ namespace lscan {
 namespace {
 
 constexpr size_t kPoolAlign = 256;
-constexpr int64_t kMaxBatchTiles = 8192;    // ~128 MiB of 16 KiB tiles
+constexpr int64_t kMaxBatchTiles = 16384;   // status words per slot / 2
+constexpr int64_t kMinTile = 2048;          // smallest tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
 
 double now_us(std::chrono::steady_clock::time_point t0) {
@@ -158,15 +159,17 @@ struct lscan_server {
     std::deque<Request *> waiting;   // not admitted yet (output not allocated)
     std::deque<Request *> admitted;  // ready to launch
     std::unordered_map<uint64_t, Request *> reqs;
-    std::mutex mu;
+    std::mutex mu;     // requests, pool, slots
+    std::mutex cb_mu;  // wake-up state only (completed_slots, kick)
     std::condition_variable cv_sched, cv_done;
+    bool kick = false;
     std::thread sched;
     bool stop = false;
     uint64_t next_id = 1;
     std::chrono::steady_clock::time_point t0;
     cudaEvent_t ref_ev = nullptr;
     double ref_us = 0;
-    std::vector<int> completed_slots;  // filled by host callbacks
+    std::vector<int> completed_slots;  // filled by host callbacks (cb_mu)
     std::vector<lscan::CallbackArg> cb_args;
 };
 
@@ -177,10 +180,12 @@ struct CallbackArg {
 };
 namespace {
 
+// Runs on a CUDA-internal thread: it must not call CUDA or wait on a lock
+// that a thread inside the CUDA runtime may hold, so it only touches cb_mu.
 void CUDART_CB batch_done_cb(void *arg) {
     CallbackArg *a = static_cast<CallbackArg *>(arg);
     {
-        std::lock_guard<std::mutex> lk(a->srv->mu);
+        std::lock_guard<std::mutex> lk(a->srv->cb_mu);
         a->srv->completed_slots.push_back(a->slot);
     }
     a->srv->cv_sched.notify_one();
@@ -319,21 +324,36 @@ bool launch_batch_locked(lscan_server *srv, int si) {
 
 void scheduler_main(lscan_server *srv) {
     cudaSetDevice(srv->device);
-    std::unique_lock<std::mutex> lk(srv->mu);
+    std::vector<int> done;
     while (true) {
-        for (int si : srv->completed_slots) retire_locked(srv, si);
-        srv->completed_slots.clear();
+        {
+            // only the wake-up state lives under cb_mu; no CUDA call is ever
+            // made while it is held, so host callbacks can never block a
+            // thread that is inside the CUDA runtime
+            std::unique_lock<std::mutex> lk(srv->cb_mu);
+            srv->cv_sched.wait(lk, [&] { return srv->kick || !srv->completed_slots.empty(); });
+            done.swap(srv->completed_slots);
+            srv->kick = false;
+        }
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (int si : done) retire_locked(srv, si);
+        done.clear();
         admit_locked(srv);
-        bool launched = false;
         for (size_t si = 0; si < srv->slots.size(); ++si)
-            if (!srv->slots[si].inflight && launch_batch_locked(srv, static_cast<int>(si)))
-                launched = true;
-        if (launched) continue;
+            if (!srv->slots[si].inflight) launch_batch_locked(srv, static_cast<int>(si));
         bool busy = false;
         for (auto &sl : srv->slots) busy = busy || sl.inflight;
         if (srv->stop && !busy && srv->admitted.empty()) break;
-        srv->cv_sched.wait(lk);
     }
+}
+
+// Wake the scheduler (never blocks on srv->mu).
+void kick(lscan_server *srv) {
+    {
+        std::lock_guard<std::mutex> lk(srv->cb_mu);
+        srv->kick = true;
+    }
+    srv->cv_sched.notify_one();
 }
 
 void release_request_locked(lscan_server *srv, Request *r) {
@@ -417,7 +437,7 @@ void lscan_server_destroy(lscan_server *srv) {
         }
         srv->waiting.clear();
     }
-    srv->cv_sched.notify_all();
+    kick(srv);
     if (srv->sched.joinable()) srv->sched.join();
     cudaSetDevice(srv->device);
     for (Slot &sl : srv->slots) {
@@ -456,7 +476,7 @@ lscan_status lscan_server_free(lscan_server *srv, void *dptr) {
         if (p < srv->pool || p >= srv->pool + srv->pool_size) return LSCAN_ERR_INVALID;
         st = srv->alloc.release(p - srv->pool) ? LSCAN_OK : LSCAN_ERR_INVALID;
     }
-    srv->cv_sched.notify_one();  // waiting requests may now fit
+    kick(srv);  // waiting requests may now fit
     return st;
 }
 
@@ -493,6 +513,11 @@ lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dty
             return LSCAN_ERR_INVALID;
         }
         const size_t need = y ? 0 : static_cast<size_t>(n) * osz;
+        // one request must fit one launch's status words
+        if ((n + kMinTile - 1) / kMinTile > kMaxBatchTiles) {
+            delete r;
+            return LSCAN_ERR_INVALID;
+        }
         if (need > srv->pool_size) {
             delete r;
             return LSCAN_ERR_NOMEM;  // can never be admitted
@@ -508,7 +533,7 @@ lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dty
         }
         *ticket = r->id;
     }
-    srv->cv_sched.notify_one();
+    kick(srv);
     return LSCAN_OK;
 }
 
@@ -544,7 +569,7 @@ lscan_status lscan_server_release(lscan_server *srv, uint64_t ticket) {
         if (!it->second->done) return LSCAN_ERR_BUSY;
         release_request_locked(srv, it->second);
     }
-    srv->cv_sched.notify_one();
+    kick(srv);
     return LSCAN_OK;
 }
 
@@ -604,7 +629,7 @@ lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace
             }
             while (scan_from < n_req && got[scan_from]) ++scan_from;
             if (progress) {
-                srv->cv_sched.notify_one();
+                kick(srv);
                 continue;
             }
             if (sub_err.load() != LSCAN_OK && collected == n_sub.load()) break;
