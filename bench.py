@@ -263,6 +263,19 @@ def run_gpu(args, ws, rank, local):
         if st != _lib.LSCAN_OK:
             raise RuntimeError(_lib.strerror(st))
 
+    # autotune the tile configuration of each scan on its own buffers
+    tuned = {}
+    if args.config == 0:
+        for c, op, dt in CASES:
+            st, best, ms = _lib.lscan_autotune(
+                _lib.LSCAN_ADD if op == "add" else _lib.LSCAN_MAX,
+                _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32, 1,
+                xs[c].data_ptr(), ys[c].data_ptr(), N,
+                opts=_lib.make_options(carry=args.carry), reps=3, stream=sp)
+            _lib.check(st, "lscan_autotune")
+            info = _lib.lscan_config_info(best, _lib.LSCAN_I32)
+            tuned[c] = {"config": best, "items": info["items"],
+                        "threads": info["threads"], "tile": info["tile"]}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             for c, op, dt in CASES:
@@ -371,7 +384,7 @@ def run_gpu(args, ws, rank, local):
         "config": {"workload": "single-array inclusive scans, N=2^28 each: "
                    "int32 add (uniform [-2^15,2^15]), int32 max (full int32 "
                    "range), fp32 add (uniform [0,1), FP64 carry)",
-                   "n": N, "tile_config": args.config or "tuned",
+                   "n": N, "tile_config": args.config or tuned,
                    "carry": ["auto", "lookback", "chained"][args.carry],
                    "l2": "inputs 1 GiB per array > 129 MB L2; no flush",
                    "parallelism": f"replicas x{ws}"},
@@ -405,6 +418,13 @@ def bench_batched(args, dev, stream, peak):
         xd = torch.from_numpy(x).to(dev)
         yd = torch.empty_like(xd)
         od = torch.from_numpy(off).to(dev)
+        tuned_cfg = None
+        if args.config == 0:
+            st, tuned_cfg, _ = _lib.lscan_autotune(
+                _lib.LSCAN_ADD, _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32,
+                1, xd.data_ptr(), yd.data_ptr(), total, od.data_ptr(),
+                len(off) - 1, reps=3, stream=sp)
+            _lib.check(st, "lscan_autotune (batched)")
         g = lscan.Graph.batched(xd, od, yd)
         reps = max(3, args.steps)
         for _ in range(3):
@@ -442,6 +462,7 @@ def bench_batched(args, dev, stream, peak):
         _lib.check(_lib.lscan_stream_status(sp), "batched")
         nbytes = 2 * total * es
         out[dt] = {"segments": len(lens), "elements": total,
+                   "tuned_config": tuned_cfg,
                    "graph_gbs": round(nbytes / tg / 1e9, 1),
                    "graph_frac_measured": round(nbytes / tg / 1e9 / peak, 4),
                    "per_array_gbs": round(nbytes / tp / 1e9, 1),

@@ -258,6 +258,27 @@ lscan_status lscan_set_wait_limit_ns(uint64_t ns);
  * waits run out and the timeout path is exercised on the host's request. */
 lscan_status lscan_debug_skip_publish(int64_t tile);
 
+/* Autotuner (not in the paper, whose K and T are fixed per dtype, Section
+ * 5.1).  Times every bulk-copy tile configuration (items per thread x CTA
+ * size x ring depth) on the caller's buffers -- a single-array scan, or a
+ * batched one when d_offsets is given -- with `reps` timed launches each on
+ * `stream`, records the fastest for this (op, dtype, precision/output kind,
+ * mode, log2(n) class), and returns it (1-based) and its time in ms.  y is
+ * overwritten with the scan of x.  LSCAN_ERR_UNSUPPORTED if the buffers are
+ * not 16-byte aligned (only the plain-load configuration applies). */
+lscan_status lscan_autotune(lscan_op op, lscan_dtype dtype, int inclusive,
+                            const void *x, void *y, int64_t n,
+                            const int64_t *d_offsets, int64_t n_seg,
+                            const lscan_options *opts, int reps, void *stream,
+                            int32_t *best_config, float *best_ms);
+/* The tuning table as JSON ({"lscan_tune": 1, "entries": [[kind, mode,
+ * size_class, config], ...]}); it is also loaded automatically from
+ * $LSCAN_TUNE_FILE on first use. */
+lscan_status lscan_tune_save(const char *path);
+lscan_status lscan_tune_load(const char *path);
+/* Back to the built-in default (configuration 2 everywhere). */
+lscan_status lscan_tune_reset(void);
+
 /* Describes a tile configuration: writes items per thread, consumer threads
  * per CTA, pipeline stages and tile length L for dtype `dtype`. */
 lscan_status lscan_config_info(int32_t config, lscan_dtype dtype,

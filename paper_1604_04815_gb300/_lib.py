@@ -36,6 +36,8 @@ EXPORTED = [
     "lscan_server_create", "lscan_server_destroy", "lscan_server_alloc",
     "lscan_server_free", "lscan_server_submit", "lscan_server_wait",
     "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
+    "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
+    "lscan_tune_reset",
 ]
 
 
@@ -100,6 +102,12 @@ def load():
         "lscan_debug_skip_publish": [i64],
         "lscan_config_info": [ctypes.c_int32, i32] +
                              [ctypes.POINTER(ctypes.c_int32)] * 4,
+        "lscan_autotune": [i32, i32, i32, vp, vp, i64, vp, i64, optp, i32, vp,
+                           ctypes.POINTER(ctypes.c_int32),
+                           ctypes.POINTER(ctypes.c_float)],
+        "lscan_tune_save": [ctypes.c_char_p],
+        "lscan_tune_load": [ctypes.c_char_p],
+        "lscan_tune_reset": [],
         "lscan_server_alloc": [vp, ctypes.c_size_t, ctypes.POINTER(vp)],
         "lscan_server_free": [vp, vp],
         "lscan_server_submit": [vp, i32, i32, i32, vp, vp, i64,
@@ -218,6 +226,30 @@ def lscan_config_info(config, dtype):
 
 def lscan_num_configs():
     return int(load().lscan_num_configs())
+
+
+def lscan_autotune(op, dtype, inclusive, x, y, n, d_offsets=None, n_seg=0,
+                   opts=None, reps=5, stream=None):
+    """Returns (status, best config, best ms)."""
+    best = ctypes.c_int32()
+    ms = ctypes.c_float()
+    st = load().lscan_autotune(op, dtype, inclusive, x, y, n, d_offsets, n_seg,
+                               ctypes.byref(opts) if opts is not None
+                               else None, reps, stream, ctypes.byref(best),
+                               ctypes.byref(ms))
+    return st, best.value, ms.value
+
+
+def lscan_tune_save(path):
+    return load().lscan_tune_save(str(path).encode())
+
+
+def lscan_tune_load(path):
+    return load().lscan_tune_load(str(path).encode())
+
+
+def lscan_tune_reset():
+    return load().lscan_tune_reset()
 
 
 def lscan_version():

@@ -108,3 +108,25 @@ def test_server_entry_points_reject_null_handles(lib):
     assert L.lscan_server_alloc(None, 16, None) == lib.LSCAN_ERR_INVALID
     assert not L.lscan_server_create(1 << 20, 0)   # bad stream count
     L.lscan_server_destroy(None)                   # no-op
+
+
+def test_tune_table_json_roundtrip(lib, tmp_path):
+    """The tuning table loads/saves without a GPU; malformed files are
+    refused and leave the table unchanged."""
+    p = tmp_path / "t.json"
+    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 3], [4, 1, 20, 1]]}')
+    assert lib.lscan_tune_load(p) == lib.LSCAN_OK
+    out = tmp_path / "o.json"
+    assert lib.lscan_tune_save(out) == lib.LSCAN_OK
+    import json
+    d = json.loads(out.read_text())
+    assert d["lscan_tune"] == 1
+    assert sorted(map(tuple, d["entries"])) == [(0, 0, 28, 3), (4, 1, 20, 1)]
+    bad = tmp_path / "bad.json"
+    bad.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 9]]}')
+    assert lib.lscan_tune_load(bad) == lib.LSCAN_ERR_INVALID
+    assert lib.lscan_tune_load(tmp_path / "missing.json") == lib.LSCAN_ERR_INVALID
+    assert lib.lscan_tune_reset() == lib.LSCAN_OK
+    assert lib.lscan_tune_save(out) == lib.LSCAN_OK
+    assert json.loads(out.read_text())["entries"] == []
+    assert lib.lscan_autotune(0, 0, 1, 16, 32, 0)[0] == lib.LSCAN_ERR_INVALID

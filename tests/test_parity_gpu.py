@@ -335,3 +335,22 @@ def test_torch_front_matches_c_abi():
     lscan.stream_status()
     assert torch.equal(a, b)
     assert a.dtype == torch.float32
+
+
+def test_autotune_picks_a_config_and_stays_correct(tmp_path):
+    """The autotuner times every configuration, records the fastest for this
+    size class, and the tuned launch (config 0) still matches the oracle."""
+    for op, dtype in (("add", "i32"), ("add", "f32")):
+        x = _input(op, dtype, (1 << 22) + 3, seed=2)
+        xd = to_device(x, dtype)
+        y = torch.empty_like(xd)
+        s = torch.cuda.current_stream().cuda_stream
+        st, best, ms = _lib.lscan_autotune(LOP[op], LDT[dtype], 1,
+                                           xd.data_ptr(), y.data_ptr(),
+                                           xd.shape[0], reps=2, stream=s)
+        assert st == _lib.LSCAN_OK and 1 <= best <= 3 and ms > 0
+        assert_matches(op, dtype, x, to_host(y))       # y holds a real scan
+        y2 = run_c_abi(op, dtype, xd, True)             # tuned configuration
+        assert_matches(op, dtype, x, to_host(y2))
+    assert _lib.lscan_tune_save(tmp_path / "t.json") == _lib.LSCAN_OK
+    assert _lib.lscan_tune_reset() == _lib.LSCAN_OK
