@@ -39,6 +39,9 @@ if ROOT not in sys.path:
 N = 1 << 28
 METRIC = ("scan GB/s & % of HBM peak, batched vs per-array; "
           "p50/p99 served latency")
+WORKLOAD = ("single-array inclusive scans, N=2^28 each: int32 add (uniform "
+            "[-2^15,2^15]), int32 max (full int32 range), fp32 add (uniform "
+            "[0,1), FP64 carry)")
 CASES = [  # (name, op, dtype)
     ("i32_add", "add", "i32"),
     ("i32_max", "max", "i32"),
@@ -218,9 +221,8 @@ def run_reference(args, ws, rank):
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32",
         "data": "synthetic",
-        "config": {"workload": "single-array inclusive scans, N=2^28: int32 "
-                   "add, int32 max, fp32 add", "sample": "first 2^26 elements "
-                   "of each array per step"},
+        "config": {"workload": WORKLOAD, "n": N,
+                   "sample": "first 2^26 elements of each array per step"},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1,
                          "kind": "oracle",
                          "sample": "first 2^26 elements of each of the three "
@@ -381,10 +383,7 @@ def run_gpu(args, ws, rank, local):
         "ms_per_step": round(1e3 * elapsed_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32/f32", "data": "synthetic",
-        "config": {"workload": "single-array inclusive scans, N=2^28 each: "
-                   "int32 add (uniform [-2^15,2^15]), int32 max (full int32 "
-                   "range), fp32 add (uniform [0,1), FP64 carry)",
-                   "n": N, "tile_config": args.config or tuned,
+        "config": {"workload": WORKLOAD, "n": N, "tile_config": args.config or tuned,
                    "carry": ["auto", "lookback", "chained"][args.carry],
                    "l2": "inputs 1 GiB per array > 129 MB L2; no flush",
                    "parallelism": f"replicas x{ws}"},
