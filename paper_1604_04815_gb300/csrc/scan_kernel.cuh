@@ -82,20 +82,29 @@ struct Layout {
     static constexpr int off_in = 0;
     static constexpr int off_out = align_up_c(off_in + kIn, 128);
     static constexpr int off_bits = align_up_c(off_out + kOut, 128);
-    // mbarriers full[ST], empty[ST], reduced[ST], carried[ST]
+    // carry hand-off ring (carry warps -> consumers), deeper than the tile ring
+    // so that no input slot waits for a look-back
+    static constexpr int CR = 2 * Cfg::STAGES;
+    // mbarriers full[ST], empty[ST], reduced[ST], carried[CR]
     static constexpr int off_bar = align_up_c(off_bits + kBits, 128);
-    static constexpr int off_tile = off_bar + 8 * 4 * Cfg::STAGES;  // int64[ST]
+    static constexpr int off_tile = off_bar + 8 * (3 * Cfg::STAGES + CR);  // int64[ST]
     static constexpr int off_agg = off_tile + 8 * Cfg::STAGES;      // Car[ST]
-    static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[ST]
-    static constexpr int off_flags = off_carry + 8 * Cfg::STAGES;   // u32[ST] x2
+    static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[CR]
+    static constexpr int off_flags = off_carry + 8 * CR;            // u32 head[ST], stop[CR]
     // per-slot tile descriptor: x and y of the tile's first element, count
-    static constexpr int off_sx = off_flags + 8 * Cfg::STAGES;      // ptr[ST]
+    static constexpr int off_sx = align_up_c(off_flags + 4 * (Cfg::STAGES + CR), 16);  // ptr[ST]
     static constexpr int off_sy = off_sx + 8 * Cfg::STAGES;         // ptr[ST]
     static constexpr int off_snt = off_sy + 8 * Cfg::STAGES;        // i32[ST]
     static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
     // warp totals, double-buffered by tile parity (one barrier per tile)
     static constexpr int off_abort = off_wtot + 2 * 16 * Cfg::CWARPS;
     static constexpr int bytes = align_up_c(off_abort + 16, 128);
+    // every field is naturally aligned (a misaligned 8-byte shared access
+    // faults the launch)
+    static_assert(off_in % 16 == 0 && off_out % 16 == 0 && off_bits % 16 == 0, "ring");
+    static_assert(off_bar % 8 == 0 && off_tile % 8 == 0 && off_agg % 8 == 0, "8-byte");
+    static_assert(off_carry % 8 == 0 && off_sx % 8 == 0 && off_snt % 4 == 0, "8-byte");
+    static_assert(off_wtot % 16 == 0 && off_abort % 4 == 0, "totals");
 };
 
 // --------------------------------------------------- 32-bit word shuffles
@@ -486,6 +495,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr int OS = Cfg::OSTAGES;
     constexpr bool SEG = MODE != MODE_SINGLE;  // segment heads exist
     constexpr int NC = Cfg::NCARRY;
+    constexpr int CR = L::CR;
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS == 1 || OS == 2, "one or two output staging buffers");
@@ -498,12 +508,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::off_bar);
     uint64_t *empty = full + ST;    // slot consumed: consumers, reducer, carry
     uint64_t *reduced = empty + ST;  // reducer published the tile's status
-    uint64_t *carried = reduced + ST;  // carry warp stored the tile's carry
+    uint64_t *carried = reduced + ST;  // carry warp stored the tile's carry [CR]
     volatile int64_t *tile_of = reinterpret_cast<int64_t *>(smem + L::off_tile);
     Car *agg_s = reinterpret_cast<Car *>(smem + L::off_agg);        // reducer -> carry
-    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // carry -> consumers
+    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // carry -> consumers [CR]
     volatile uint32_t *head_s = reinterpret_cast<uint32_t *>(smem + L::off_flags);
-    volatile uint32_t *stop_s = head_s + ST;
+    volatile uint32_t *stop_s = head_s + ST;  // [CR]
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
@@ -520,10 +530,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], CW + 2);  // consumer warps + reducer + its carry warp
             mbar_init(&reduced[s], 1);
-            mbar_init(&carried[s], 1);
             tile_of[s] = INT64_MAX;
             head_s[s] = 0;
-            stop_s[s] = 0;
+        }
+        for (int c = 0; c < CR; ++c) {
+            mbar_init(&carried[c], 1);
+            stop_s[c] = 0;
         }
         *abort_s = 0;
         fence_mbar_init();
@@ -744,8 +756,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             if (t >= p.n_tiles) break;
             const bool okr = wait_phase(&reduced[s], par, wc);
             if (!__all_sync(0xffffffffu, okr) && lane == 0) *abort_s = 1;
+            // take what the look-back needs and free the tile slot at once:
+            // input buffers must not wait for carries
             const bool has_head = SEG && head_s[s] != 0u;
             const bool head0 = SEG && ((bits[s * (TILE / 32)] & 1u) != 0u);
+            const Car agg = agg_s[s];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
             Car excl = K::cident();
             if (t > 0 && !head0)
                 excl = p.carry_mode == CARRY_CHAINED ? chained_wait<K>(p, wc, t, ebase, lane)
@@ -754,13 +771,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 // tile 0 and tiles holding a head got theirs from the reducer
                 if (t > 0 && !has_head && t != p.skip_tile)
                     StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
-                                         K::cop(excl, agg_s[s]));
-                carry_s[s] = K::to_apply(excl);
-                stop_s[s] = *abort_s;  // one snapshot for every consumer warp
-                mbar_arrive(&carried[s]);
+                                         K::cop(excl, agg));
+                const int c = static_cast<int>(k % CR);
+                carry_s[c] = K::to_apply(excl);
+                stop_s[c] = *abort_s;  // one snapshot for every consumer warp
+                mbar_arrive(&carried[c]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
         }
     } else {
         // ============================ consumer warps ===========================
@@ -795,6 +811,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 const uint32_t w = bits[s * (TILE / 32) + (e0 >> 5)];
                 hb = (w >> (e0 & 31)) & (ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u));
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
             // ---- thread-serial scan ----
 #pragma unroll
             for (int i = 1; i < ITEMS; ++i) {
@@ -861,12 +879,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             const uint32_t tbf = SEG ? (wef | lf) : 0u;
 
             // ---- carry from the carry warp (Section 4.3) ----
-            const bool okc = wait_phase(&carried[s], par, wc);
+            const int cslot = static_cast<int>(k % CR);
+            const bool okc = wait_phase(&carried[cslot],
+                                        static_cast<uint32_t>((k / CR) & 1), wc);
             if (!__all_sync(0xffffffffu, okc) && lane == 0) *abort_s = 1;
-            const CarA cin = carry_s[s];
-            const bool stop = stop_s[s] != 0u;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+            const CarA cin = carry_s[cslot];
+            const bool stop = stop_s[cslot] != 0u;
 
             // ---- apply carry and write y once (Section 4.4) ----
             const CarA B = K::base(cin, tbv);            // carry (+) thread base
