@@ -53,7 +53,7 @@ struct TileCfg {
     static constexpr int ITEMS = ITEMS_;
     static constexpr int CWARPS = CWARPS_;
     static constexpr int STAGES = STAGES_;
-    static constexpr int OSTAGES = OSTAGES_;  // output staging buffers (1 or 2)
+    static constexpr int OSTAGES = OSTAGES_;  // output staging buffers (0: direct)
     static constexpr int MINB = MINB_;        // CTAs per SM the registers must fit
     static constexpr int NCARRY = NCARRY_;    // carry warps (ring slots round-robin)
     static constexpr int CTHREADS = CWARPS * 32;
@@ -323,20 +323,50 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
 
 // Decoupled look-back, run by one full warp: exclusive prefix of tile t.
 //
-// Each round loads the status words of kLookbackWindows 32-tile sub-windows
-// (lane l of sub-window j reads tile base - 32 j - l) and resolves them
-// nearest-first; only the sub-windows still needed are re-polled.  Measured
-// on GB300 with aggregates published at data arrival, one sub-window per
-// round is fastest (4.64 TB/s vs 3.36 TB/s with eight, int32 N = 2^28).
+// A round loads the status words of kLookbackWindows 32-tile windows (lane l
+// of window j reads tile base - 32 j - l).  From the ballots alone it finds
+// how far it may go: every window up to the first one that holds an
+// inclusive prefix (cut after that lane) or a not-yet-published tile.  Each
+// lane folds its own tiles of those windows, then one butterfly combines the
+// lanes (depth kLookbackWindows + 5).  The operators are commutative; float
+// max keeps the first occurrence by comparing tile indices on ties.
+// Measured on GB300 with aggregates published at data arrival: one window
+// per round is fastest (int32, 2^28: 5462 GB/s with 1 window, 5290 with 2,
+// 4900 with 4, 4024 with 8); the status words near the frontier are read by
+// every carry warp, and more words per round cost more than the rounds they
+// save.  A two-level variant (cached 32-tile group statuses) measured slower
+// still (3455 GB/s): the groups near the frontier are always fresh.
 constexpr int kLookbackWindows = 1;
+
+template <class K>
+struct CarryFold {
+    using Car = typename K::Car;
+    Car v;
+    int64_t i;  // earliest tile holding v (tie order of float max)
+    __device__ void init() {
+        v = K::cident();
+        i = INT64_MAX;
+    }
+    __device__ void add(Car x, int64_t idx) {
+        if constexpr (K::kTieOrdered) {
+            if (x > v || (!(v > x) && idx < i)) {
+                v = x;
+                i = idx;
+            }
+        } else {
+            v = K::cop(v, x);
+        }
+    }
+};
 
 template <class K>
 __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
                                     int64_t t, uint32_t ebase, int lane) {
     using Car = typename K::Car;
     constexpr int P = kLookbackWindows;
-    Car excl = K::cident();
-    int64_t base = t - 1;  // tile seen by lane 0 of sub-window 0
+    CarryFold<K> excl;
+    excl.init();
+    int64_t base = t - 1;  // tile seen by lane 0 of window 0
     uint64_t t0 = 0;
     bool started = false, gave_up = false;
     while (true) {
@@ -348,52 +378,64 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
             st[j] = ST_INCLUSIVE;  // before tile 0: identity, inclusive
             val[j] = K::cident();
             if (idx >= 0) st[j] = StatusIO<K>::read(p.status, idx, ebase, val[j]);
+            if (gave_up && st[j] == ST_INVALID) {
+                st[j] = ST_INCLUSIVE;
+                val[j] = K::cident();
+            }
         }
-        bool done = false;
-        int consumed = 0;  // sub-windows folded into excl this round
+        // how far this round may go (warp-uniform, from ballots only)
+        int use = 0;             // windows fully or partly consumed
+        uint32_t last_mask = 0;  // lanes consumed in window use - 1
+        bool found = false;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-            if (done || consumed != j) continue;
-            uint32_t sj = st[j];
-            Car vj = val[j];
-            if (gave_up && sj == ST_INVALID) {
-                sj = ST_INCLUSIVE;
-                vj = K::cident();
-            }
-            const uint32_t inc = __ballot_sync(0xffffffffu, sj == ST_INCLUSIVE);
-            const uint32_t bad = __ballot_sync(0xffffffffu, sj == ST_INVALID);
-            // lanes 0..(first inclusive lane), or all 32 if none is inclusive
+            const uint32_t inc = __ballot_sync(0xffffffffu, st[j] == ST_INCLUSIVE);
+            const uint32_t bad = __ballot_sync(0xffffffffu, st[j] == ST_INVALID);
+            if (found || use != j) continue;
             const uint32_t need = inc ? (((inc & (0u - inc)) << 1) - 1u) : 0xffffffffu;
-            if (bad & need) continue;  // not ready: re-poll from here
-            // ordered reduction: higher lanes hold earlier tiles
-            Car agg = ((need >> lane) & 1u) ? vj : K::cident();
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const Car o = shfl_down_any(agg, off);
-                if (lane + off < 32) agg = K::cop(o, agg);
-            }
-            excl = K::cop(shfl_idx_any(agg, 0), excl);
-            consumed = j + 1;
-            if (inc) done = true;
+            if (bad & need) continue;  // window j not ready: stop before it
+            use = j + 1;
+            last_mask = need;
+            found = inc != 0u;
         }
-        if (done) break;
-        base -= 32 * consumed;
-        if (consumed == 0) {
-            if (!started) {
-                t0 = global_timer_ns();
-                started = true;
+        if (use > 0) {
+            CarryFold<K> part;
+            part.init();
+#pragma unroll
+            for (int j = P - 1; j >= 0; --j) {  // earliest tiles first
+                if (j >= use) continue;
+                const bool in = (j < use - 1) || ((last_mask >> lane) & 1u);
+                if (in) part.add(val[j], base - 32 * j - lane);
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) {
+                const Car ov = shfl_idx_any(part.v, lane ^ off);
+                const int64_t oi = __shfl_xor_sync(0xffffffffu, part.i, off);
+                part.add(ov, oi);
+            }
+            // part covers tiles earlier than everything folded into excl so far
+            if constexpr (K::kTieOrdered) {
+                excl.add(part.v, part.i);
             } else {
-                bool over = (global_timer_ns() - t0) > wc.limit_ns ||
-                            launch_gave_up(wc);
-                over = __shfl_sync(0xffffffffu, over, 0);
-                if (over && !gave_up) {
-                    gave_up = true;
-                    if (lane == 0) note_gave_up(wc, DEV_ERR_CARRY_WAIT);
-                }
+                excl.v = K::cop(part.v, excl.v);
+            }
+            if (found) break;
+            base -= 32 * use;
+            continue;  // progress: next round at once
+        }
+        if (!started) {
+            t0 = global_timer_ns();
+            started = true;
+        } else {
+            bool over = (global_timer_ns() - t0) > wc.limit_ns || launch_gave_up(wc);
+            over = __shfl_sync(0xffffffffu, over, 0);
+            if (over && !gave_up) {
+                gave_up = true;
+                if (lane == 0) note_gave_up(wc, DEV_ERR_CARRY_WAIT);
             }
         }
     }
-    return excl;
+    return excl.v;
 }
 
 // Chained hand-off (Algorithm 4): wait for tile t-1's inclusive prefix.
@@ -498,7 +540,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr int CR = L::CR;
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
-    static_assert(OS == 1 || OS == 2, "one or two output staging buffers");
+    static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
     // Each carry warp must see every phase of the slots it waits on (an
     // mbarrier parity wait aliases if a phase is skipped), so carry warp c
     // always takes the same slots: ST must be a multiple of NC.
@@ -911,7 +953,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 const CarA b = pf ? BI : ((SEG && tbf) ? BL : B);
                 o[i] = K::fin(b, pv);
             }
-            if (TMA && full_tile) {
+            if (TMA && full_tile && OS == 0) {
+                // 16-byte stores straight from registers (no staging buffer)
+                constexpr int OB = ITEMS * int(sizeof(Out));
+                uint4 ov[OB / 16];
+                pack_chunks<Out, ITEMS, OB / 16>(o, ov);
+                uint4 *dst = reinterpret_cast<uint4 *>(ty + e0);
+#pragma unroll
+                for (int j = 0; j < OB / 16; ++j) dst[j] = ov[j];
+            } else if (TMA && full_tile) {
                 constexpr int WBYTES = 32 * ITEMS * int(sizeof(Out));
                 uint8_t *region = smem + L::off_out +
                                   (OS == 2 ? (k & 1) : 0) * (TILE * sizeof(Out)) +
