@@ -174,11 +174,15 @@ void lscan_graph_destroy(lscan_graph *g);
  * allocation of hbm_budget_bytes: per-stream scratch plus a pool for request
  * outputs and client buffers, so nothing is allocated while serving.
  * Requests wait in a FIFO admission queue until the pool can hold their
- * output; a scheduler thread keeps n_streams launch slots busy, each running
- * one persistent launch over every admitted request of one (op, dtype,
- * inclusive) kind, so kinds overlap on the device and later arrivals join
- * the next launch.  Times are microseconds on the host's steady clock since
- * server creation; launch and completion times come from CUDA events. */
+ * output; a scheduler thread keeps two launch slots per stream busy (the
+ * second queued behind the first, so the device does not wait for the host
+ * between launches), each running one persistent launch over the admitted
+ * requests of one (op, dtype, inclusive) kind -- up to 65536 tiles -- so
+ * kinds overlap on the device and later arrivals join the next launch.
+ * While batches are in flight the scheduler thread polls their completion
+ * events (it sleeps when the server is idle).  Times are microseconds on the
+ * host's steady clock since server creation; launch and completion times
+ * come from CUDA events. */
 typedef struct lscan_server lscan_server;
 typedef struct lscan_req_stats {
     double submit_us;  /* submit() call (replay: scheduled arrival) */
@@ -202,6 +206,11 @@ typedef struct lscan_trace_req {
 lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams);
 /* Finishes in-flight batches, fails never-admitted requests, frees all. */
 void lscan_server_destroy(lscan_server *srv);
+/* hold != 0: keep admitting and queueing requests but start no new launch
+ * (batches already launched finish); hold == 0: launch what has queued,
+ * batched by kind.  Lets a client gather a burst into few launches.
+ * Destroying a held server still runs everything it admitted. */
+lscan_status lscan_server_hold(lscan_server *srv, int hold);
 /* Client buffers from the pool (count against the budget); NOMEM if full. */
 lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr);
 lscan_status lscan_server_free(lscan_server *srv, void *dptr);
@@ -224,7 +233,9 @@ lscan_status lscan_server_release(lscan_server *srv, uint64_t ticket);
 /* Open-loop load replay: a native thread submits trace[i] at its arrival
  * time (outputs allocated by the server), completions are collected and
  * released in completion order; out[i] receives each request's stats and
- * *wall_us the time from the first arrival to the last completion. */
+ * *wall_us the time from the first arrival to the last completion.  One
+ * replay at a time per server: a second concurrent call returns
+ * LSCAN_ERR_BUSY. */
 lscan_status lscan_server_replay(lscan_server *srv,
                                  const lscan_trace_req *trace, int64_t n_req,
                                  lscan_req_stats *out, double *wall_us);
@@ -250,7 +261,8 @@ uint64_t lscan_launch_count(void);
 
 /* Upper bound, in nanoseconds, on any device-side wait (carry flags, bulk
  * copy barriers).  A wait that runs out sets the stream's error word to
- * LSCAN_ERR_TIMEOUT and the kernel finishes without hanging.  Default 1 s. */
+ * LSCAN_ERR_TIMEOUT and the kernel finishes without hanging.  Default 1 s;
+ * limits below 20 us act as 20 us (waits check the limit only after that). */
 lscan_status lscan_set_wait_limit_ns(uint64_t ns);
 
 /* Fault injection for tests: the next launch on any stream skips publishing

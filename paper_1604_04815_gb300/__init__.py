@@ -201,6 +201,11 @@ class Server:
         return _lib.device_view(stats["y"], stats["n"],
                                 out_dtype_for(op, dtype))
 
+    def hold(self, on=True):
+        """Queue requests without launching (on) / launch what queued (off)."""
+        _lib.check(_lib.load().lscan_server_hold(self._h, int(bool(on))),
+                   "lscan_server_hold")
+
     def release(self, ticket):
         _lib.check(_lib.load().lscan_server_release(self._h, ticket),
                    "lscan_server_release")

@@ -36,6 +36,7 @@ EXPORTED = [
     "lscan_server_create", "lscan_server_destroy", "lscan_server_alloc",
     "lscan_server_free", "lscan_server_submit", "lscan_server_wait",
     "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
+    "lscan_server_hold",
     "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
     "lscan_tune_reset",
 ]
@@ -117,6 +118,7 @@ def load():
         "lscan_server_poll": [vp, ctypes.c_uint64,
                               ctypes.POINTER(lscan_req_stats)],
         "lscan_server_release": [vp, ctypes.c_uint64],
+        "lscan_server_hold": [vp, ctypes.c_int],
         "lscan_server_replay": [vp, ctypes.POINTER(lscan_trace_req), i64,
                                 ctypes.POINTER(lscan_req_stats),
                                 ctypes.POINTER(ctypes.c_double)],

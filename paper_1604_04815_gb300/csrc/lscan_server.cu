@@ -11,16 +11,20 @@
 //  * Admission.  A request whose output the server must allocate waits in a
 //    FIFO queue until the pool can hold it; requests are admitted in arrival
 //    order as earlier ones release their outputs.
-//  * Continuous batching.  A scheduler thread keeps n_streams launch slots.
-//    Whenever a slot is idle it takes the oldest admitted request, gathers
+//  * Continuous batching.  A scheduler thread keeps two launch slots per
+//    stream (the second batch of a stream is queued behind the first, so the
+//    GPU never waits for the host between batches).  Whenever a slot is idle
+//    it takes the oldest admitted request, gathers
 //    every admitted request of the same (op, dtype, inclusive) up to a tile
 //    budget, and issues ONE persistent MODE_LIST launch over them (each array
 //    keeps its own carry chain).  Different kinds run on different streams
 //    and overlap on the device; requests arriving while batches run are
 //    admitted and launched as slots free up.
-//  * Timing.  A batch's completion is signalled by a host callback queued
-//    behind the kernel; completion and launch times are read from CUDA events
-//    and mapped onto the host clock, so latencies are device-accurate.
+//  * Completion.  The scheduler polls each in-flight slot's last event
+//    (cudaEventQuery); nothing host-side sits in the stream, so the batch
+//    queued behind it starts the moment the kernel before it ends.  Launch
+//    and completion times are read from CUDA events and mapped onto the host
+//    clock, so latencies are device-accurate.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +48,8 @@ namespace lscan {
 namespace {
 
 constexpr size_t kPoolAlign = 256;
-constexpr int64_t kMaxBatchTiles = 16384;   // status words per slot / 2
+constexpr int64_t kMaxBatchTiles = 65536;   // ~1 GiB of 16 KiB tiles per launch
+constexpr int kSlotsPerStream = 2;          // a second batch queues behind the first
 constexpr int64_t kMinTile = 2048;          // smallest tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
 
@@ -119,6 +124,7 @@ struct Request {
     int64_t n = 0;
     lscan_req_stats st{};
     bool done = false;
+    int64_t tag = -1;  // index in a replayed trace, -1 otherwise
 };
 
 struct Batch {
@@ -137,15 +143,14 @@ struct Slot {
     uint32_t *h_err = nullptr;   // pinned copy of the batch's device error word
     Batch *inflight = nullptr;
     uint64_t launches = 0;
+    bool owns_stream = false;
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+    cudaEvent_t ev_fin = nullptr;  // after the batch's last operation (no timing)
 };
 
 }  // namespace
 }  // namespace lscan
 
-namespace lscan {
-struct CallbackArg;
-}
 using namespace lscan;
 
 struct lscan_server {
@@ -160,35 +165,27 @@ struct lscan_server {
     std::deque<Request *> admitted;  // ready to launch
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;     // requests, pool, slots
-    std::mutex cb_mu;  // wake-up state only (completed_slots, kick)
+    std::mutex cb_mu;  // wake-up flag only
     std::condition_variable cv_sched, cv_done;
     bool kick = false;
     std::thread sched;
     bool stop = false;
+    bool hold = false;  // admit and queue, launch nothing (mu)
     uint64_t next_id = 1;
     std::chrono::steady_clock::time_point t0;
     cudaEvent_t ref_ev = nullptr;
     double ref_us = 0;
-    std::vector<int> completed_slots;  // filled by host callbacks (cb_mu)
-    std::vector<lscan::CallbackArg> cb_args;
+    bool collecting = false;          // a replay is running (mu)
+    std::vector<Request *> finished;  // replayed requests done, not yet collected (mu)
 };
 
 namespace lscan {
-struct CallbackArg {
-    lscan_server *srv;
-    int slot;
-};
 namespace {
 
-// Runs on a CUDA-internal thread: it must not call CUDA or wait on a lock
-// that a thread inside the CUDA runtime may hold, so it only touches cb_mu.
-void CUDART_CB batch_done_cb(void *arg) {
-    CallbackArg *a = static_cast<CallbackArg *>(arg);
-    {
-        std::lock_guard<std::mutex> lk(a->srv->cb_mu);
-        a->srv->completed_slots.push_back(a->slot);
-    }
-    a->srv->cv_sched.notify_one();
+// Mark a request done.  Caller holds mu.
+void finish_locked(lscan_server *srv, Request *r) {
+    r->done = true;
+    if (srv->collecting && r->tag >= 0) srv->finished.push_back(r);
 }
 
 int out_dtype_of(int op, int dtype) {
@@ -222,7 +219,7 @@ double event_us(lscan_server *srv, cudaEvent_t ev) {
 }
 
 // Finish a slot's batch.  Caller holds mu.
-void retire_locked(lscan_server *srv, int si) {
+void retire_locked(lscan_server *srv, int si, bool cuda_ok) {
     Slot &sl = srv->slots[si];
     Batch *b = sl.inflight;
     if (!b) return;
@@ -232,9 +229,10 @@ void retire_locked(lscan_server *srv, int si) {
     for (Request *r : b->reqs) {
         r->st.launch_us = t_start;
         r->st.done_us = t_done;
-        r->st.status = err ? LSCAN_ERR_TIMEOUT : LSCAN_OK;
+        if (r->st.status == LSCAN_OK)
+            r->st.status = !cuda_ok ? LSCAN_ERR_CUDA : err ? LSCAN_ERR_TIMEOUT : LSCAN_OK;
         r->st.batch_requests = static_cast<int32_t>(b->reqs.size());
-        r->done = true;
+        finish_locked(srv, r);
     }
     delete b;
     sl.inflight = nullptr;
@@ -252,8 +250,8 @@ bool launch_batch_locked(lscan_server *srv, int si) {
                   reinterpret_cast<void *>(4096), 1, nullptr, MODE_LIST, nullptr, 0,
                   &ls) != LSCAN_OK) {
         head->st.status = LSCAN_ERR_UNSUPPORTED;
-        head->done = true;
         srv->admitted.pop_front();
+        finish_locked(srv, head);
         srv->cv_done.notify_all();
         return true;
     }
@@ -313,35 +311,50 @@ bool launch_batch_locked(lscan_server *srv, int si) {
         if (st != LSCAN_OK)
             for (Request *r : b->reqs) r->st.status = st;
     }
-    // the batch's error word travels with it; the host callback then wakes
-    // the scheduler (no blocking CUDA call is ever made under the lock)
+    // the batch's error word travels with it; ev_fin marks the end of all of
+    // it and is what the scheduler polls (no blocking CUDA call is ever made
+    // under the lock)
     cudaMemcpyAsync(sl.h_err, sl.ctl + CTL_ERROR, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                     sl.stream);
     cudaMemsetAsync(sl.ctl + CTL_ERROR, 0, sizeof(uint32_t), sl.stream);
-    cudaLaunchHostFunc(sl.stream, batch_done_cb, &srv->cb_args[si]);
+    cudaEventRecord(sl.ev_fin, sl.stream);
     return true;
 }
 
+// The scheduler sleeps while no batch is in flight; otherwise it polls the
+// in-flight slots' last events (only this thread launches or retires
+// batches, so it reads the slots without the lock) and takes the lock only
+// when a batch has finished or a client has kicked it.
 void scheduler_main(lscan_server *srv) {
     cudaSetDevice(srv->device);
-    std::vector<int> done;
+    std::vector<std::pair<int, bool>> done;  // (slot, CUDA ok)
+    bool busy = false;
     while (true) {
+        bool kicked;
         {
-            // only the wake-up state lives under cb_mu; no CUDA call is ever
-            // made while it is held, so host callbacks can never block a
-            // thread that is inside the CUDA runtime
             std::unique_lock<std::mutex> lk(srv->cb_mu);
-            srv->cv_sched.wait(lk, [&] { return srv->kick || !srv->completed_slots.empty(); });
-            done.swap(srv->completed_slots);
+            if (!busy) srv->cv_sched.wait(lk, [&] { return srv->kick; });
+            kicked = srv->kick;
             srv->kick = false;
         }
-        std::lock_guard<std::mutex> lk(srv->mu);
-        for (int si : done) retire_locked(srv, si);
         done.clear();
+        for (size_t si = 0; si < srv->slots.size(); ++si) {
+            const Slot &sl = srv->slots[si];
+            if (!sl.inflight) continue;
+            const cudaError_t q = cudaEventQuery(sl.ev_fin);
+            if (q != cudaErrorNotReady) done.emplace_back(static_cast<int>(si), q == cudaSuccess);
+        }
+        if (!kicked && done.empty()) {
+            std::this_thread::yield();
+            continue;
+        }
+        std::lock_guard<std::mutex> lk(srv->mu);
+        for (auto &d : done) retire_locked(srv, d.first, d.second);
         admit_locked(srv);
-        for (size_t si = 0; si < srv->slots.size(); ++si)
-            if (!srv->slots[si].inflight) launch_batch_locked(srv, static_cast<int>(si));
-        bool busy = false;
+        if (!srv->hold || srv->stop)
+            for (size_t si = 0; si < srv->slots.size(); ++si)
+                if (!srv->slots[si].inflight) launch_batch_locked(srv, static_cast<int>(si));
+        busy = false;
         for (auto &sl : srv->slots) busy = busy || sl.inflight;
         if (srv->stop && !busy && srv->admitted.empty()) break;
     }
@@ -381,7 +394,7 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     const size_t desc_b = up(kMaxBatchRequests * sizeof(SegDesc));
     const size_t first_b = up((kMaxBatchRequests + 1) * sizeof(int64_t));
     const size_t slot_b = ctl_b + st_b + desc_b + first_b;
-    const size_t reserve = slot_b * n_streams;
+    const size_t reserve = slot_b * n_streams * kSlotsPerStream;
     if (hbm_budget_bytes < reserve + (size_t{1} << 20)) {
         delete srv;
         return nullptr;
@@ -395,23 +408,27 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     srv->pool = srv->mem + reserve;
     srv->pool_size = hbm_budget_bytes - reserve;
     srv->alloc.init(srv->pool_size);
-    srv->slots.resize(n_streams);
-    srv->cb_args.resize(n_streams);
-    for (int i = 0; i < n_streams; ++i) {
+    const int n_slots = n_streams * kSlotsPerStream;
+    srv->slots.resize(n_slots);
+    for (int i = 0; i < n_slots; ++i) {
         Slot &sl = srv->slots[i];
         uint8_t *base = srv->mem + i * slot_b;
         sl.ctl = reinterpret_cast<uint32_t *>(base);
         sl.status = reinterpret_cast<uint64_t *>(base + ctl_b);
         sl.d_desc = reinterpret_cast<SegDesc *>(base + ctl_b + st_b);
         sl.d_first = reinterpret_cast<int64_t *>(base + ctl_b + st_b + desc_b);
-        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (i < n_streams)
+            cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        else
+            sl.stream = srv->slots[i - n_streams].stream;  // shares the stream
+        sl.owns_stream = i < n_streams;
         cudaMallocHost(&sl.h_desc, kMaxBatchRequests * sizeof(SegDesc));
         cudaMallocHost(&sl.h_first, (kMaxBatchRequests + 1) * sizeof(int64_t));
         cudaMallocHost(&sl.h_err, sizeof(uint32_t));
         *sl.h_err = 0;
         cudaEventCreate(&sl.ev_start);
         cudaEventCreate(&sl.ev_done);
-        srv->cb_args[i] = CallbackArg{srv, i};
+        cudaEventCreateWithFlags(&sl.ev_fin, cudaEventDisableTiming);
     }
     cudaEventCreate(&srv->ref_ev);
     cudaEventRecord(srv->ref_ev, srv->slots[0].stream);
@@ -433,7 +450,7 @@ void lscan_server_destroy(lscan_server *srv) {
         // requests that were never admitted cannot run any more
         for (Request *r : srv->waiting) {
             r->st.status = LSCAN_ERR_NOMEM;
-            r->done = true;
+            finish_locked(srv, r);
         }
         srv->waiting.clear();
     }
@@ -441,21 +458,31 @@ void lscan_server_destroy(lscan_server *srv) {
     if (srv->sched.joinable()) srv->sched.join();
     cudaSetDevice(srv->device);
     for (Slot &sl : srv->slots) {
-        if (sl.stream) {
-            cudaStreamSynchronize(sl.stream);
-            cudaStreamDestroy(sl.stream);
-        }
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.h_desc) cudaFreeHost(sl.h_desc);
         if (sl.h_first) cudaFreeHost(sl.h_first);
         if (sl.h_err) cudaFreeHost(sl.h_err);
         if (sl.ev_start) cudaEventDestroy(sl.ev_start);
         if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+        if (sl.ev_fin) cudaEventDestroy(sl.ev_fin);
         delete sl.inflight;
     }
+    for (Slot &sl : srv->slots)
+        if (sl.owns_stream && sl.stream) cudaStreamDestroy(sl.stream);
     if (srv->ref_ev) cudaEventDestroy(srv->ref_ev);
     for (auto &kv : srv->reqs) delete kv.second;
     if (srv->mem) cudaFree(srv->mem);
     delete srv;
+}
+
+lscan_status lscan_server_hold(lscan_server *srv, int hold) {
+    if (!srv) return LSCAN_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->hold = hold != 0;
+    }
+    kick(srv);
+    return LSCAN_OK;
 }
 
 lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr) {
@@ -480,9 +507,14 @@ lscan_status lscan_server_free(lscan_server *srv, void *dptr) {
     return st;
 }
 
-lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dtype,
-                                 int inclusive, const void *x, void *y, int64_t n,
-                                 uint64_t *ticket) {
+}  // extern "C"
+
+// Submission.  A replayed request carries its trace index (tag >= 0) and its
+// scheduled arrival time, both set under the same lock that makes it visible
+// to the scheduler.
+static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtype,
+                                int inclusive, const void *x, void *y, int64_t n,
+                                uint64_t *ticket, int64_t tag, double arrival_us) {
     if (!srv || !ticket || n < 0) return LSCAN_ERR_INVALID;
     if (op != LSCAN_ADD && op != LSCAN_MAX) return LSCAN_ERR_INVALID;
     const int isz = dtype_size(dtype);
@@ -523,7 +555,8 @@ lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dty
             return LSCAN_ERR_NOMEM;  // can never be admitted
         }
         r->id = srv->next_id++;
-        r->st.submit_us = now_us(srv->t0);
+        r->tag = tag;
+        r->st.submit_us = tag >= 0 ? arrival_us : now_us(srv->t0);
         srv->reqs[r->id] = r;
         if (y) {
             r->st.admit_us = r->st.submit_us;
@@ -535,6 +568,14 @@ lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dty
     }
     kick(srv);
     return LSCAN_OK;
+}
+
+extern "C" {
+
+lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dtype,
+                                 int inclusive, const void *x, void *y, int64_t n,
+                                 uint64_t *ticket) {
+    return submit_impl(srv, op, dtype, inclusive, x, y, n, ticket, -1, 0.0);
 }
 
 static lscan_status server_get(lscan_server *srv, uint64_t ticket, lscan_req_stats *out,
@@ -576,8 +617,12 @@ lscan_status lscan_server_release(lscan_server *srv, uint64_t ticket) {
 lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace,
                                  int64_t n_req, lscan_req_stats *out, double *wall_us) {
     if (!srv || (n_req > 0 && (!trace || !out))) return LSCAN_ERR_INVALID;
-    std::vector<uint64_t> tickets(n_req, 0);
-    std::vector<char> submitted(n_req, 0);
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->collecting || srv->stop) return LSCAN_ERR_BUSY;  // one replay at a time
+        srv->collecting = true;
+        srv->finished.clear();
+    }
     std::atomic<int64_t> n_sub{0};
     const double base = now_us(srv->t0);
     std::atomic<int> sub_err{LSCAN_OK};
@@ -590,51 +635,43 @@ lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace
                 if (left > 200) std::this_thread::sleep_for(std::chrono::microseconds(100));
             }
             uint64_t tk = 0;
-            const lscan_status st = lscan_server_submit(
+            const lscan_status st = submit_impl(
                 srv, static_cast<lscan_op>(trace[i].op), static_cast<lscan_dtype>(trace[i].dtype),
-                trace[i].inclusive, trace[i].x, nullptr, trace[i].n, &tk);
+                trace[i].inclusive, trace[i].x, nullptr, trace[i].n, &tk, i, due);
             if (st != LSCAN_OK) {
                 sub_err.store(st);
                 break;
             }
-            {
-                std::lock_guard<std::mutex> lk(srv->mu);
-                srv->reqs[tk]->st.submit_us = due;  // latency counts from arrival
-                tickets[i] = tk;
-                submitted[i] = 1;
-            }
             n_sub.fetch_add(1);
         }
+        kick(srv);  // lets the collector see the end of submission
+        srv->cv_done.notify_all();
     });
     // collector: release outputs in completion order so admission never stalls
     int64_t collected = 0;
-    std::vector<char> got(n_req, 0);
     double last_done = base;
+    std::vector<Request *> fin;
     {
         std::unique_lock<std::mutex> lk(srv->mu);
-        int64_t scan_from = 0;
         while (collected < n_req) {
-            bool progress = false;
-            for (int64_t i = scan_from; i < n_req; ++i) {
-                if (got[i] || !submitted[i]) continue;
-                auto it = srv->reqs.find(tickets[i]);
-                if (it == srv->reqs.end() || !it->second->done) continue;
-                out[i] = it->second->st;
-                out[i].y = nullptr;  // released below
-                last_done = std::max(last_done, out[i].done_us);
-                release_request_locked(srv, it->second);
-                got[i] = 1;
-                ++collected;
-                progress = true;
-            }
-            while (scan_from < n_req && got[scan_from]) ++scan_from;
-            if (progress) {
-                kick(srv);
+            if (srv->finished.empty()) {
+                if (sub_err.load() != LSCAN_OK && collected == n_sub.load()) break;
+                srv->cv_done.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
-            if (sub_err.load() != LSCAN_OK && collected == n_sub.load()) break;
-            srv->cv_done.wait_for(lk, std::chrono::milliseconds(2));
+            fin.swap(srv->finished);
+            for (Request *r : fin) {
+                const int64_t i = r->tag;
+                out[i] = r->st;
+                out[i].y = nullptr;  // released below
+                last_done = std::max(last_done, out[i].done_us);
+                release_request_locked(srv, r);
+                ++collected;
+            }
+            fin.clear();
+            kick(srv);  // freed outputs may admit waiting requests
         }
+        srv->collecting = false;
     }
     submitter.join();
     if (wall_us) *wall_us = last_done - base;

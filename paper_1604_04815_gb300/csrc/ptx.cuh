@@ -38,6 +38,14 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar,
                  : "memory");
 }
 
+// Adds expected transaction bytes without arriving (the arrival comes later).
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(

@@ -40,6 +40,7 @@
 //    tile that contains a head publishes its inclusive status immediately.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 
 #include "kinds.cuh"
 #include "ptx.cuh"
@@ -90,9 +91,10 @@ struct Layout {
     static constexpr int off_tile = off_bar + 8 * (3 * Cfg::STAGES + CR);  // int64[ST]
     static constexpr int off_agg = off_tile + 8 * Cfg::STAGES;      // Car[ST]
     static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[CR]
-    static constexpr int off_flags = off_carry + 8 * CR;            // u32 head[ST], stop[CR]
+    // u32 head[ST], stop[CR], inner[ST]
+    static constexpr int off_flags = off_carry + 8 * CR;
     // per-slot tile descriptor: x and y of the tile's first element, count
-    static constexpr int off_sx = align_up_c(off_flags + 4 * (Cfg::STAGES + CR), 16);  // ptr[ST]
+    static constexpr int off_sx = align_up_c(off_flags + 4 * (2 * Cfg::STAGES + CR), 16);  // ptr[ST]
     static constexpr int off_sy = off_sx + 8 * Cfg::STAGES;         // ptr[ST]
     static constexpr int off_snt = off_sy + 8 * Cfg::STAGES;        // i32[ST]
     static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
@@ -305,6 +307,13 @@ __device__ __forceinline__ bool launch_gave_up(const WaitCtx &w) {
     return *reinterpret_cast<volatile uint32_t *>(w.ctl + CTL_ERR_EPOCH) ==
            w.epoch + 1u;
 }
+// A wait reads the launch-wide give-up word only once it has lasted this
+// long: normal waits end well before, so waiting warps do not all poll one
+// global word, and a launch that gave up elsewhere still ends quickly.
+constexpr uint64_t kGiveUpCheckNs = 20000;
+__device__ __forceinline__ bool wait_over(const WaitCtx &w, uint64_t waited_ns) {
+    return waited_ns > kGiveUpCheckNs && (waited_ns > w.limit_ns || launch_gave_up(w));
+}
 
 // Bounded wait on an mbarrier phase; false (and a device error bit) if the
 // limit ran out.
@@ -313,7 +322,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > w.limit_ns || launch_gave_up(w)) {
+        if (wait_over(w, global_timer_ns() - t0)) {
             note_gave_up(w, DEV_ERR_BARRIER_WAIT);
             return false;
         }
@@ -427,7 +436,7 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
             t0 = global_timer_ns();
             started = true;
         } else {
-            bool over = (global_timer_ns() - t0) > wc.limit_ns || launch_gave_up(wc);
+            bool over = wait_over(wc, global_timer_ns() - t0);
             over = __shfl_sync(0xffffffffu, over, 0);
             if (over && !gave_up) {
                 gave_up = true;
@@ -451,7 +460,7 @@ __device__ typename K::Car chained_wait(const ScanParams &p, const WaitCtx &wc,
             while (true) {
                 st = StatusIO<K>::read(p.status, t - 1, ebase, v);
                 if (st == ST_INCLUSIVE) break;
-                if (global_timer_ns() - t0 > wc.limit_ns || launch_gave_up(wc)) {
+                if (wait_over(wc, global_timer_ns() - t0)) {
                     note_gave_up(wc, DEV_ERR_CARRY_WAIT);
                     v = K::cident();
                     break;
@@ -509,6 +518,17 @@ struct TileReduce {
             v = K::op(v, x);
         }
     }
+    // x comes after every element folded so far (a left fold)
+    __device__ void add_in_order(Acc x, int32_t idx) {
+        if constexpr (K::kTieOrdered) {
+            if (x > v) {
+                v = x;
+                i = idx;
+            }
+        } else {
+            v = K::op(v, x);
+        }
+    }
     __device__ void warp_all() {
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
@@ -556,6 +576,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // carry -> consumers [CR]
     volatile uint32_t *head_s = reinterpret_cast<uint32_t *>(smem + L::off_flags);
     volatile uint32_t *stop_s = head_s + ST;  // [CR]
+    // tile has a segment head after its first element (segmented code needed)
+    volatile uint32_t *inner_s = stop_s + CR;  // [ST]
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
@@ -574,6 +596,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             mbar_init(&reduced[s], 1);
             tile_of[s] = INT64_MAX;
             head_s[s] = 0;
+            inner_s[s] = 0;
         }
         for (int c = 0; c < CR; ++c) {
             mbar_init(&carried[c], 1);
@@ -594,6 +617,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
         // ============================ producer warp ============================
         uint32_t armed_mask = 0;  // slots whose last phase was a bulk copy
         uint32_t par_mask = 0;    // parity of each slot's last bulk copy
+        // A CTA's tickets only increase, so the array (list mode) or the
+        // next segment head (segmented mode) of its next tile lies at or
+        // after the one its previous tile needed: both searches resume here.
+        int64_t cur = 0;
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             if (k >= ST) {
@@ -644,11 +671,31 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             bool list_head = false;
             int64_t ts = 0, te = 0;
             if constexpr (MODE == MODE_LIST) {
-                // array holding tile t: last s with first_tile[s] <= t
-                const int64_t seg =
-                    warp_lower_bound(p.offsets, p.n_seg + 1, t + 1, lane) - 1;
-                const int64_t lt = t - p.offsets[seg];
-                const SegDesc d = p.segs[seg];
+                // array holding tile t: the last a with first_tile[a] <= t.
+                // One round of independent loads probes arrays cur .. cur+31
+                // (their descriptors and the next arrays' first tiles); a
+                // binary search covers longer jumps.
+                const int64_t j = cur + lane;
+                const int64_t fnext = (j + 1 <= p.n_seg) ? p.offsets[j + 1] : INT64_MAX;
+                SegDesc dj{nullptr, nullptr, 0};
+                if (j < p.n_seg) dj = p.segs[j];
+                const uint32_t m = __ballot_sync(0xffffffffu, fnext > t);
+                SegDesc d;
+                if (m) {
+                    const int b = __ffs(m) - 1;
+                    cur += b;
+                    d.x = reinterpret_cast<const void *>(__shfl_sync(
+                        0xffffffffu, reinterpret_cast<unsigned long long>(dj.x), b));
+                    d.y = reinterpret_cast<void *>(__shfl_sync(
+                        0xffffffffu, reinterpret_cast<unsigned long long>(dj.y), b));
+                    d.n = __shfl_sync(0xffffffffu, static_cast<long long>(dj.n), b);
+                } else {
+                    // first_tile[cur+1 .. cur+32] <= t, so cur + 32 < n_seg
+                    const int64_t lo = cur + 33;
+                    cur = lo + warp_lower_bound(p.offsets + lo, p.n_seg + 1 - lo, t + 1, lane) - 1;
+                    d = p.segs[cur];
+                }
+                const int64_t lt = t - p.offsets[cur];
                 const int64_t left = d.n - lt * TILE;
                 nt = left < TILE ? static_cast<int>(left) : TILE;
                 tx = static_cast<const In *>(d.x) + lt * TILE;
@@ -661,49 +708,68 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 tx = x + ts;
                 ty = y + ts;
             }
+            const bool bulk = TMA && nt == TILE;
             if (lane == 0) {
                 slot_x[s] = tx;
                 slot_y[s] = ty;
                 slot_nt[s] = nt;
+                if (bulk) {
+                    // start the copy now; the slot's phase also needs the
+                    // arrival below, made once the head bitmap is written
+                    constexpr uint32_t bytes = TILE * sizeof(In);
+                    mbar_expect_tx(&full[s], bytes);
+                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bytes, &full[s]);
+                    armed_mask |= 1u << s;
+                    par_mask = (par_mask & ~(1u << s)) |
+                               (static_cast<uint32_t>((k / ST) & 1) << s);
+                } else {
+                    armed_mask &= ~(1u << s);
+                }
             }
             if constexpr (MODE == MODE_LIST) {
                 uint32_t *bm = bits + s * (TILE / 32);
                 for (int i = lane; i < TILE / 32; i += 32) bm[i] = 0u;
                 __syncwarp();
-                if (lane == 0 && list_head) bm[0] = 1u;  // each array starts a chain
+                if (lane == 0) {
+                    if (list_head) bm[0] = 1u;  // each array starts a chain
+                    inner_s[s] = 0u;            // its only head is element 0
+                }
                 __threadfence_block();
             } else if constexpr (SEG) {
+                // heads in [ts, te), from the first offset not below the
+                // previous tile's end; a binary search skips runs of more
+                // than 32 offsets that lie before ts
                 uint32_t *bm = bits + s * (TILE / 32);
                 for (int i = lane; i < TILE / 32; i += 32) bm[i] = 0u;
                 __syncwarp();
-                const int64_t sa = warp_lower_bound(p.offsets, p.n_seg + 1, ts, lane);
-                for (int64_t i0 = sa; i0 <= p.n_seg; i0 += 32) {
-                    const int64_t i = i0 + lane;
-                    const int64_t o = (i <= p.n_seg) ? p.offsets[i] : te;
+                int64_t i0 = cur;
+                int64_t o = (i0 + lane <= p.n_seg) ? p.offsets[i0 + lane] : INT64_MAX;
+                if (__ballot_sync(0xffffffffu, o >= ts) == 0u) {
+                    // offsets[i0 .. i0+31] < ts, so i0 + 31 <= n_seg
+                    const int64_t lo = i0 + 32;
+                    i0 = lo + warp_lower_bound(p.offsets + lo, p.n_seg + 1 - lo, ts, lane);
+                    o = (i0 + lane <= p.n_seg) ? p.offsets[i0 + lane] : INT64_MAX;
+                }
+                bool inner = false;
+                while (true) {
                     if (o >= ts && o < te) {
                         const int64_t r = o - ts;
                         atomicOr(&bm[r >> 5], 1u << (r & 31));
                     }
-                    if (__ballot_sync(0xffffffffu, o < te) != 0xffffffffu) break;
+                    inner = inner || __any_sync(0xffffffffu, o > ts && o < te);
+                    const uint32_t before_end = __ballot_sync(0xffffffffu, o < te);
+                    if (before_end != 0xffffffffu) {
+                        cur = i0 + __popc(before_end);  // offsets are sorted
+                        break;
+                    }
+                    i0 += 32;
+                    o = (i0 + lane <= p.n_seg) ? p.offsets[i0 + lane] : INT64_MAX;
                 }
+                if (lane == 0) inner_s[s] = inner ? 1u : 0u;
                 __threadfence_block();
             }
             __syncwarp();
-            if (lane == 0) {
-                const bool full_tile = nt == TILE;
-                if (TMA && full_tile) {
-                    constexpr uint32_t bytes = TILE * sizeof(In);
-                    mbar_arrive_expect_tx(&full[s], bytes);
-                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bytes,
-                             &full[s]);
-                    armed_mask |= 1u << s;
-                    par_mask = (par_mask & ~(1u << s)) |
-                               (static_cast<uint32_t>((k / ST) & 1) << s);
-                } else {
-                    mbar_arrive(&full[s]);
-                    armed_mask &= ~(1u << s);
-                }
-            }
+            if (lane == 0) mbar_arrive(&full[s]);
         }
         // Never leave the CTA with a bulk copy still writing its shared memory:
         // wait for every slot whose LAST phase was a bulk copy.  (A slot re-armed
@@ -732,7 +798,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             const int nt = slot_nt[s];
             int start = 0;  // reduce elements [start, nt)
             bool has_head = false;
-            if constexpr (SEG) {
+            const bool inner = SEG && inner_s[s] != 0u;
+            if (inner) {
                 // last segment head in the tile: the aggregate restarts there
                 int last = -1;
                 for (int w = lane; w < TILE / 32; w += 32) {
@@ -742,26 +809,45 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 last = __reduce_max_sync(0xffffffffu, last);
                 has_head = last >= 0;
                 start = has_head ? last : 0;
+            } else if (SEG) {
+                has_head = (bits[s * (TILE / 32)] & 1u) != 0u;  // element 0 at most
             }
             TileReduce<K> r;
             r.init();
-            if (TMA && nt == TILE) {
-                constexpr int EPC = 16 / int(sizeof(In));
-                const uint8_t *tsm = smem + L::off_in + s * TILE * sizeof(In);
-                for (int c = lane; c < TILE / EPC; c += 32) {
-                    const uint4 q = *reinterpret_cast<const uint4 *>(tsm + 16 * c);
-                    const uint4 qa[1] = {q};
-                    In e[EPC];
-                    unpack_chunks<In, EPC, 1>(qa, e);
+            // with and without a head inside the tile
+            auto reduce_tile = [&](auto seg_tag) {
+                constexpr bool SG = decltype(seg_tag)::value;
+                if (TMA && nt == TILE) {
+                    // one accumulator per element position in a 16-byte chunk:
+                    // EPC independent left folds (instruction-level
+                    // parallelism), merged with the order-free rule at the end
+                    constexpr int EPC = 16 / int(sizeof(In));
+                    const uint8_t *tsm = smem + L::off_in + s * TILE * sizeof(In);
+                    TileReduce<K> ra[EPC];
 #pragma unroll
-                    for (int u = 0; u < EPC; ++u) {
-                        const int idx = c * EPC + u;
-                        if (!SEG || idx >= start) r.add(K::load(e[u]), idx);
+                    for (int u = 0; u < EPC; ++u) ra[u].init();
+                    for (int c = lane; c < TILE / EPC; c += 32) {
+                        const uint4 q = *reinterpret_cast<const uint4 *>(tsm + 16 * c);
+                        const uint4 qa[1] = {q};
+                        In e[EPC];
+                        unpack_chunks<In, EPC, 1>(qa, e);
+#pragma unroll
+                        for (int u = 0; u < EPC; ++u) {
+                            const int idx = c * EPC + u;
+                            if (!SG || idx >= start) ra[u].add_in_order(K::load(e[u]), idx);
+                        }
                     }
+#pragma unroll
+                    for (int u = 0; u < EPC; ++u) r.add(ra[u].v, ra[u].i);
+                } else {
+                    for (int i = lane; i < nt; i += 32)
+                        if (!SG || i >= start) r.add(K::load(tx[i]), i);
                 }
+            };
+            if (inner) {
+                reduce_tile(std::true_type{});
             } else {
-                for (int i = lane; i < nt; i += 32)
-                    if (!SEG || i >= start) r.add(K::load(tx[i]), i);
+                reduce_tile(std::false_type{});
             }
             r.warp_all();
             if (lane == 0) {
@@ -848,34 +934,41 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 for (int i = 0; i < ITEMS; ++i)
                     v[i] = (e0 + i < nt) ? K::load(tx[e0 + i]) : K::ident();
             }
+            // A tile whose only segment head is its first element takes the
+            // unsegmented code: its carry is the identity (the carry warp
+            // skips the look-back for it), which restarts the chain there.
+            const bool inner = SEG && inner_s[s] != 0u;
             uint32_t hb = 0;  // head bits of my ITEMS elements
-            if constexpr (SEG) {
+            if (inner) {
                 const uint32_t w = bits[s * (TILE / 32) + (e0 >> 5)];
                 hb = (w >> (e0 & 31)) & (ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u));
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+            // the rest of the tile, compiled with and without segment heads
+            auto finish_tile = [&](auto seg_tag) -> bool {
+            constexpr bool SG = decltype(seg_tag)::value;
             // ---- thread-serial scan ----
 #pragma unroll
             for (int i = 1; i < ITEMS; ++i) {
-                if (SEG && ((hb >> i) & 1u)) continue;
+                if (SG && ((hb >> i) & 1u)) continue;
                 v[i] = K::op(v[i - 1], v[i]);
             }
             // ---- warp scan of thread totals (Hillis-Steele, 5 rounds) ----
             Acc wv = v[ITEMS - 1];
-            uint32_t wf = SEG ? (hb != 0u) : 0u;
+            uint32_t wf = SG ? (hb != 0u) : 0u;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
                 const Acc ov = shfl_up_any(wv, d);
-                const uint32_t of = SEG ? __shfl_up_sync(0xffffffffu, wf, d) : 0u;
+                const uint32_t of = SG ? __shfl_up_sync(0xffffffffu, wf, d) : 0u;
                 if (lane >= d) {
-                    if (!(SEG && wf)) wv = K::op(ov, wv);
+                    if (!(SG && wf)) wv = K::op(ov, wv);
                     wf |= of;
                 }
             }
             // exclusive lane prefix
             Acc lv = shfl_up_any(wv, 1);
-            uint32_t lf = SEG ? __shfl_up_sync(0xffffffffu, wf, 1) : 0u;
+            uint32_t lf = SG ? __shfl_up_sync(0xffffffffu, wf, 1) : 0u;
             if (lane == 0) {
                 lv = K::ident();
                 lf = 0u;
@@ -894,31 +987,31 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             uint32_t bf = 0u;
             if (lane < CW) {
                 bv = wt[lane].v;
-                bf = SEG ? wt[lane].f : 0u;
+                bf = SG ? wt[lane].f : 0u;
             }
 #pragma unroll
             for (int d = 1; d < CW; d <<= 1) {
                 const Acc ov = shfl_up_any(bv, d);
-                const uint32_t of = SEG ? __shfl_up_sync(0xffffffffu, bf, d) : 0u;
+                const uint32_t of = SG ? __shfl_up_sync(0xffffffffu, bf, d) : 0u;
                 if (lane >= d) {
-                    if (!(SEG && bf)) bv = K::op(ov, bv);
+                    if (!(SG && bf)) bv = K::op(ov, bv);
                     bf |= of;
                 }
             }
             Acc wev = shfl_idx_any(bv, warp > 0 ? warp - 1 : 0);
-            uint32_t wef = SEG ? __shfl_sync(0xffffffffu, bf, warp > 0 ? warp - 1 : 0) : 0u;
+            uint32_t wef = SG ? __shfl_sync(0xffffffffu, bf, warp > 0 ? warp - 1 : 0) : 0u;
             if (warp == 0) {
                 wev = K::ident();
                 wef = 0u;
             }
             // thread base = warp offset (+) lane offset
             Acc tbv;
-            if (SEG && lf) {
+            if (SG && lf) {
                 tbv = lv;
             } else {
                 tbv = K::op(wev, lv);
             }
-            const uint32_t tbf = SEG ? (wef | lf) : 0u;
+            const uint32_t tbf = SG ? (wef | lf) : 0u;
 
             // ---- carry from the carry warp (Section 4.3) ----
             const int cslot = static_cast<int>(k % CR);
@@ -939,8 +1032,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 bool pf;  // a head at or before the contributing prefix, in thread
                 if (p.inclusive) {
                     pv = v[i];
-                    pf = SEG && ((hb & ((2u << i) - 1u)) != 0u);
-                } else if (SEG && ((hb >> i) & 1u)) {
+                    pf = SG && ((hb & ((2u << i) - 1u)) != 0u);
+                } else if (SG && ((hb >> i) & 1u)) {
                     pv = K::ident();  // a segment head's exclusive value
                     pf = true;
                 } else if (i == 0) {
@@ -948,9 +1041,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     pf = false;
                 } else {
                     pv = v[i - 1];
-                    pf = SEG && ((hb & ((1u << i) - 1u)) != 0u);
+                    pf = SG && ((hb & ((1u << i) - 1u)) != 0u);
                 }
-                const CarA b = pf ? BI : ((SEG && tbf) ? BL : B);
+                const CarA b = pf ? BI : ((SG && tbf) ? BL : B);
                 o[i] = K::fin(b, pv);
             }
             if (TMA && full_tile && OS == 0) {
@@ -985,6 +1078,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i)
                     if (e0 + i < nt) ty[e0 + i] = o[i];
+            }
+            return stop;
+            };
+            bool stop;
+            if constexpr (SEG) {
+                stop = inner ? finish_tile(std::true_type{}) : finish_tile(std::false_type{});
+            } else {
+                stop = finish_tile(std::false_type{});
             }
             if (stop) break;
         }

@@ -106,6 +106,7 @@ def test_server_entry_points_reject_null_handles(lib):
     assert L.lscan_server_wait(None, 1, None) == lib.LSCAN_ERR_INVALID
     assert L.lscan_server_release(None, 1) == lib.LSCAN_ERR_INVALID
     assert L.lscan_server_alloc(None, 16, None) == lib.LSCAN_ERR_INVALID
+    assert L.lscan_server_hold(None, 1) == lib.LSCAN_ERR_INVALID
     assert not L.lscan_server_create(1 << 20, 0)   # bad stream count
     L.lscan_server_destroy(None)                   # no-op
 

@@ -178,13 +178,18 @@ def _offsets(kind, rng):
         lens = [300001] + [1, 2, 0, 3] * 500
     elif kind == "empty_tail":
         lens = [10, 0, 0, 0]
+    elif kind == "tile_aligned":
+        # heads only at tile starts for every config (tiles of 2^11..2^14
+        # elements): tiles take the unsegmented code with an identity carry
+        lens = [16384, 32768, 0, 49152, 16384, 5]
     else:  # log-uniform like the batched workload, smaller
         lens = batched_lengths(300, max_log2=14, seed=int(rng.integers(1e6)))
     return offsets_from_lengths(lens)
 
 
 @pytest.mark.parametrize("pattern", ["mixed", "tiny", "huge_plus_tiny",
-                                     "empty_tail", "loguniform"])
+                                     "empty_tail", "loguniform",
+                                     "tile_aligned"])
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
 @pytest.mark.parametrize("kind", [KINDS[0], KINDS[1], KINDS[2], KINDS[3],
                                   KINDS[5], KINDS[6], KINDS[8]],

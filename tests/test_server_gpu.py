@@ -62,10 +62,13 @@ def test_same_alone_and_in_the_mix():
             assert st["status"] == 0 and st["batch_requests"] == 1
             srv.release(tk)
             alone.append(to_host(y))
-        # in the mix: everything submitted back to back, then collected
+        # in the mix: everything queued while the server holds, then
+        # launched together (batched by kind) and collected
         ys = [_out_like(r) for r in reqs]
+        srv.hold(True)
         tks = [srv.submit(xd, r["op"], r["incl"], out=y)
                for r, xd, y in zip(reqs, xs, ys)]
+        srv.hold(False)
         stats = [srv.wait(tk) for tk in tks]
         for tk in tks:
             srv.release(tk)
