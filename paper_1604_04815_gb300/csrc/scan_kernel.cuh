@@ -86,15 +86,17 @@ struct Layout {
     // carry hand-off ring (carry warps -> consumers), deeper than the tile ring
     // so that no input slot waits for a look-back
     static constexpr int CR = 2 * Cfg::STAGES;
-    // mbarriers full[ST], empty[ST], reduced[ST], carried[CR]
+    // mbarriers full[ST], empty[ST] (tile slots); ticketed[CR], reduced[CR],
+    // carried[CR] (carry ring)
     static constexpr int off_bar = align_up_c(off_bits + kBits, 128);
-    static constexpr int off_tile = off_bar + 8 * (3 * Cfg::STAGES + CR);  // int64[ST]
-    static constexpr int off_agg = off_tile + 8 * Cfg::STAGES;      // Car[ST]
-    static constexpr int off_carry = off_agg + 8 * Cfg::STAGES;     // CarA[CR]
-    // u32 head[ST], stop[CR], inner[ST]
+    static constexpr int off_tile = off_bar + 8 * (2 * Cfg::STAGES + 3 * CR);  // int64[ST]
+    static constexpr int off_tr = off_tile + 8 * Cfg::STAGES;       // int64[CR]
+    static constexpr int off_agg = off_tr + 8 * CR;                 // Car[CR]
+    static constexpr int off_carry = off_agg + 8 * CR;              // CarA[CR]
+    // u32 head[CR], stop[CR], head0[CR], inner[ST]
     static constexpr int off_flags = off_carry + 8 * CR;
     // per-slot tile descriptor: x and y of the tile's first element, count
-    static constexpr int off_sx = align_up_c(off_flags + 4 * (2 * Cfg::STAGES + CR), 16);  // ptr[ST]
+    static constexpr int off_sx = align_up_c(off_flags + 4 * (3 * CR + Cfg::STAGES), 16);  // ptr[ST]
     static constexpr int off_sy = off_sx + 8 * Cfg::STAGES;         // ptr[ST]
     static constexpr int off_snt = off_sy + 8 * Cfg::STAGES;        // i32[ST]
     static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
@@ -104,7 +106,8 @@ struct Layout {
     // every field is naturally aligned (a misaligned 8-byte shared access
     // faults the launch)
     static_assert(off_in % 16 == 0 && off_out % 16 == 0 && off_bits % 16 == 0, "ring");
-    static_assert(off_bar % 8 == 0 && off_tile % 8 == 0 && off_agg % 8 == 0, "8-byte");
+    static_assert(off_bar % 8 == 0 && off_tile % 8 == 0 && off_tr % 8 == 0 &&
+                      off_agg % 8 == 0, "8-byte");
     static_assert(off_carry % 8 == 0 && off_sx % 8 == 0 && off_snt % 4 == 0, "8-byte");
     static_assert(off_wtot % 16 == 0 && off_abort % 4 == 0, "totals");
 };
@@ -407,6 +410,17 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
             last_mask = need;
             found = inc != 0u;
         }
+        if (use == 1 && last_mask == 1u) {
+            // only the nearest tile is needed and it holds an inclusive
+            // prefix (the common case): no butterfly
+            const Car v0 = shfl_idx_any(val[0], 0);
+            if constexpr (K::kTieOrdered) {
+                excl.add(v0, base);
+            } else {
+                excl.v = K::cop(v0, excl.v);
+            }
+            break;
+        }
         if (use > 0) {
             CarryFold<K> part;
             part.init();
@@ -561,23 +575,30 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
-    // Each carry warp must see every phase of the slots it waits on (an
-    // mbarrier parity wait aliases if a phase is skipped), so carry warp c
-    // always takes the same slots: ST must be a multiple of NC.
-    static_assert(NC >= 1 && ST % NC == 0, "carry warps must own whole slots");
+    // Each carry warp must see every phase of the ring entries it waits on
+    // (an mbarrier parity wait aliases if a phase is skipped), so carry warp
+    // c always takes the same entries: CR = 2 ST must be a multiple of NC.
+    // NC <= ST also keeps the terminator hand-off below safe.
+    static_assert(NC >= 1 && ST % NC == 0, "carry warps must own whole entries");
 
     extern __shared__ __align__(128) uint8_t smem[];
+    // Tile slots (input data, per slot s = k % ST of ring use k) and the
+    // carry ring (per entry c = k % CR): the carry warp only touches the
+    // ring, so it never holds an input slot while it looks back.
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::off_bar);
-    uint64_t *empty = full + ST;    // slot consumed: consumers, reducer, carry
-    uint64_t *reduced = empty + ST;  // reducer published the tile's status
-    uint64_t *carried = reduced + ST;  // carry warp stored the tile's carry [CR]
-    volatile int64_t *tile_of = reinterpret_cast<int64_t *>(smem + L::off_tile);
-    Car *agg_s = reinterpret_cast<Car *>(smem + L::off_agg);        // reducer -> carry
-    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // carry -> consumers [CR]
-    volatile uint32_t *head_s = reinterpret_cast<uint32_t *>(smem + L::off_flags);
-    volatile uint32_t *stop_s = head_s + ST;  // [CR]
+    uint64_t *empty = full + ST;       // slot consumed: consumer warps + reducer
+    uint64_t *ticketed = empty + ST;   // [CR] producer: tile index, head0
+    uint64_t *reduced = ticketed + CR;  // [CR] reducer: tile aggregate published
+    uint64_t *carried = reduced + CR;  // [CR] carry warp: the tile's carry
+    volatile int64_t *tile_of = reinterpret_cast<int64_t *>(smem + L::off_tile);  // [ST]
+    volatile int64_t *tile_r = reinterpret_cast<int64_t *>(smem + L::off_tr);     // [CR]
+    Car *agg_r = reinterpret_cast<Car *>(smem + L::off_agg);        // [CR] reducer -> carry
+    CarA *carry_s = reinterpret_cast<CarA *>(smem + L::off_carry);  // [CR] carry -> consumers
+    volatile uint32_t *head_r = reinterpret_cast<uint32_t *>(smem + L::off_flags);  // [CR]
+    volatile uint32_t *stop_s = head_r + CR;   // [CR]
+    volatile uint32_t *head0_r = stop_s + CR;  // [CR] head at the tile's first element
     // tile has a segment head after its first element (segmented code needed)
-    volatile uint32_t *inner_s = stop_s + CR;  // [ST]
+    volatile uint32_t *inner_s = head0_r + CR;  // [ST]
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
@@ -592,14 +613,17 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW + 2);  // consumer warps + reducer + its carry warp
-            mbar_init(&reduced[s], 1);
+            mbar_init(&empty[s], CW + 1);  // consumer warps + reducer
             tile_of[s] = INT64_MAX;
-            head_s[s] = 0;
             inner_s[s] = 0;
         }
         for (int c = 0; c < CR; ++c) {
+            mbar_init(&ticketed[c], 1);
+            mbar_init(&reduced[c], 1);
             mbar_init(&carried[c], 1);
+            tile_r[c] = INT64_MAX;
+            head_r[c] = 0;
+            head0_r[c] = 0;
             stop_s[c] = 0;
         }
         *abort_s = 0;
@@ -642,24 +666,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             if (t >= p.n_tiles) {
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(&full[s]);
+                    mbar_arrive(&full[s]);     // consumer warps and reducer stop
                     armed_mask &= ~(1u << s);  // this slot's last phase is plain
-                    // The carry warps that own the next NC - 1 ring uses would
-                    // wait for them forever: hand them the terminator too.
-                    // (Those slots' previous uses were real tiles, so their
-                    // empty phases complete.)
-                    for (int64_t j = 1; j < NC; ++j) {
-                        const int64_t kj = k + j;
-                        const int sj = static_cast<int>(kj % ST);
-                        if (kj >= ST &&
-                            !wait_phase(&empty[sj],
-                                        static_cast<uint32_t>(((kj / ST) - 1) & 1), wc)) {
-                            *abort_s = 1;
-                            break;
-                        }
-                        tile_of[sj] = INT64_MAX;
-                        mbar_arrive(&full[sj]);
-                        armed_mask &= ~(1u << sj);
+                    // every carry warp stops at its next ring use: uses k ..
+                    // k + NC - 1.  Entry (k + j) % CR was last used by
+                    // k + j - 2 ST <= k - ST - 1 (NC <= ST), whose carry the
+                    // consumers took before releasing slot s for use k.
+                    for (int64_t j = 0; j < NC; ++j) {
+                        const int cj = static_cast<int>((k + j) % CR);
+                        tile_r[cj] = INT64_MAX;
+                        mbar_arrive(&ticketed[cj]);
                     }
                 }
                 break;
@@ -769,7 +785,21 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 __threadfence_block();
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&full[s]);
+            if (lane == 0) {
+                // the carry warp may start this tile's look-back now, while
+                // its data is still in flight
+                const int c = static_cast<int>(k % CR);
+                tile_r[c] = t;
+                bool h0 = false;
+                if constexpr (MODE == MODE_LIST) {
+                    h0 = list_head;
+                } else if constexpr (SEG) {
+                    h0 = (bits[s * (TILE / 32)] & 1u) != 0u;
+                }
+                head0_r[c] = h0 ? 1u : 0u;
+                mbar_arrive(&ticketed[c]);
+                mbar_arrive(&full[s]);
+            }
         }
         // Never leave the CTA with a bulk copy still writing its shared memory:
         // wait for every slot whose LAST phase was a bulk copy.  (A slot re-armed
@@ -857,9 +887,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                                          ebase | ((t == 0 || has_head) ? ST_INCLUSIVE
                                                                         : ST_AGGREGATE),
                                          agg);
-                agg_s[s] = agg;
-                head_s[s] = has_head ? 1u : 0u;
-                mbar_arrive(&reduced[s]);
+                const int c = static_cast<int>(k % CR);
+                agg_r[c] = agg;
+                head_r[c] = has_head ? 1u : 0u;
+                mbar_arrive(&reduced[c]);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
@@ -867,40 +898,40 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     } else if (warp >= W_CARRY) {
         // ========================= carry warps ==========================
         // Resolve each tile's exclusive prefix (Section 4.3) as soon as the
-        // reducer has published the tile's status, running ahead of the
-        // consumer warps, and publish the tile's inclusive prefix.  Carry
-        // warp c takes ring uses k = c, c + NC, ...: the tiles of one CTA are
-        // not neighbours (tickets interleave across CTAs), so their look-backs
+        // reducer has published the tile's aggregate, running ahead of the
+        // consumer warps, and publish the tile's inclusive prefix.  The carry
+        // warp reads only the carry ring, so the tile's input slot is
+        // released by the consumers and the reducer alone.  Carry warp c
+        // takes ring uses k = c, c + NC, ...: the tiles of one CTA are not
+        // neighbours (tickets interleave across CTAs), so their look-backs
         // are independent and may overlap.
         for (int64_t k = warp - W_CARRY;; k += NC) {
-            const int s = static_cast<int>(k % ST);
-            const uint32_t par = static_cast<uint32_t>((k / ST) & 1);
-            const bool okf = wait_phase(&full[s], par, wc);
-            if (!__all_sync(0xffffffffu, okf)) {
+            const int c = static_cast<int>(k % CR);
+            const uint32_t par = static_cast<uint32_t>((k / CR) & 1);
+            const bool okt = wait_phase(&ticketed[c], par, wc);
+            if (!__all_sync(0xffffffffu, okt)) {
                 if (lane == 0) *abort_s = 1;
                 break;
             }
-            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
+            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_r[c]), 0);
             if (t >= p.n_tiles) break;
-            const bool okr = wait_phase(&reduced[s], par, wc);
+            const bool head0 = SEG && head0_r[c] != 0u;
+            // Measured on GB300: looking back once the tile's own aggregate
+            // is out is as fast for int32 and faster for fp32 add than
+            // starting at the ticket (the early look-back only polls longer
+            // for predecessors whose data is still in flight).
+            const bool okr = wait_phase(&reduced[c], par, wc);
             if (!__all_sync(0xffffffffu, okr) && lane == 0) *abort_s = 1;
-            // take what the look-back needs and free the tile slot at once:
-            // input buffers must not wait for carries
-            const bool has_head = SEG && head_s[s] != 0u;
-            const bool head0 = SEG && ((bits[s * (TILE / 32)] & 1u) != 0u);
-            const Car agg = agg_s[s];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
             Car excl = K::cident();
             if (t > 0 && !head0)
                 excl = p.carry_mode == CARRY_CHAINED ? chained_wait<K>(p, wc, t, ebase, lane)
                                                      : lookback<K>(p, wc, t, ebase, lane);
             if (lane == 0) {
+                const bool has_head = SEG && head_r[c] != 0u;
                 // tile 0 and tiles holding a head got theirs from the reducer
                 if (t > 0 && !has_head && t != p.skip_tile)
                     StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
-                                         K::cop(excl, agg));
-                const int c = static_cast<int>(k % CR);
+                                         K::cop(excl, agg_r[c]));
                 carry_s[c] = K::to_apply(excl);
                 stop_s[c] = *abort_s;  // one snapshot for every consumer warp
                 mbar_arrive(&carried[c]);
