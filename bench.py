@@ -511,7 +511,7 @@ def bench_serving(args, dev, peak, n_req, fracs, seed=6):
         out_es = 4 if (r["op"] == "add" and r["dtype"] == "bf16") else es
         nbytes += r["n"] * (es + out_es)
         base.append([r["op"], t, True, lk.data_ptr() + off * es, r["n"]])
-    n_streams = getattr(args, "serving_streams", 4)
+    n_streams = getattr(args, "serving_streams", 2)
     srv = lscan.Server(budget_bytes=16 << 30, n_streams=n_streams)
     out = {"requests": n_req, "budget_gib": 16, "n_streams": n_streams,
            "mean_elems": float(np.mean([r["n"] for r in mix]))}
@@ -572,7 +572,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=3000)
-    ap.add_argument("--serving-streams", type=int, default=4)
+    ap.add_argument("--serving-streams", type=int, default=2)
     ap.add_argument("--serving-full", action="store_true",
                     help="20000 requests per load level, loads 0.5/0.8/0.95")
     ap.add_argument("--log2n", type=int, default=28,

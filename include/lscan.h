@@ -284,11 +284,14 @@ lscan_status lscan_autotune(lscan_op op, lscan_dtype dtype, int inclusive,
                             const lscan_options *opts, int reps, void *stream,
                             int32_t *best_config, float *best_ms);
 /* The tuning table as JSON ({"lscan_tune": 1, "entries": [[kind, mode,
- * size_class, config], ...]}); it is also loaded automatically from
- * $LSCAN_TUNE_FILE on first use. */
+ * size_class, config], ...]}, only entries that differ from the defaults);
+ * it is also loaded automatically from $LSCAN_TUNE_FILE on first use. */
 lscan_status lscan_tune_save(const char *path);
 lscan_status lscan_tune_load(const char *path);
-/* Back to the built-in default (configuration 2 everywhere). */
+/* Back to the built-in defaults: each kind's fastest configuration on a
+ * 2^28-element array (2 for most; 3 for fp32 add with the FP64 carry and
+ * for bf16 add with the FP64 carry and bf16 output; 1 for the compensated
+ * bf16 adds). */
 lscan_status lscan_tune_reset(void);
 
 /* Describes a tile configuration: writes items per thread, consumer threads

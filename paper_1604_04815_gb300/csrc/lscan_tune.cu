@@ -1,7 +1,11 @@
 // lscan_tune.cu -- tile-configuration table and the autotuner that fills it.
 //
-// Entries are (kind, mode, log2 size class) -> variant (1..kNumTmaCfg); the
-// default is variant 2 (16 KiB input tiles, 8 consumer warps, 3-stage ring).
+// Entries are (kind, mode, log2 size class) -> variant (1..kNumTmaCfg).  The
+// default is each kind's fastest variant on a 2^28-element array (GB300,
+// 16-segment batches agree): variant 2 (16 KiB input tiles, 8 consumer warps)
+// for most kinds, variant 3 (32 KiB tiles, 16 consumer warps) for fp32 add
+// with an FP64 carry (5478 vs 4454 GB/s) and for bf16 add with an FP64 carry
+// and bf16 output, variant 1 for the compensated bf16 adds.
 // lscan_autotune times every bulk-copy configuration on the caller's buffers
 // with CUDA events and records the fastest; the table persists as JSON
 // ({"lscan_tune": 1, "entries": [[kind, mode, size_class, config], ...]}) and
@@ -15,6 +19,7 @@
 
 #include "../../include/lscan.h"
 #include "kernel_table.h"
+#include "kinds.cuh"
 #include "lscan_internal.h"
 
 namespace lscan {
@@ -27,10 +32,27 @@ std::mutex g_tab_mu;
 
 lscan_status load_file(const char *path);
 
+int default_variant(int kind) {
+    switch (kind) {
+        case KIND_F32_ADD_F64:
+        case KIND_BF16_ADD_F64_BF16:
+            return 3;
+        case KIND_BF16_ADD_COMP_F32:
+        case KIND_BF16_ADD_COMP_BF16:
+            return 1;
+        default:
+            return 2;
+    }
+}
+
+void fill_defaults(int (&t)[kNumKinds][MODE_COUNT][kSizeClasses]) {
+    for (int k = 0; k < kNumKinds; ++k)
+        for (auto &b : t[k])
+            for (int &v : b) v = default_variant(k);
+}
+
 void init_table() {
-    for (auto &a : g_table)
-        for (auto &b : a)
-            for (int &v : b) v = 2;
+    fill_defaults(g_table);
     if (const char *f = std::getenv("LSCAN_TUNE_FILE")) (void)load_file(f);
 }
 
@@ -45,7 +67,7 @@ int tuned_variant(int kind, int mode, int64_t n) {
     std::call_once(g_tab_once, init_table);
     std::lock_guard<std::mutex> lk(g_tab_mu);
     const int v = g_table[kind][mode][size_class(n)];
-    return (v >= 1 && v <= kNumTmaCfg) ? v : 2;
+    return (v >= 1 && v <= kNumTmaCfg) ? v : default_variant(kind);
 }
 
 void set_tuned_variant(int kind, int mode, int size_cls, int variant) {
@@ -129,7 +151,7 @@ lscan_status lscan_tune_save(const char *path) {
     for (int k = 0; k < kNumKinds; ++k)
         for (int m = 0; m < MODE_COUNT; ++m)
             for (int c = 0; c < kSizeClasses; ++c)
-                if (g_table[k][m][c] != 2) {
+                if (g_table[k][m][c] != default_variant(k)) {
                     std::fprintf(f, "%s[%d, %d, %d, %d]", first ? "" : ", ", k, m, c,
                                  g_table[k][m][c]);
                     first = false;
@@ -147,9 +169,7 @@ lscan_status lscan_tune_load(const char *path) {
 lscan_status lscan_tune_reset(void) {
     std::call_once(g_tab_once, init_table);
     std::lock_guard<std::mutex> lk(g_tab_mu);
-    for (auto &a : g_table)
-        for (auto &b : a)
-            for (int &v : b) v = 2;
+    fill_defaults(g_table);
     return LSCAN_OK;
 }
 
@@ -174,9 +194,7 @@ lscan_status load_file(const char *path) {
     if (pos == std::string::npos) return LSCAN_ERR_INVALID;
     ++pos;
     int loaded[kNumKinds][MODE_COUNT][kSizeClasses];
-    for (auto &a : loaded)
-        for (auto &b : a)
-            for (int &v : b) v = 2;
+    fill_defaults(loaded);
     while (true) {
         const size_t open = text.find('[', pos);
         if (open == std::string::npos) break;

@@ -940,13 +940,20 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     } else {
         // ============================ consumer warps ===========================
         const int e0 = tid * ITEMS;  // first element of this thread in a tile
+        // Consumer warps leave the loop only together (they share named
+        // barriers): each tile starts with a vote.  A warp votes to stop on
+        // the terminator, on a wait that ran out (its slot or tile index may
+        // then be stale) or when the previous tile's carry did not arrive or
+        // came with the abort flag.
+        bool stop_next = false;
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             const uint32_t par = static_cast<uint32_t>((k / ST) & 1);
-            const bool ok = wait_phase(&full[s], par, wc);
-            if (!__all_sync(0xffffffffu, ok) && lane == 0) *abort_s = 1;
-            const int64_t t = __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0);
-            if (t >= p.n_tiles) break;
+            const bool ok = __all_sync(0xffffffffu, wait_phase(&full[s], par, wc));
+            if (!ok && lane == 0) *abort_s = 1;
+            const int64_t t =
+                ok ? __shfl_sync(0xffffffffu, static_cast<long long>(tile_of[s]), 0) : INT64_MAX;
+            if (named_bar_or(2, CT, !ok || t >= p.n_tiles || stop_next)) break;
             const In *tx = slot_x[s];
             Out *ty = slot_y[s];
             const int nt = slot_nt[s];
@@ -1046,11 +1053,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
 
             // ---- carry from the carry warp (Section 4.3) ----
             const int cslot = static_cast<int>(k % CR);
-            const bool okc = wait_phase(&carried[cslot],
-                                        static_cast<uint32_t>((k / CR) & 1), wc);
-            if (!__all_sync(0xffffffffu, okc) && lane == 0) *abort_s = 1;
+            const bool okc = __all_sync(
+                0xffffffffu,
+                wait_phase(&carried[cslot], static_cast<uint32_t>((k / CR) & 1), wc));
+            if (!okc && lane == 0) *abort_s = 1;
             const CarA cin = carry_s[cslot];
-            const bool stop = stop_s[cslot] != 0u;
+            const bool stop = !okc || stop_s[cslot] != 0u;
 
             // ---- apply carry and write y once (Section 4.4) ----
             const CarA B = K::base(cin, tbv);            // carry (+) thread base
@@ -1112,13 +1120,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             }
             return stop;
             };
-            bool stop;
             if constexpr (SEG) {
-                stop = inner ? finish_tile(std::true_type{}) : finish_tile(std::false_type{});
+                stop_next = inner ? finish_tile(std::true_type{}) : finish_tile(std::false_type{});
             } else {
-                stop = finish_tile(std::false_type{});
+                stop_next = finish_tile(std::false_type{});
             }
-            if (stop) break;
         }
         if (lane == 0) bulk_wait_all<0>();
     }

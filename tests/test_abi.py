@@ -130,4 +130,11 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
     assert json.loads(out.read_text())["entries"] == []
+    # defaults are per kind (kind 5, fp32 add with an FP64 carry, defaults to
+    # configuration 3): only entries that differ from them are saved
+    p.write_text('{"lscan_tune": 1, "entries": [[5, 0, 28, 3], [5, 0, 27, 2]]}')
+    assert lib.lscan_tune_load(p) == lib.LSCAN_OK
+    assert lib.lscan_tune_save(out) == lib.LSCAN_OK
+    assert json.loads(out.read_text())["entries"] == [[5, 0, 27, 2]]
+    assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_autotune(0, 0, 1, 16, 32, 0)[0] == lib.LSCAN_ERR_INVALID
