@@ -183,6 +183,13 @@ def _barrier(ws):
         dist.barrier()
 
 
+def _aggregate(step_bytes, steps, elapsed_s, ws):
+    """Whole-job throughput: the bytes of every rank's steps over the slowest
+    rank's timed region.  Returns (max elapsed seconds, GB/s)."""
+    elapsed_max = _reduce_max(elapsed_s, ws)
+    return elapsed_max, step_bytes * steps * ws / elapsed_max / 1e9
+
+
 # --------------------------------------------------------------- CPU oracle
 def cpu_baseline(budget_s=12.0, n=N):
     """Times the sequential oracle on the step's three arrays (bounded)."""
@@ -320,8 +327,7 @@ def run_gpu(args, ws, rank, local):
     clk = clocks.stop() if clocks else None
     _lib.check(_lib.lscan_stream_status(sp), "timed region")
     elapsed = t_start.elapsed_time(t_end) / 1e3
-    elapsed_max = _reduce_max(elapsed, ws)
-    value = step_bytes * args.steps * ws / elapsed_max / 1e9
+    elapsed_max, value = _aggregate(step_bytes, args.steps, elapsed, ws)
 
     per_kernel = {}
     for c, op, dt in CASES:
