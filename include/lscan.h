@@ -93,7 +93,16 @@ typedef struct lscan_options {
     int32_t config;      /* 0 = tuned; 1..lscan_num_configs() pick a
                             bulk-copy tile configuration */
     int32_t max_ctas;    /* cap on persistent CTAs, 0 = occupancy x SMs */
-    int32_t reserved[3];
+    int32_t reserved;
+    /* Single-array scans only (not in the paper: the carry-in of a scan
+     * sharded over devices, where shard g starts from the total of the shards
+     * before it).  NULL = the operator's identity.  Otherwise a device
+     * pointer to ONE element of the output type, read by the kernel in
+     * stream order: inclusive y_j = c (+) x_0 (+) ... (+) x_j, exclusive
+     * y_0 = c and y_j = c (+) x_0 (+) ... (+) x_{j-1}.  It must be aligned
+     * to the output element size; batched calls with a carry-in return
+     * LSCAN_ERR_INVALID. */
+    const void *carry_in;
 } lscan_options;
 
 /* Single-array scan (Section 4; Algorithm 1).  x: n input elements, y: n

@@ -39,13 +39,22 @@ def out_dtype_for(op, dtype, out_dtype=None):
     return dtype
 
 
-def _options(op, x_dtype, out_dtype, precision, carry, config, max_ctas):
+def _options(op, x_dtype, out_dtype, precision, carry, config, max_ctas,
+             carry_in=None):
     od = 0
     if out_dtype is not None and out_dtype != out_dtype_for(op, x_dtype):
         od = _DT[out_dtype]
+    cin = None
+    if carry_in is not None:
+        if (not isinstance(carry_in, torch.Tensor) or not carry_in.is_cuda
+                or carry_in.numel() < 1
+                or carry_in.dtype != out_dtype_for(op, x_dtype, out_dtype)):
+            raise TypeError("carry_in must be a CUDA tensor holding one "
+                            "element of the output dtype")
+        cin = carry_in.data_ptr()
     return _lib.make_options(out_dtype=od, precision=_PREC[precision],
                              carry=_CARRY[carry], config=int(config),
-                             max_ctas=int(max_ctas))
+                             max_ctas=int(max_ctas), carry_in=cin)
 
 
 def _check_input(x):
@@ -58,15 +67,19 @@ def _check_input(x):
 
 
 def scan(x, op="add", inclusive=True, out=None, *, precision=None,
-         carry=None, config=0, max_ctas=0, out_dtype=None, stream=None):
-    """Inclusive or exclusive scan of a 1-D CUDA tensor (one kernel launch)."""
+         carry=None, config=0, max_ctas=0, out_dtype=None, carry_in=None,
+         stream=None):
+    """Inclusive or exclusive scan of a 1-D CUDA tensor (one kernel launch).
+    carry_in: optional one-element CUDA tensor of the output dtype that is
+    combined in front of x[0] (the offset of a shard of a longer scan)."""
     _check_input(x)
     odt = out_dtype_for(op, x.dtype, out_dtype)
     if out is None:
         out = torch.empty(x.shape[0], dtype=odt, device=x.device)
     elif out.dtype != odt or out.shape != x.shape or not out.is_contiguous():
         raise ValueError("out has the wrong dtype, shape or layout")
-    opts = _options(op, x.dtype, out_dtype, precision, carry, config, max_ctas)
+    opts = _options(op, x.dtype, out_dtype, precision, carry, config, max_ctas,
+                    carry_in)
     st = _lib.lscan_scan(_OPS[op], _DT[x.dtype], int(bool(inclusive)),
                          x.data_ptr(), out.data_ptr(), x.shape[0], opts,
                          _stream_ptr(stream))
@@ -119,15 +132,16 @@ class Graph:
     def scan(cls, x, out, op="add", inclusive=True, **kw):
         import ctypes
         _check_input(x)
+        cin = kw.get("carry_in")
         opts = _options(op, x.dtype, kw.get("out_dtype"), kw.get("precision"),
                         kw.get("carry"), kw.get("config", 0),
-                        kw.get("max_ctas", 0))
+                        kw.get("max_ctas", 0), cin)
         h = ctypes.c_void_p()
         st = _lib.load().lscan_graph_create_scan(
             _OPS[op], _DT[x.dtype], int(bool(inclusive)), x.data_ptr(),
             out.data_ptr(), x.shape[0], ctypes.byref(opts), ctypes.byref(h))
         _lib.check(st, "lscan_graph_create_scan")
-        return cls(h, (x, out))
+        return cls(h, (x, out, cin))
 
     @classmethod
     def batched(cls, x, offsets, out, op="add", inclusive=True, **kw):

@@ -45,8 +45,8 @@ EXPORTED = [
 class lscan_options(ctypes.Structure):
     _fields_ = [("out_dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("carry", ctypes.c_int32), ("config", ctypes.c_int32),
-                ("max_ctas", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("max_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("carry_in", ctypes.c_void_p)]
 
 
 class lscan_req_stats(ctypes.Structure):
@@ -156,13 +156,15 @@ def check(status, where):
         raise LscanError(status, where)
 
 
-def make_options(out_dtype=0, precision=0, carry=0, config=0, max_ctas=0):
+def make_options(out_dtype=0, precision=0, carry=0, config=0, max_ctas=0,
+                 carry_in=None):
     o = lscan_options()
     o.out_dtype = out_dtype
     o.precision = precision
     o.carry = carry
     o.config = config
     o.max_ctas = max_ctas
+    o.carry_in = carry_in
     return o
 
 

@@ -2,7 +2,8 @@
 //
 // A "kind" fixes: storage types In/Out, the in-tile accumulation type Acc,
 // the inter-tile carry type Car (what the status words carry), and CarA, the
-// form in which a tile applies its carry to its elements.  The operator is
+// form in which a tile applies its carry to its elements; car_of_out reads a
+// caller's carry-in (one output element) as a carry.  The operator is
 // always combined as op(earlier, later), so the code never relies on
 // commutativity even though add and max are commutative (Section 1 only asks
 // for associativity).
@@ -93,6 +94,7 @@ struct KI32Add {
     __device__ static Out fin(CarA b, Acc v) {
         return static_cast<int32_t>(b + v);
     }
+    __device__ static Car car_of_out(Out o) { return static_cast<uint32_t>(o); }
 };
 
 struct KI32Max {
@@ -112,6 +114,7 @@ struct KI32Max {
     __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
     __device__ static CarA base_local(Acc tb) { return tb; }
     __device__ static Out fin(CarA b, Acc v) { return max_keep_left(b, v); }
+    __device__ static Car car_of_out(Out o) { return o; }
 };
 
 template <class InT>
@@ -161,6 +164,7 @@ struct KFMax {
     __device__ static Out fin(CarA b, Acc v) {
         return FloatOut<InT>::cvt_exact(max_keep_left(b, v));
     }
+    __device__ static Car car_of_out(Out o) { return FloatIn<InT>::load(o); }
 };
 
 // float add, plain fp32 carry
@@ -184,6 +188,7 @@ struct KFAddPlain {
     __device__ static Out fin(CarA b, Acc v) {
         return FloatOut<OutT>::cvt(__fadd_rn(b, v));
     }
+    __device__ static Car car_of_out(Out o) { return FloatIn<OutT>::load(o); }
 };
 
 // float add, fp32 in tile, FP64 carry applied as an fp32 (hi, lo) pair
@@ -209,6 +214,9 @@ struct KFAddF64 {
     __device__ static CarA base_local(Acc tb) { return make_float2(tb, 0.0f); }
     __device__ static Out fin(CarA b, Acc v) {
         return FloatOut<OutT>::cvt(__fadd_rn(b.x, __fadd_rn(v, b.y)));
+    }
+    __device__ static Car car_of_out(Out o) {
+        return static_cast<double>(FloatIn<OutT>::load(o));
     }
 };
 
@@ -236,6 +244,9 @@ struct KFAddComp {
     __device__ static CarA base_local(Acc tb) { return tb; }
     __device__ static Out fin(CarA b, Acc v) {
         return FloatOut<OutT>::cvt(df_add(b, v).x);
+    }
+    __device__ static Car car_of_out(Out o) {
+        return static_cast<double>(FloatIn<OutT>::load(o));
     }
 };
 

@@ -238,6 +238,7 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.skip_tile = g_skip_tile.exchange(-1);
     p.inclusive = ls.inclusive ? 1 : 0;
     p.carry_mode = ls.carry_mode;
+    p.carry_in = ls.carry_in;
     void *args[] = {&p};
     cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
                                       dim3(e.threads), args, e.smem, cs);
@@ -282,6 +283,9 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     if (n_tiles > (int64_t{1} << 31) - 1) return LSCAN_ERR_INVALID;
     const int carry = opts ? opts->carry : LSCAN_CARRY_AUTO;
     if (carry < LSCAN_CARRY_AUTO || carry > LSCAN_CARRY_CHAINED) return LSCAN_ERR_INVALID;
+    const void *carry_in = opts ? opts->carry_in : nullptr;
+    if (carry_in && (mode != MODE_SINGLE || reinterpret_cast<uintptr_t>(carry_in) % osz != 0))
+        return LSCAN_ERR_INVALID;
 
     ls->kind = kind;
     ls->mode = mode;
@@ -295,6 +299,7 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     ls->carry_mode = carry == LSCAN_CARRY_CHAINED ? CARRY_CHAINED : CARRY_LOOKBACK;
     ls->max_ctas = opts ? opts->max_ctas : 0;
     ls->status_words = static_cast<size_t>(n_tiles) * e.car_words;
+    ls->carry_in = carry_in;
     return LSCAN_OK;
 }
 

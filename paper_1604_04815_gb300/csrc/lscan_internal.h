@@ -26,6 +26,7 @@ struct LaunchSpec {
     int carry_mode = 0;  // CarryMode
     int max_ctas = 0;
     size_t status_words = 0;
+    const void *carry_in = nullptr;  // MODE_SINGLE only
 };
 
 // Device scratch a launch uses (control block + status words).

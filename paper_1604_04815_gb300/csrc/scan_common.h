@@ -65,6 +65,7 @@ struct ScanParams {
     int64_t skip_tile;  // fault injection: never publish this tile (-1: off)
     int32_t inclusive;
     int32_t carry_mode;  // CarryMode
+    const void *carry_in;  // MODE_SINGLE: one output-type element or null
 };
 
 // Per-launch constants the wait loops need.

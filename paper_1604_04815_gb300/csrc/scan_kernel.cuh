@@ -350,6 +350,14 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
 // still (3455 GB/s): the groups near the frontier are always fresh.
 constexpr int kLookbackWindows = 1;
 
+// The carry-in of a single-array scan: the caller's output-type element, or
+// the operator's identity.
+template <class K>
+__device__ __forceinline__ typename K::Car carry_in_of(const ScanParams &p) {
+    if (p.carry_in == nullptr) return K::cident();
+    return K::car_of_out(*static_cast<const typename K::Out *>(p.carry_in));
+}
+
 template <class K>
 struct CarryFold {
     using Car = typename K::Car;
@@ -882,11 +890,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             r.warp_all();
             if (lane == 0) {
                 const Car agg = K::to_car(r.v);
+                // tile 0 of a single-array scan with a carry-in publishes
+                // carry-in (+) aggregate as its inclusive prefix
+                const Car pub = (!SEG && t == 0 && p.carry_in != nullptr)
+                                    ? K::cop(carry_in_of<K>(p), agg)
+                                    : agg;
                 if (t != p.skip_tile)
                     StatusIO<K>::publish(p.status, t,
                                          ebase | ((t == 0 || has_head) ? ST_INCLUSIVE
                                                                         : ST_AGGREGATE),
-                                         agg);
+                                         pub);
                 const int c = static_cast<int>(k % CR);
                 agg_r[c] = agg;
                 head_r[c] = has_head ? 1u : 0u;
@@ -926,6 +939,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             if (t > 0 && !head0)
                 excl = p.carry_mode == CARRY_CHAINED ? chained_wait<K>(p, wc, t, ebase, lane)
                                                      : lookback<K>(p, wc, t, ebase, lane);
+            else if (!SEG && t == 0)
+                excl = carry_in_of<K>(p);
             if (lane == 0) {
                 const bool has_head = SEG && head_r[c] != 0u;
                 // tile 0 and tiles holding a head got theirs from the reducer

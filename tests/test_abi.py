@@ -80,6 +80,13 @@ def test_host_argument_checks(lib):
     o = L.make_options(carry=5)
     assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
         L.LSCAN_ERR_INVALID
+    # carry-in: aligned to the output element, single-array calls only
+    o = L.make_options(carry_in=base + 2)
+    assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, 10, o) == \
+        L.LSCAN_ERR_INVALID
+    o = L.make_options(carry_in=base * 8)
+    assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2,
+                           base * 4, 3, 10, o) == L.LSCAN_ERR_INVALID
     # batched: negative counts, missing offsets
     assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, None,
                            3, 10) == L.LSCAN_ERR_INVALID
@@ -87,6 +94,15 @@ def test_host_argument_checks(lib):
                            -1, 10) == L.LSCAN_ERR_INVALID
     assert L.lscan_set_wait_limit_ns(0) == L.LSCAN_ERR_INVALID
     assert L.strerror(L.LSCAN_ERR_TIMEOUT) == "device wait ran out of time"
+
+
+def test_options_struct_layout(lib):
+    """lscan_options: five int32 settings, one reserved int32, then the
+    carry-in pointer at byte 24 (32 bytes in all)."""
+    import ctypes
+    from paper_1604_04815_gb300 import _lib
+    assert ctypes.sizeof(_lib.lscan_options) == 32
+    assert _lib.lscan_options.carry_in.offset == 24
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

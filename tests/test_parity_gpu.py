@@ -359,3 +359,111 @@ def test_autotune_picks_a_config_and_stays_correct(tmp_path):
         assert_matches(op, dtype, x, to_host(y2))
     assert _lib.lscan_tune_save(tmp_path / "t.json") == _lib.LSCAN_OK
     assert _lib.lscan_tune_reset() == _lib.LSCAN_OK
+
+
+# ------------------------------------------------------------- carry-in
+def _carry_value(op, dtype, ob, x, rng):
+    """A carry-in in the output representation (numpy scalar) that matters:
+    for max, a value above part of the input."""
+    if op == "add" and dtype == "i32":
+        return np.int32(rng.integers(-2**31, 2**31))
+    if op == "max":
+        if dtype == "bf16":
+            from paper_1604_04815_gb300.workloads import bf16_bits_to_f32
+            v = np.sort(bf16_bits_to_f32(x))[len(x) * 3 // 5] if len(x) else 0.0
+            return np.uint16(np.float32(v).view(np.uint32) >> 16)  # exact
+        if dtype == "i32":
+            return np.int32(np.sort(x)[len(x) * 3 // 5])
+        return np.float32(np.sort(x)[len(x) * 3 // 5])
+    v = np.float32(rng.choice([-1.0, 1.0]) * rng.random() * 100.0)
+    if ob:
+        from paper_1604_04815_gb300.workloads import f32_to_bf16_bits
+        return f32_to_bf16_bits(np.array([v], dtype=np.float32))[0]
+    return v
+
+
+def _expect_with_carry(op, dtype, ob, want, c):
+    """c (+) oracle prefix: exact for int and max, FP64 for float add."""
+    from paper_1604_04815_gb300.workloads import bf16_bits_to_f32
+    if op == "add" and dtype == "i32":
+        return ((want.astype(np.int64) + int(c)) & 0xFFFFFFFF).astype(
+            np.uint32).view(np.int32)
+    if op == "max":
+        if dtype == "bf16":
+            wv = bf16_bits_to_f32(want)
+            cv = bf16_bits_to_f32(np.array([c], dtype=np.uint16))[0]
+            return np.where(wv > cv, want, np.uint16(c)).astype(np.uint16)
+        return np.where(want > c, want, c).astype(want.dtype)
+    cv = float(bf16_bits_to_f32(np.array([c], dtype=np.uint16))[0]) if ob \
+        else float(c)
+    return want + cv, abs(cv)
+
+
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
+def test_carry_in(kind, inclusive):
+    """y = carry_in (+) scan(x): a shard of a longer scan."""
+    import oracle
+    from gpu_util import BOUND
+    from paper_1604_04815_gb300.workloads import bf16_bits_to_f32
+    op, dtype, prec, ob = kind
+    rng = np.random.default_rng(77)
+    odt = torch.bfloat16 if ob else (
+        torch.float32 if (op == "add" and dtype == "bf16") else
+        {"i32": torch.int32, "f32": torch.float32,
+         "bf16": torch.bfloat16}[dtype])
+    tile = _tile(2, dtype)
+    for config, carry in ((0, 0), (2, 0), (2, _lib.LSCAN_CARRY_CHAINED)):
+        for i, n in enumerate([1, 33, tile + 1, 7 * tile + 123]):
+            x = _input(op, dtype, n, seed=300 + i)
+            c = _carry_value(op, dtype, ob, x, rng)
+            ca = np.array([c])
+            if odt == torch.bfloat16:
+                ca = ca.astype(np.uint16).view(np.int16)
+            cdev = torch.from_numpy(ca).cuda().view(odt)
+            xd = to_device(x, dtype)
+            y = torch.empty(n, dtype=odt, device="cuda")
+            opts = _lib.make_options(
+                out_dtype=_lib.LSCAN_BF16 if ob else 0,
+                precision=PREC_CODE[prec] if prec else 0, carry=carry,
+                config=config, carry_in=cdev.data_ptr())
+            s = torch.cuda.current_stream().cuda_stream
+            st = _lib.lscan_scan(LOP[op], LDT[dtype], int(inclusive),
+                                 xd.data_ptr(), y.data_ptr(), n, opts, s)
+            assert st == _lib.LSCAN_OK
+            assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
+            got = to_host(y)
+            want = oracle.scan(op, dtype, x, inclusive)
+            if op == "max" or dtype == "i32":
+                exp = _expect_with_carry(op, dtype, ob, want, c)
+                gb = got.view(np.uint32) if dtype == "f32" else got
+                eb = exp.view(np.uint32) if dtype == "f32" else exp
+                assert np.array_equal(gb, eb), (config, carry, n)
+            else:
+                exp, ac = _expect_with_carry(op, dtype, ob, want, c)
+                sj = oracle.abs_prefix(dtype, x, inclusive) + ac
+                g = (bf16_bits_to_f32(got) if ob else got).astype(np.float64)
+                lim = BOUND[prec] * sj + (2.0 ** -8 * np.abs(exp) if ob else 0)
+                assert np.all(np.abs(g - exp) <= lim), (config, carry, n)
+
+
+def test_carry_in_is_read_at_each_graph_replay():
+    """The carry-in is a device value read in stream order: a graph replays
+    with whatever it holds at that time."""
+    import paper_1604_04815_gb300 as lscan
+    rng = np.random.default_rng(12)
+    n = 5 * 4096 + 17
+    x = random_array("i32", n, rng, kind="uniform")
+    xd = to_device(x, "i32")
+    y = torch.empty_like(xd)
+    c = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g = lscan.Graph.scan(xd, y, carry_in=c)
+    try:
+        for v in (0, 12345, -7):
+            c.fill_(v)
+            g.launch()
+            g.status()
+            want = (np.cumsum(x.astype(np.int64)) + v).astype(np.int32)
+            assert np.array_equal(to_host(y), want)
+    finally:
+        g.close()
