@@ -15,9 +15,11 @@ Python API (numpy in, numpy out):
     abs_prefix(dtype, x, inclusive=True)           -> np.ndarray (float64)
     abs_segprefix(dtype, x, offsets, inclusive=True)
     bf16_to_double(bits)                           -> float
-op in {"add", "max"}; dtype in {"i32", "f32", "bf16"}; bf16 data are uint16
-bit patterns.  Output dtype: i32 add/max -> int32, f32/bf16 add -> float64
-(the FP64 reference), f32 max -> float32, bf16 max -> uint16 bits.
+op in {"add", "max"}; dtype in {"i32", "f32", "bf16", "i64", "f64"}; bf16
+data are uint16 bit patterns.  Output dtype: i32 add/max -> int32, f32/bf16
+add -> float64 (the FP64 reference), f32 max -> float32, bf16 max -> uint16
+bits, i64 add/max -> int64, f64 add -> float64 (double-double sum rounded
+to double), f64 max -> float64 (selected element's bits).
 """
 import ctypes
 import os
@@ -27,8 +29,9 @@ import numpy as np
 from . import build as _build
 
 _OPS = {"add": 0, "max": 1}
-_DTYPES = {"i32": 0, "f32": 1, "bf16": 2}
-_IN_NP = {"i32": np.int32, "f32": np.float32, "bf16": np.uint16}
+_DTYPES = {"i32": 0, "f32": 1, "bf16": 2, "i64": 3, "f64": 4}
+_IN_NP = {"i32": np.int32, "f32": np.float32, "bf16": np.uint16,
+          "i64": np.int64, "f64": np.float64}
 
 _lib = None
 
@@ -60,7 +63,9 @@ def _load():
 def out_dtype(op, dtype):
     """numpy dtype of the oracle's output for (op, dtype)."""
     if op == "add":
-        return np.int32 if dtype == "i32" else np.float64
+        if dtype in ("i32", "i64"):
+            return _IN_NP[dtype]
+        return np.float64
     return _IN_NP[dtype]
 
 
@@ -134,6 +139,10 @@ def identity(op, dtype):
         return 0
     if dtype == "i32":
         return np.iinfo(np.int32).min
+    if dtype == "i64":
+        return np.iinfo(np.int64).min
     if dtype == "f32":
         return np.float32(-np.inf)
+    if dtype == "f64":
+        return np.float64(-np.inf)
     return np.uint16(0xFF80)

@@ -91,13 +91,63 @@ static void scan_bf16_max(const uint16_t *x, uint16_t *y, int64_t n, int incl) {
     }
 }
 
+/* ---- int64 add: wrapping two's-complement sum ------------------------ */
+static void scan_i64_add(const int64_t *x, int64_t *y, int64_t n, int incl) {
+    uint64_t acc = 0; /* unsigned: overflow wraps mod 2^64, defined in C */
+    for (int64_t j = 0; j < n; ++j) {
+        if (!incl) y[j] = (int64_t)acc;
+        acc += (uint64_t)x[j];
+        if (incl) y[j] = (int64_t)acc;
+    }
+}
+
+/* ---- int64 max ----------------------------------------------------- */
+static void scan_i64_max(const int64_t *x, int64_t *y, int64_t n, int incl) {
+    int64_t acc = INT64_MIN;
+    for (int64_t j = 0; j < n; ++j) {
+        if (!incl) y[j] = acc;
+        if (x[j] > acc) acc = x[j];
+        if (incl) y[j] = acc;
+    }
+}
+
+/* ---- double add: sequential double-double accumulation --------------- */
+static void scan_f64_add(const double *x, double *y, int64_t n, int incl) {
+    double hi = 0.0, lo = 0.0; /* the running sum is hi + lo */
+    for (int64_t j = 0; j < n; ++j) {
+        if (!incl) y[j] = hi + lo;
+        /* two-sum: s + e == hi + x_j exactly */
+        double s = hi + x[j];
+        double bb = s - hi;
+        double e = (hi - (s - bb)) + (x[j] - bb);
+        /* fold the error into lo, then renormalise (fast-two-sum, |s| >= |lo|) */
+        lo += e;
+        double t = s + lo;
+        lo = lo - (t - s);
+        hi = t;
+        if (incl) y[j] = hi + lo;
+    }
+}
+
+/* ---- double max: first occurrence of the maximum -------------------- */
+static void scan_f64_max(const double *x, double *y, int64_t n, int incl) {
+    double acc = -INFINITY;
+    for (int64_t j = 0; j < n; ++j) {
+        if (!incl) y[j] = acc;
+        if (x[j] > acc) acc = x[j]; /* strict: a tie keeps the earlier bits */
+        if (incl) y[j] = acc;
+    }
+}
+
 static int out_size(int op, int dtype) {
     if (op == ORACLE_OP_ADD) {
         if (dtype == ORACLE_I32) return 4;
         if (dtype == ORACLE_F32 || dtype == ORACLE_BF16) return 8;
+        if (dtype == ORACLE_I64 || dtype == ORACLE_F64) return 8;
     } else if (op == ORACLE_OP_MAX) {
         if (dtype == ORACLE_I32 || dtype == ORACLE_F32) return 4;
         if (dtype == ORACLE_BF16) return 2;
+        if (dtype == ORACLE_I64 || dtype == ORACLE_F64) return 8;
     }
     return 0;
 }
@@ -105,6 +155,7 @@ static int out_size(int op, int dtype) {
 static int in_size(int dtype) {
     if (dtype == ORACLE_I32 || dtype == ORACLE_F32) return 4;
     if (dtype == ORACLE_BF16) return 2;
+    if (dtype == ORACLE_I64 || dtype == ORACLE_F64) return 8;
     return 0;
 }
 
@@ -122,8 +173,16 @@ int oracle_scan(int op, int dtype, const void *x, void *y, int64_t n,
         scan_f32_max((const float *)x, (float *)y, n, incl);
     else if (op == ORACLE_OP_ADD && dtype == ORACLE_BF16)
         scan_bf16_add((const uint16_t *)x, (double *)y, n, incl);
-    else
+    else if (op == ORACLE_OP_MAX && dtype == ORACLE_BF16)
         scan_bf16_max((const uint16_t *)x, (uint16_t *)y, n, incl);
+    else if (op == ORACLE_OP_ADD && dtype == ORACLE_I64)
+        scan_i64_add((const int64_t *)x, (int64_t *)y, n, incl);
+    else if (op == ORACLE_OP_MAX && dtype == ORACLE_I64)
+        scan_i64_max((const int64_t *)x, (int64_t *)y, n, incl);
+    else if (op == ORACLE_OP_ADD && dtype == ORACLE_F64)
+        scan_f64_add((const double *)x, (double *)y, n, incl);
+    else
+        scan_f64_max((const double *)x, (double *)y, n, incl);
     return 0;
 }
 
@@ -153,6 +212,8 @@ int oracle_abs_prefix(int dtype, const void *x, double *s, int64_t n,
             v = oracle_bf16_to_double(((const uint16_t *)x)[j]);
         else if (dtype == ORACLE_I32)
             v = (double)((const int32_t *)x)[j];
+        else if (dtype == ORACLE_F64)
+            v = ((const double *)x)[j];
         else
             return -1;
         if (!inclusive) s[j] = acc;

@@ -15,10 +15,16 @@
  *               int32 addition.
  *   fp32/bf16 add : every input converted exactly to double and accumulated
  *               sequentially in double; the double is the reference value.
+ *   int64 add : accumulated in 64-bit unsigned arithmetic (wrap mod 2^64).
+ *   double add : accumulated sequentially in double-double arithmetic (a
+ *               (hi, lo) pair updated with Knuth's two-sum, TAOCP vol. 2,
+ *               4.2.2, and renormalised with Dekker's fast-two-sum), so the
+ *               running sum carries ~106 bits; the reference value is
+ *               hi + lo rounded to double.
  *   max       : exact; ties keep the EARLIER element (result bits are those of
- *               the first occurrence of the maximum).  Identity INT32_MIN for
- *               int32, -infinity for floats.  NaN inputs are outside the
- *               contract.
+ *               the first occurrence of the maximum).  Identity INT32_MIN /
+ *               INT64_MIN for integers, -infinity for floats.  NaN inputs
+ *               are outside the contract.
  *   bf16      : a bf16 value is the upper 16 bits of an IEEE binary32, so the
  *               decode is exact (bits << 16).
  *
@@ -40,6 +46,8 @@ extern "C" {
 #define ORACLE_I32  0
 #define ORACLE_F32  1
 #define ORACLE_BF16 2
+#define ORACLE_I64  3
+#define ORACLE_F64  4
 
 /* Returns 0 on success, -1 on an unknown (op, dtype) or n < 0.
  * Output element type:
@@ -48,7 +56,11 @@ extern "C" {
  *   (ADD, BF16) -> double   (FP64 reference value)
  *   (MAX, I32)  -> int32_t
  *   (MAX, F32)  -> float    (bits of the selected element)
- *   (MAX, BF16) -> uint16_t (bits of the selected element)            */
+ *   (MAX, BF16) -> uint16_t (bits of the selected element)
+ *   (ADD, I64)  -> int64_t
+ *   (ADD, F64)  -> double   (double-double sum rounded to double)
+ *   (MAX, I64)  -> int64_t
+ *   (MAX, F64)  -> double   (bits of the selected element)            */
 int oracle_scan(int op, int dtype, const void *x, void *y, int64_t n,
                 int inclusive);
 

@@ -342,3 +342,108 @@ def test_abs_prefix_properties(oracle_mod):
     ss = oracle_mod.abs_segprefix("f32", x, off)
     np.testing.assert_array_equal(ss[:10], s[:10])
     np.testing.assert_array_equal(ss[10:], oracle_mod.abs_prefix("f32", x[10:]))
+
+
+# ------------------------------------------------------ int64 and double
+def test_golden_i64_wrap(oracle_mod):
+    g = golden("scan_i64_wrap.txt")
+    x = np.array([int(v) for v in g["x"]], dtype=np.int64)
+    for key, incl in (("add_inclusive", True), ("add_exclusive", False)):
+        want = np.array([int(v) for v in g[key]], dtype=np.int64)
+        assert np.array_equal(oracle_mod.scan("add", "i64", x, incl), want)
+    x2 = np.array([int(v) for v in g["x2"]], dtype=np.int64)
+    want2 = np.array([int(v) for v in g["add_inclusive2"]], dtype=np.int64)
+    assert np.array_equal(oracle_mod.scan("add", "i64", x2, True), want2)
+
+
+def test_golden_f64_add_double_double(oracle_mod):
+    g = golden("scan_f64_add_dd.txt")
+    for xk, keys in (("x", (("add_inclusive", True), ("add_exclusive", False))),
+                     ("x2", (("add_inclusive2", True),))):
+        x = np.array([float(v) for v in g[xk]], dtype=np.float64)
+        for key, incl in keys:
+            want = np.array([float(v) for v in g[key]], dtype=np.float64)
+            got = oracle_mod.scan("add", "f64", x, incl)
+            assert np.array_equal(got, want), (xk, key, got, want)
+
+
+@pytest.mark.parametrize("n", [1, 2, 17, 64])
+def test_brute_force_int64_mod_2_64(oracle_mod, n):
+    rng = np.random.default_rng(640 + n)
+    x = rng.integers(-2**63, 2**63, size=n, dtype=np.int64)
+    for incl in (True, False):
+        want = []
+        for j in range(n):
+            acc = sum(int(v) for v in x[: j + 1 if incl else j]) % 2**64
+            want.append(acc - 2**64 if acc >= 2**63 else acc)
+        assert np.array_equal(oracle_mod.scan("add", "i64", x, incl),
+                              np.array(want, dtype=np.int64))
+
+
+@pytest.mark.parametrize("n", [1, 3, 40, 200])
+def test_brute_force_f64_add_vs_exact_rationals(oracle_mod, n):
+    """Each output is the exact prefix sum (Python Fractions) rounded to
+    double, to within one unit in the last place; magnitudes spread over
+    2^-40 .. 2^40 with both signs so that double accumulation would lose
+    many digits."""
+    from fractions import Fraction
+    rng = np.random.default_rng(641 + n)
+    x = (rng.choice([-1.0, 1.0], size=n) *
+         np.ldexp(rng.random(n) + 0.5, rng.integers(-40, 41, size=n)))
+    for incl in (True, False):
+        got = oracle_mod.scan("add", "f64", x, incl)
+        acc = Fraction(0)
+        for j in range(n):
+            if incl:
+                acc += Fraction(float(x[j]))
+            exact = float(acc)
+            tol = np.spacing(abs(exact)) if exact != 0 else 0.0
+            assert abs(got[j] - exact) <= tol, (j, got[j], exact)
+            if not incl:
+                acc += Fraction(float(x[j]))
+
+
+@pytest.mark.parametrize("dtype", ["i64", "f64"])
+def test_brute_force_max_64bit_first_occurrence(oracle_mod, dtype):
+    rng = np.random.default_rng(642)
+    if dtype == "i64":
+        x = rng.integers(-5, 5, size=50, dtype=np.int64) * (2**40)
+    else:
+        x = rng.integers(-3, 3, size=50).astype(np.float64)
+        x[rng.random(50) < 0.3] = 0.0
+        x[rng.random(50) < 0.3] = -0.0
+    ident = oracle_mod.identity("max", dtype)
+    for incl in (True, False):
+        got = oracle_mod.scan("max", dtype, x, incl)
+        for j in range(50):
+            best = ident
+            for i in range(j + 1 if incl else j):
+                if x[i] > best:
+                    best = x[i]
+            assert np.array(got[j]).tobytes() == np.array(
+                best, dtype=x.dtype).tobytes(), (j, got[j], best)
+
+
+@pytest.mark.parametrize("op,dtype", [("add", "i64"), ("max", "i64"),
+                                      ("add", "f64"), ("max", "f64")])
+def test_inclusive_exclusive_relation_64bit(oracle_mod, op, dtype):
+    rng = np.random.default_rng(643)
+    if dtype == "i64":
+        x = rng.integers(-2**40, 2**40, size=300, dtype=np.int64)
+    else:
+        x = rng.standard_normal(300) * 1e3
+    inc = oracle_mod.scan(op, dtype, x, True)
+    exc = oracle_mod.scan(op, dtype, x, False)
+    assert np.array_equal(exc[1:], inc[:-1])
+    if op == "max":
+        assert exc[0] == oracle_mod.identity(op, dtype)
+    else:
+        assert exc[0] == 0
+
+
+def test_abs_prefix_f64(oracle_mod):
+    x = np.array([1.5, -2.25, 0.0, -0.125])
+    assert np.array_equal(oracle_mod.abs_prefix("f64", x, True),
+                          [1.5, 3.75, 3.75, 3.875])
+    assert np.array_equal(oracle_mod.abs_prefix("f64", x, False),
+                          [0.0, 1.5, 3.75, 3.75])
