@@ -51,7 +51,16 @@ extern "C" {
 
 typedef enum { LSCAN_ADD = 0, LSCAN_MAX = 1 } lscan_op;
 
-typedef enum { LSCAN_I32 = 0, LSCAN_F32 = 1, LSCAN_BF16 = 2 } lscan_dtype;
+/* LSCAN_I64 and LSCAN_F64 are the paper's other two types (Section 5,
+ * Table 2): int64 add wraps mod 2^64; double add runs in double in the tile
+ * and in the carry chain (precision DEFAULT or F64_CARRY only). */
+typedef enum {
+    LSCAN_I32 = 0,
+    LSCAN_F32 = 1,
+    LSCAN_BF16 = 2,
+    LSCAN_I64 = 3,
+    LSCAN_F64 = 4
+} lscan_dtype;
 
 typedef enum {
     LSCAN_OK = 0,
@@ -226,7 +235,9 @@ lscan_status lscan_server_free(lscan_server *srv, void *dptr);
 /* x: device input (any element-aligned address; 16-byte aligned inputs and
  * outputs take the bulk-copy path).  y: device output, or NULL to have the
  * server allocate it from the pool at admission (reported in the stats and
- * kept until lscan_server_release).  Returns at once with a ticket. */
+ * kept until lscan_server_release).  Returns at once with a ticket.  One
+ * request holds at most 512 MiB of input (65536 tiles of 8 KiB); larger n
+ * returns LSCAN_ERR_INVALID. */
 lscan_status lscan_server_submit(lscan_server *srv, lscan_op op,
                                  lscan_dtype dtype, int inclusive,
                                  const void *x, void *y, int64_t n,

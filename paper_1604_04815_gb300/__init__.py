@@ -15,9 +15,9 @@ from . import _lib
 from ._lib import LscanError, load  # noqa: F401
 
 _DT = {torch.int32: _lib.LSCAN_I32, torch.float32: _lib.LSCAN_F32,
-       torch.bfloat16: _lib.LSCAN_BF16}
-_TORCH_DT = {_lib.LSCAN_I32: torch.int32, _lib.LSCAN_F32: torch.float32,
-             _lib.LSCAN_BF16: torch.bfloat16}
+       torch.bfloat16: _lib.LSCAN_BF16, torch.int64: _lib.LSCAN_I64,
+       torch.float64: _lib.LSCAN_F64}
+_TORCH_DT = {v: k for k, v in _DT.items()}
 _OPS = {"add": _lib.LSCAN_ADD, "max": _lib.LSCAN_MAX}
 _PREC = {None: 0, "default": 0, "f32": 1, "plain": 1, "f64": 2,
          "compensated": 3, "comp": 3}

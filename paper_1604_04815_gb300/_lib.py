@@ -11,7 +11,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "liblscan.so")
 
 LSCAN_ADD, LSCAN_MAX = 0, 1
-LSCAN_I32, LSCAN_F32, LSCAN_BF16 = 0, 1, 2
+LSCAN_I32, LSCAN_F32, LSCAN_BF16, LSCAN_I64, LSCAN_F64 = 0, 1, 2, 3, 4
 LSCAN_OK = 0
 LSCAN_ERR_INVALID = 1
 LSCAN_ERR_UNSUPPORTED = 2

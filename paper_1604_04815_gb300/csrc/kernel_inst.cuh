@@ -8,7 +8,7 @@ namespace lscan {
 // Tile configurations by input element size: <items/thread, consumer warps,
 // ring stages, output staging buffers, CTAs per SM the registers must fit>.
 // Variant 0 (G) loads straight from global memory; C1..C3 stream 8, 16 and
-// 32 KiB input tiles through the bulk-copy ring.
+// 32 KiB input tiles through the bulk-copy ring (for every element size).
 template <int ISZ>
 struct Cfgs;
 template <>
@@ -17,6 +17,13 @@ struct Cfgs<4> {
     using C1 = TileCfg<8, 8, 4, 1, 3>;
     using C2 = TileCfg<16, 8, 3, 1, 3>;
     using C3 = TileCfg<16, 16, 2, 1, 2>;
+};
+template <>
+struct Cfgs<8> {
+    using G = TileCfg<4, 8, 4, 1, 3>;
+    using C1 = TileCfg<4, 8, 4, 1, 3>;
+    using C2 = TileCfg<8, 8, 3, 1, 3>;
+    using C3 = TileCfg<8, 16, 2, 1, 2>;
 };
 template <>
 struct Cfgs<2> {

@@ -250,6 +250,88 @@ struct KFAddComp {
     }
 };
 
+// 64-bit integers and doubles (the paper's other two types, Table 2)
+struct KI64Add {
+    static constexpr bool kTieOrdered = false;
+    using In = int64_t;
+    using Out = int64_t;
+    using Acc = uint64_t;  // wrapping mod 2^64
+    using Car = uint64_t;
+    using CarA = uint64_t;
+    __device__ static Acc ident() { return 0ull; }
+    __device__ static Acc load(In v) { return static_cast<uint64_t>(v); }
+    __device__ static Acc op(Acc a, Acc b) { return a + b; }
+    __device__ static Car cident() { return 0ull; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return a + b; }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return c + tb; }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) { return static_cast<int64_t>(b + v); }
+    __device__ static Car car_of_out(Out o) { return static_cast<uint64_t>(o); }
+};
+
+struct KI64Max {
+    static constexpr bool kTieOrdered = false;  // equal ints have equal bits
+    using In = int64_t;
+    using Out = int64_t;
+    using Acc = int64_t;
+    using Car = int64_t;
+    using CarA = int64_t;
+    __device__ static Acc ident() { return INT64_MIN; }
+    __device__ static Acc load(In v) { return v; }
+    __device__ static Acc op(Acc a, Acc b) { return max_keep_left(a, b); }
+    __device__ static Car cident() { return INT64_MIN; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return max_keep_left(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) { return max_keep_left(b, v); }
+    __device__ static Car car_of_out(Out o) { return o; }
+};
+
+struct KF64Max {
+    static constexpr bool kTieOrdered = true;  // +0 / -0 compare equal
+    using In = double;
+    using Out = double;
+    using Acc = double;
+    using Car = double;
+    using CarA = double;
+    __device__ static Acc ident() { return __longlong_as_double(0xfff0000000000000ll); }
+    __device__ static Acc load(In v) { return v; }
+    __device__ static Acc op(Acc a, Acc b) { return max_keep_left(a, b); }
+    __device__ static Car cident() { return ident(); }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return max_keep_left(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) { return max_keep_left(b, v); }
+    __device__ static Car car_of_out(Out o) { return o; }
+};
+
+// double add: double in tile and in the carry chain
+struct KF64Add {
+    static constexpr bool kTieOrdered = false;
+    using In = double;
+    using Out = double;
+    using Acc = double;
+    using Car = double;
+    using CarA = double;
+    __device__ static Acc ident() { return 0.0; }
+    __device__ static Acc load(In v) { return v; }
+    __device__ static Acc op(Acc a, Acc b) { return __dadd_rn(a, b); }
+    __device__ static Car cident() { return 0.0; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return __dadd_rn(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return __dadd_rn(c, tb); }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA b, Acc v) { return __dadd_rn(b, v); }
+    __device__ static Car car_of_out(Out o) { return o; }
+};
+
 // ------------------------------------------------- kind ids (host + device)
 enum KindId : int {
     KIND_I32_ADD = 0,
@@ -265,6 +347,10 @@ enum KindId : int {
     KIND_BF16_ADD_PLAIN_BF16,
     KIND_BF16_ADD_F64_BF16,
     KIND_BF16_ADD_COMP_BF16,
+    KIND_I64_ADD,
+    KIND_I64_MAX,
+    KIND_F64_MAX,
+    KIND_F64_ADD,
     KIND_COUNT
 };
 

@@ -38,6 +38,10 @@ void register_bf16_add_comp_f32();
 void register_bf16_add_plain_bf16();
 void register_bf16_add_f64_bf16();
 void register_bf16_add_comp_bf16();
+void register_i64_add();
+void register_i64_max();
+void register_f64_max();
+void register_f64_add();
 
 void register_all_kernels() {
     register_i32_add();
@@ -53,6 +57,10 @@ void register_all_kernels() {
     register_bf16_add_plain_bf16();
     register_bf16_add_f64_bf16();
     register_bf16_add_comp_bf16();
+    register_i64_add();
+    register_i64_max();
+    register_f64_max();
+    register_f64_add();
 }
 
 namespace {
@@ -101,10 +109,18 @@ int select_kind(int op, int dtype, int out_dtype, int precision) {
         if (dtype == LSCAN_I32) return KIND_I32_MAX;
         if (dtype == LSCAN_F32) return KIND_F32_MAX;
         if (dtype == LSCAN_BF16) return KIND_BF16_MAX;
+        if (dtype == LSCAN_I64) return KIND_I64_MAX;
+        if (dtype == LSCAN_F64) return KIND_F64_MAX;
         return -1;
     }
     if (op != LSCAN_ADD) return -1;
     if (dtype == LSCAN_I32) return out_dtype == LSCAN_I32 ? KIND_I32_ADD : -1;
+    if (dtype == LSCAN_I64) return out_dtype == LSCAN_I64 ? KIND_I64_ADD : -1;
+    if (dtype == LSCAN_F64) {
+        // one path: double in tile and in the carry chain
+        const bool ok = precision == LSCAN_PREC_DEFAULT || precision == LSCAN_PREC_F64_CARRY;
+        return (out_dtype == LSCAN_F64 && ok) ? KIND_F64_ADD : -1;
+    }
     int prec = precision == LSCAN_PREC_DEFAULT ? LSCAN_PREC_F64_CARRY : precision;
     if (prec < LSCAN_PREC_F32_CARRY || prec > LSCAN_PREC_COMPENSATED) return -1;
     const int pi = prec - LSCAN_PREC_F32_CARRY;  // 0 plain, 1 f64, 2 comp
@@ -122,6 +138,7 @@ int select_kind(int op, int dtype, int out_dtype, int precision) {
 int dtype_size(int dt) {
     if (dt == LSCAN_I32 || dt == LSCAN_F32) return 4;
     if (dt == LSCAN_BF16) return 2;
+    if (dt == LSCAN_I64 || dt == LSCAN_F64) return 8;
     return 0;
 }
 
@@ -256,7 +273,7 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     if (isz == 0 || (op != LSCAN_ADD && op != LSCAN_MAX)) return LSCAN_ERR_INVALID;
     int out_dtype = dtype;
     if (op == LSCAN_ADD && dtype == LSCAN_BF16) out_dtype = LSCAN_F32;
-    if (opts && opts->out_dtype > 0 && opts->out_dtype <= LSCAN_BF16)
+    if (opts && opts->out_dtype > 0 && opts->out_dtype <= LSCAN_F64)
         out_dtype = opts->out_dtype;
     const int prec = opts ? opts->precision : LSCAN_PREC_DEFAULT;
     const int kind = select_kind(op, dtype, out_dtype, prec);
@@ -458,7 +475,9 @@ lscan_status lscan_config_info(int32_t config, lscan_dtype dtype, int32_t *items
     if (config < 0 || config > kNumTmaCfg) return LSCAN_ERR_INVALID;
     int kind = dtype == LSCAN_I32 ? KIND_I32_ADD
                : dtype == LSCAN_F32 ? KIND_F32_MAX
-               : dtype == LSCAN_BF16 ? KIND_BF16_MAX : -1;
+               : dtype == LSCAN_BF16 ? KIND_BF16_MAX
+               : dtype == LSCAN_I64 ? KIND_I64_ADD
+               : dtype == LSCAN_F64 ? KIND_F64_MAX : -1;
     if (kind < 0) return LSCAN_ERR_INVALID;
     const KernelEntry &e = g_kernels[kind][MODE_SINGLE][config];
     if (items) *items = e.items;

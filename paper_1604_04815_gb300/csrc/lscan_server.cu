@@ -50,7 +50,7 @@ namespace {
 constexpr size_t kPoolAlign = 256;
 constexpr int64_t kMaxBatchTiles = 65536;   // ~1 GiB of 16 KiB tiles per launch
 constexpr int kSlotsPerStream = 2;          // a second batch queues behind the first
-constexpr int64_t kMinTile = 2048;          // smallest tile of any config
+constexpr int64_t kMinTileBytes = 8192;     // smallest input tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
 
 double now_us(std::chrono::steady_clock::time_point t0) {
@@ -546,7 +546,8 @@ static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtyp
         }
         const size_t need = y ? 0 : static_cast<size_t>(n) * osz;
         // one request must fit one launch's status words
-        if ((n + kMinTile - 1) / kMinTile > kMaxBatchTiles) {
+        const int64_t min_tile = kMinTileBytes / isz;  // elements
+        if ((n + min_tile - 1) / min_tile > kMaxBatchTiles) {
             delete r;
             return LSCAN_ERR_INVALID;
         }

@@ -168,11 +168,18 @@ __device__ __forceinline__ void unpack_chunks(const uint4 (&t)[C], E (&e)[ITEMS]
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         const uint32_t w[4] = {t[c].x, t[c].y, t[c].z, t[c].w};
-        if constexpr (sizeof(E) == 4) {
+        if constexpr (sizeof(E) == 8) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint64_t d = static_cast<uint64_t>(w[2 * q]) |
+                                   (static_cast<uint64_t>(w[2 * q + 1]) << 32);
+                memcpy(&e[2 * c + q], &d, 8);
+            }
+        } else if constexpr (sizeof(E) == 4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) e[4 * c + q] = word_to<E>(w[q]);
         } else {
-            static_assert(sizeof(E) == 2, "2- or 4-byte elements");
+            static_assert(sizeof(E) == 2, "2-, 4- or 8-byte elements");
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 e[8 * c + 2 * q] = static_cast<E>(w[q] & 0xffffu);
@@ -188,7 +195,15 @@ __device__ __forceinline__ void pack_chunks(const E (&e)[ITEMS], uint4 (&t)[C]) 
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         uint32_t w[4];
-        if constexpr (sizeof(E) == 4) {
+        if constexpr (sizeof(E) == 8) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                uint64_t d;
+                memcpy(&d, &e[2 * c + q], 8);
+                w[2 * q] = static_cast<uint32_t>(d);
+                w[2 * q + 1] = static_cast<uint32_t>(d >> 32);
+            }
+        } else if constexpr (sizeof(E) == 4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) w[q] = to_word(e[4 * c + q]);
         } else {

@@ -108,11 +108,23 @@ def batched(dtype, n_seg=4096, max_log2=20, seed=SEEDS["batched"]):
 
 
 def random_array(dtype, n, rng, kind="uniform"):
-    """Generic test input of a given dtype (bf16 as uint16 bits)."""
+    """Generic test input of a given dtype (bf16 as uint16 bits; i64/f64 for
+    the 64-bit kinds)."""
     if dtype == "i32":
         if kind == "full":
             return rng.integers(-(1 << 31), 1 << 31, size=n, dtype=np.int32)
         return rng.integers(-1000, 1001, size=n, dtype=np.int32)
+    if dtype == "i64":
+        if kind == "full":
+            return rng.integers(-(1 << 63), (1 << 63) - 1, size=n, dtype=np.int64,
+                                endpoint=True)
+        return rng.integers(-(1 << 40), (1 << 40) + 1, size=n, dtype=np.int64)
+    if dtype == "f64":
+        if kind == "intval":
+            return rng.integers(-8, 9, size=n).astype(np.float64)
+        if kind == "signed":
+            return rng.random(size=n) * 2 - 1
+        return rng.random(size=n)
     if kind == "intval":
         # integer-valued floats: fp32 prefixes stay exact below 2^24
         f = rng.integers(-8, 9, size=n).astype(np.float32)

@@ -7,8 +7,10 @@ import oracle
 import paper_1604_04815_gb300 as lscan
 from paper_1604_04815_gb300 import _lib
 
-DTYPES = {"i32": torch.int32, "f32": torch.float32, "bf16": torch.bfloat16}
-LDT = {"i32": _lib.LSCAN_I32, "f32": _lib.LSCAN_F32, "bf16": _lib.LSCAN_BF16}
+DTYPES = {"i32": torch.int32, "f32": torch.float32, "bf16": torch.bfloat16,
+          "i64": torch.int64, "f64": torch.float64}
+LDT = {"i32": _lib.LSCAN_I32, "f32": _lib.LSCAN_F32, "bf16": _lib.LSCAN_BF16,
+       "i64": _lib.LSCAN_I64, "f64": _lib.LSCAN_F64}
 LOP = {"add": _lib.LSCAN_ADD, "max": _lib.LSCAN_MAX}
 
 # device wait limit used by the GPU tests (a hang-free failure in ~0.2 s)
@@ -16,6 +18,9 @@ TEST_WAIT_NS = 200_000_000
 
 # |y_j - ref_j| <= c * S_j for float add, per precision path
 BOUND = {"plain": 1e-5, "f64": 1e-5, "comp": 2.5e-7}
+# double add (double in tile and carry): |y_j - ref_j| <= 1e-12 * S_j
+# (~9000 units of roundoff; see the readings of the paper in the design doc)
+BOUND_F64_ADD = 1e-12
 PREC_CODE = {"plain": _lib.LSCAN_PREC_F32_CARRY, "f64": _lib.LSCAN_PREC_F64_CARRY,
              "comp": _lib.LSCAN_PREC_COMPENSATED}
 
@@ -74,9 +79,11 @@ def assert_matches(op, dtype, x_np, got, inclusive=True, prec="f64",
         want = oracle.scan(op, dtype, x_np, inclusive)
     else:
         want = oracle.segscan(op, dtype, x_np, offsets, inclusive)
-    if op == "max" or dtype == "i32":
+    if op == "max" or dtype in ("i32", "i64"):
         if dtype == "f32":
             got_b, want_b = got.view(np.uint32), want.view(np.uint32)
+        elif dtype == "f64":
+            got_b, want_b = got.view(np.uint64), want.view(np.uint64)
         else:
             got_b, want_b = got, want
         if not np.array_equal(got_b, want_b):
@@ -97,6 +104,8 @@ def assert_matches(op, dtype, x_np, got, inclusive=True, prec="f64",
         g = got.astype(np.float64)
     err = np.abs(g - want)
     c = BOUND[prec] if bound is None else bound
+    if dtype == "f64" and bound is None:
+        c = BOUND_F64_ADD
     lim = c * s
     if out_bf16:
         lim = lim + 2.0 ** -8 * np.abs(want)

@@ -31,6 +31,11 @@ KINDS = [
     ("add", "bf16", "plain", True),
     ("add", "bf16", "f64", True),
     ("add", "bf16", "comp", True),
+    # the paper's 64-bit types (Table 2)
+    ("add", "i64", None, False),
+    ("max", "i64", None, False),
+    ("max", "f64", None, False),
+    ("add", "f64", None, False),
 ]
 KIND_IDS = [f"{o}-{d}-{p or 'exact'}{'-bf16out' if b else ''}"
             for o, d, p, b in KINDS]
@@ -48,8 +53,8 @@ def _built():
 
 def _input(op, dtype, n, seed):
     rng = np.random.default_rng(seed)
-    if dtype == "i32":
-        return random_array("i32", n, rng, kind="full" if op == "max" or
+    if dtype in ("i32", "i64"):
+        return random_array(dtype, n, rng, kind="full" if op == "max" or
                             seed % 2 else "uniform")
     return random_array(dtype, n, rng, kind="signed")
 
@@ -120,9 +125,8 @@ def test_in_place(kind, config):
 
 
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
-@pytest.mark.parametrize("kind", [KINDS[0], KINDS[1], KINDS[5], KINDS[9]],
-                         ids=[KIND_IDS[0], KIND_IDS[1], KIND_IDS[5],
-                              KIND_IDS[9]])
+@pytest.mark.parametrize("kind", [KINDS[i] for i in (0, 1, 5, 9, 13, 16)],
+                         ids=[KIND_IDS[i] for i in (0, 1, 5, 9, 13, 16)])
 def test_chained_carry(kind, inclusive):
     """The paper's neighbour-to-neighbour hand-off (Algorithm 4)."""
     op, dtype, prec, ob = kind
@@ -191,9 +195,10 @@ def _offsets(kind, rng):
                                      "empty_tail", "loguniform",
                                      "tile_aligned"])
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
-@pytest.mark.parametrize("kind", [KINDS[0], KINDS[1], KINDS[2], KINDS[3],
-                                  KINDS[5], KINDS[6], KINDS[8]],
-                         ids=[KIND_IDS[i] for i in (0, 1, 2, 3, 5, 6, 8)])
+@pytest.mark.parametrize("kind", [KINDS[i] for i in
+                                  (0, 1, 2, 3, 5, 6, 8, 13, 14, 15, 16)],
+                         ids=[KIND_IDS[i] for i in
+                              (0, 1, 2, 3, 5, 6, 8, 13, 14, 15, 16)])
 def test_batched(kind, inclusive, pattern):
     op, dtype, prec, ob = kind
     rng = np.random.default_rng(sum(map(ord, pattern)))
@@ -367,13 +372,17 @@ def _carry_value(op, dtype, ob, x, rng):
     for max, a value above part of the input."""
     if op == "add" and dtype == "i32":
         return np.int32(rng.integers(-2**31, 2**31))
+    if op == "add" and dtype == "i64":
+        return np.int64(rng.integers(-2**63, 2**63 - 1, endpoint=True))
+    if op == "add" and dtype == "f64":
+        return np.float64(rng.choice([-1.0, 1.0]) * rng.random() * 100.0)
     if op == "max":
         if dtype == "bf16":
             from paper_1604_04815_gb300.workloads import bf16_bits_to_f32
             v = np.sort(bf16_bits_to_f32(x))[len(x) * 3 // 5] if len(x) else 0.0
             return np.uint16(np.float32(v).view(np.uint32) >> 16)  # exact
-        if dtype == "i32":
-            return np.int32(np.sort(x)[len(x) * 3 // 5])
+        if dtype in ("i32", "i64", "f64"):
+            return np.sort(x)[len(x) * 3 // 5]
         return np.float32(np.sort(x)[len(x) * 3 // 5])
     v = np.float32(rng.choice([-1.0, 1.0]) * rng.random() * 100.0)
     if ob:
@@ -388,6 +397,8 @@ def _expect_with_carry(op, dtype, ob, want, c):
     if op == "add" and dtype == "i32":
         return ((want.astype(np.int64) + int(c)) & 0xFFFFFFFF).astype(
             np.uint32).view(np.int32)
+    if op == "add" and dtype == "i64":  # mod 2^64
+        return (want.view(np.uint64) + np.uint64(int(c) % 2**64)).view(np.int64)
     if op == "max":
         if dtype == "bf16":
             wv = bf16_bits_to_f32(want)
@@ -404,14 +415,12 @@ def _expect_with_carry(op, dtype, ob, want, c):
 def test_carry_in(kind, inclusive):
     """y = carry_in (+) scan(x): a shard of a longer scan."""
     import oracle
-    from gpu_util import BOUND
+    from gpu_util import BOUND, BOUND_F64_ADD, DTYPES
     from paper_1604_04815_gb300.workloads import bf16_bits_to_f32
     op, dtype, prec, ob = kind
     rng = np.random.default_rng(77)
     odt = torch.bfloat16 if ob else (
-        torch.float32 if (op == "add" and dtype == "bf16") else
-        {"i32": torch.int32, "f32": torch.float32,
-         "bf16": torch.bfloat16}[dtype])
+        torch.float32 if (op == "add" and dtype == "bf16") else DTYPES[dtype])
     tile = _tile(2, dtype)
     for config, carry in ((0, 0), (2, 0), (2, _lib.LSCAN_CARRY_CHAINED)):
         for i, n in enumerate([1, 33, tile + 1, 7 * tile + 123]):
@@ -434,16 +443,18 @@ def test_carry_in(kind, inclusive):
             assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
             got = to_host(y)
             want = oracle.scan(op, dtype, x, inclusive)
-            if op == "max" or dtype == "i32":
+            if op == "max" or dtype in ("i32", "i64"):
                 exp = _expect_with_carry(op, dtype, ob, want, c)
-                gb = got.view(np.uint32) if dtype == "f32" else got
-                eb = exp.view(np.uint32) if dtype == "f32" else exp
+                bits = {"f32": np.uint32, "f64": np.uint64}.get(dtype)
+                gb = got.view(bits) if bits else got
+                eb = exp.view(bits) if bits else exp
                 assert np.array_equal(gb, eb), (config, carry, n)
             else:
                 exp, ac = _expect_with_carry(op, dtype, ob, want, c)
                 sj = oracle.abs_prefix(dtype, x, inclusive) + ac
                 g = (bf16_bits_to_f32(got) if ob else got).astype(np.float64)
-                lim = BOUND[prec] * sj + (2.0 ** -8 * np.abs(exp) if ob else 0)
+                c_rel = BOUND_F64_ADD if dtype == "f64" else BOUND[prec]
+                lim = c_rel * sj + (2.0 ** -8 * np.abs(exp) if ob else 0)
                 assert np.all(np.abs(g - exp) <= lim), (config, carry, n)
 
 

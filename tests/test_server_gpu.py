@@ -16,7 +16,8 @@ from paper_1604_04815_gb300.workloads import random_array
 
 pytestmark = pytest.mark.gpu
 
-TDT = {"i32": torch.int32, "f32": torch.float32, "bf16": torch.bfloat16}
+TDT = {"i32": torch.int32, "f32": torch.float32, "bf16": torch.bfloat16,
+       "i64": torch.int64, "f64": torch.float64}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -34,10 +35,11 @@ def _mix(n_req, seed, max_log2=18):
         if i % 17 == 0:
             n = 0 if i % 34 == 0 else 1
         d = rng.random()
-        dtype = "i32" if d < 0.5 else ("f32" if d < 0.85 else "bf16")
+        dtype = ("i32" if d < 0.45 else "f32" if d < 0.75 else
+                 "bf16" if d < 0.9 else "i64" if d < 0.95 else "f64")
         op = "add" if rng.random() < 0.5 else "max"
         incl = bool(rng.random() < 0.8)
-        kind = "full" if dtype == "i32" else "signed"
+        kind = "full" if dtype in ("i32", "i64") else "signed"
         reqs.append(dict(n=n, dtype=dtype, op=op, incl=incl,
                          x=random_array(dtype, n, rng, kind=kind)))
     return reqs
@@ -78,13 +80,14 @@ def test_same_alone_and_in_the_mix():
             m = to_host(y)
             assert_matches(r["op"], r["dtype"], r["x"], a, r["incl"])
             assert_matches(r["op"], r["dtype"], r["x"], m, r["incl"])
-            if r["op"] == "max" or r["dtype"] == "i32":
+            if r["op"] == "max" or r["dtype"] in ("i32", "i64"):
                 assert np.array_equal(a.view(np.uint8), m.view(np.uint8))
             else:
                 import oracle
+                from gpu_util import BOUND_F64_ADD
                 s = oracle.abs_prefix(r["dtype"], r["x"], r["incl"])
-                assert np.all(np.abs(a.astype(np.float64) - m) <=
-                              2 * BOUND["f64"] * s)
+                c = BOUND_F64_ADD if r["dtype"] == "f64" else BOUND["f64"]
+                assert np.all(np.abs(a.astype(np.float64) - m) <= 2 * c * s)
     finally:
         srv.close()
 
