@@ -147,6 +147,8 @@ struct FloatOut<uint16_t> {
 template <class InT>
 struct KFMax {
     static constexpr bool kTieOrdered = true;  // +0 / -0 compare equal
+    // strict "greater" of the operator (tie-ordered folds; +0 == -0)
+    __device__ static bool gt(float a, float b) { return a > b; }
     using In = InT;
     using Out = InT;
     using Acc = float;
@@ -291,24 +293,35 @@ struct KI64Max {
     __device__ static Car car_of_out(Out o) { return o; }
 };
 
+// double max on order-preserving int64 keys: GB300's FP64 pipe is narrow,
+// and a key comparison runs on the integer ALUs.  key(bits) flips the
+// magnitude bits of negative values, so signed key order is the order of
+// the doubles, except that -0 (key -1) sits just below +0 (key 0); gt()
+// treats that one pair as equal, as the floating-point comparison does.
+// The mapping is an involution (key(key(b)) == b).  NaN is out of contract.
 struct KF64Max {
     static constexpr bool kTieOrdered = true;  // +0 / -0 compare equal
     using In = double;
     using Out = double;
-    using Acc = double;
-    using Car = double;
-    using CarA = double;
-    __device__ static Acc ident() { return __longlong_as_double(0xfff0000000000000ll); }
-    __device__ static Acc load(In v) { return v; }
-    __device__ static Acc op(Acc a, Acc b) { return max_keep_left(a, b); }
+    using Acc = int64_t;  // key
+    using Car = int64_t;
+    using CarA = int64_t;
+    __device__ static int64_t key(int64_t b) {
+        return b ^ static_cast<int64_t>(static_cast<uint64_t>(b >> 63) >> 1);
+    }
+    __device__ static bool gt(int64_t a, int64_t b) { return a > b && !(b == -1 && a == 0); }
+    __device__ static int64_t mx(int64_t a, int64_t b) { return gt(b, a) ? b : a; }
+    __device__ static Acc ident() { return key(static_cast<int64_t>(0xfff0000000000000ull)); }
+    __device__ static Acc load(In v) { return key(__double_as_longlong(v)); }
+    __device__ static Acc op(Acc a, Acc b) { return mx(a, b); }
     __device__ static Car cident() { return ident(); }
     __device__ static Car to_car(Acc a) { return a; }
-    __device__ static Car cop(Car a, Car b) { return max_keep_left(a, b); }
+    __device__ static Car cop(Car a, Car b) { return mx(a, b); }
     __device__ static CarA to_apply(Car c) { return c; }
-    __device__ static CarA base(CarA c, Acc tb) { return max_keep_left(c, tb); }
+    __device__ static CarA base(CarA c, Acc tb) { return mx(c, tb); }
     __device__ static CarA base_local(Acc tb) { return tb; }
-    __device__ static Out fin(CarA b, Acc v) { return max_keep_left(b, v); }
-    __device__ static Car car_of_out(Out o) { return o; }
+    __device__ static Out fin(CarA b, Acc v) { return __longlong_as_double(key(mx(b, v))); }
+    __device__ static Car car_of_out(Out o) { return load(o); }
 };
 
 // double add: double in tile and in the carry chain

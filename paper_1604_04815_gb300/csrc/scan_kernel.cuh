@@ -384,7 +384,7 @@ struct CarryFold {
     }
     __device__ void add(Car x, int64_t idx) {
         if constexpr (K::kTieOrdered) {
-            if (x > v || (!(v > x) && idx < i)) {
+            if (K::gt(x, v) || (!K::gt(v, x) && idx < i)) {
                 v = x;
                 i = idx;
             }
@@ -547,7 +547,7 @@ struct TileReduce {
     }
     __device__ void add(Acc x, int32_t idx) {
         if constexpr (K::kTieOrdered) {
-            if (x > v || (!(v > x) && idx < i)) {
+            if (K::gt(x, v) || (!K::gt(v, x) && idx < i)) {
                 v = x;
                 i = idx;
             }
@@ -558,7 +558,7 @@ struct TileReduce {
     // x comes after every element folded so far (a left fold)
     __device__ void add_in_order(Acc x, int32_t idx) {
         if constexpr (K::kTieOrdered) {
-            if (x > v) {
+            if (K::gt(x, v)) {
                 v = x;
                 i = idx;
             }
