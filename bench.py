@@ -385,6 +385,10 @@ def run_gpu(args, ws, rank, local):
     if not args.no_batched:
         batched = bench_batched(args, dev, stream, peak)
 
+    # ---- the paper's data types (Table 2) and the small-array latency ----
+    dtypes = None if args.no_dtypes else bench_dtypes(args, dev, stream, peak)
+    small = None if args.no_small else bench_small(args, dev, stream)
+
     # ---- serving: Poisson stream through the continuous-batching server ----
     serving = None
     if args.serving_full:
@@ -412,6 +416,8 @@ def run_gpu(args, ws, rank, local):
         "gpu_launches": int(launches),
         "e2e": e2e,
         "batched": batched,
+        "dtypes": dtypes,
+        "small": small,
         "serving": serving,
         "clocks": clk,
     }
@@ -419,6 +425,101 @@ def run_gpu(args, ws, rank, local):
         line["cpu_baseline"] = cpu_baseline(budget_s=args.cpu_budget, n=N)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _time_launches(stream, fn, reps):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def bench_dtypes(args, dev, stream, peak, log2n=27):
+    """Add scans of every element type at one size, GB/s and GEPS (giga
+    elements per second, the paper's Table 2 unit); the default tile
+    configuration of each kind.  Inputs (2^27 elements: 0.5-1 GiB) exceed
+    L2."""
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    n = 1 << log2n
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    out = {"n": n, "op": "add", "inclusive": True}
+    cases = (("i32", torch.int32), ("f32", torch.float32),
+             ("i64", torch.int64), ("f64", torch.float64))
+    with torch.cuda.stream(stream):
+        for name, dt in cases:
+            if dt.is_floating_point:
+                x = torch.rand(n, device=dev, dtype=dt, generator=g)
+            else:
+                x = torch.randint(-1000, 1001, (n,), device=dev, dtype=dt,
+                                  generator=g)
+            y = torch.empty_like(x)
+            def run():
+                lscan.scan(x, "add", True, out=y, stream=stream)
+            for _ in range(3):
+                run()
+            t = _time_launches(stream, run, 10)
+            gbs = 2 * n * x.element_size() / t / 1e9
+            out[name] = {"gbs": round(gbs, 1), "geps": round(n / t / 1e9, 2),
+                         "frac_measured": round(gbs / peak, 4)}
+            del x, y
+    lscan.stream_status(stream)
+    return out
+
+
+def bench_small(args, dev, stream):
+    """The 2^20-element int32 add (4 MiB in + out): it fits in L2, so it is
+    reported as latency per launch, warm (inputs L2-resident, launches back
+    to back) and cold (a 256 MiB buffer written between launches evicts
+    L2)."""
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    n = 1 << 20
+    g = torch.Generator(device=dev)
+    g.manual_seed(8)
+    x = torch.randint(-1000, 1001, (n,), device=dev, dtype=torch.int32,
+                      generator=g)
+    y = torch.empty_like(x)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    with torch.cuda.stream(stream):
+        def run():
+            lscan.scan(x, "add", True, out=y, stream=stream)
+        for _ in range(5):
+            run()
+        warm = _time_launches(stream, run, 50)
+        cold = []
+        for i in range(20):
+            flush.fill_(i)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            e1.synchronize()
+            cold.append(e0.elapsed_time(e1) / 1e3)
+        # a tiny array (one partial tile): launch-latency bound
+        xt, yt = x[:1000], y[:1000]
+        def run_tiny():
+            lscan.scan(xt, "add", True, out=yt, stream=stream)
+        for _ in range(5):
+            run_tiny()
+        tiny = _time_launches(stream, run_tiny, 200)
+    lscan.stream_status(stream)
+    cold = float(np.median(cold))
+    return {"n": n, "dtype": "i32", "op": "add",
+            "warm_us_per_launch": round(warm * 1e6, 2),
+            "warm_gbs": round(8 * n / warm / 1e9, 1),
+            "cold_us_per_launch": round(cold * 1e6, 2),
+            "cold_gbs": round(8 * n / cold / 1e9, 1),
+            "n1000_us_per_launch": round(tiny * 1e6, 2)}
 
 
 def bench_batched(args, dev, stream, peak):
@@ -585,6 +686,8 @@ def main():
     ap.add_argument("--carry", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-dtypes", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
