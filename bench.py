@@ -505,13 +505,22 @@ def bench_small(args, dev, stream):
             e1.record(stream)
             e1.synchronize()
             cold.append(e0.elapsed_time(e1) / 1e3)
-        # a tiny array (one partial tile): launch-latency bound
+        # a tiny array (the single-CTA kernel): per call through Python, and
+        # on the device from a CUDA graph of 100 captured launches (the
+        # tiny path allocates nothing, so it can be captured directly)
         xt, yt = x[:1000], y[:1000]
         def run_tiny():
             lscan.scan(xt, "add", True, out=yt, stream=stream)
         for _ in range(5):
             run_tiny()
         tiny = _time_launches(stream, run_tiny, 200)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(100):
+                lscan.scan(xt, "add", True, out=yt,
+                           stream=torch.cuda.current_stream())
+        graph.replay()
+        tiny_graph = _time_launches(stream, graph.replay, 10) / 100
     lscan.stream_status(stream)
     cold = float(np.median(cold))
     return {"n": n, "dtype": "i32", "op": "add",
@@ -519,7 +528,8 @@ def bench_small(args, dev, stream):
             "warm_gbs": round(8 * n / warm / 1e9, 1),
             "cold_us_per_launch": round(cold * 1e6, 2),
             "cold_gbs": round(8 * n / cold / 1e9, 1),
-            "n1000_us_per_launch": round(tiny * 1e6, 2)}
+            "n1000_us_per_call": round(tiny * 1e6, 2),
+            "n1000_us_per_launch_in_graph": round(tiny_graph * 1e6, 2)}
 
 
 def bench_batched(args, dev, stream, peak):

@@ -115,7 +115,10 @@ typedef struct lscan_options {
 } lscan_options;
 
 /* Single-array scan (Section 4; Algorithm 1).  x: n input elements, y: n
- * output elements (layout: contiguous, element type from dtype/out_dtype). */
+ * output elements (layout: contiguous, element type from dtype/out_dtype).
+ * With the tile configuration left to the library (config 0), arrays of at
+ * most 4096 elements run a single-CTA kernel that has no inter-tile carry
+ * and uses no scratch (not in the paper: a latency path for tiny arrays). */
 lscan_status lscan_inclusive(lscan_op op, lscan_dtype dtype, const void *x,
                              void *y, int64_t n, void *stream);
 lscan_status lscan_exclusive(lscan_op op, lscan_dtype dtype, const void *x,

@@ -2,6 +2,7 @@
 #pragma once
 #include "kernel_table.h"
 #include "scan_kernel.cuh"
+#include "tiny_kernel.cuh"
 
 namespace lscan {
 
@@ -60,6 +61,7 @@ void fill_mode(int kind) {
 
 template <class K>
 void fill_kind(int kind) {
+    g_tiny_kernels[kind] = reinterpret_cast<const void *>(&lscan_tiny_kernel<K>);
     fill_mode<K, MODE_SINGLE>(kind);
     fill_mode<K, MODE_SEGMENTED>(kind);
     fill_mode<K, MODE_LIST>(kind);

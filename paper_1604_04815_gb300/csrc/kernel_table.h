@@ -27,6 +27,8 @@ struct KernelEntry {
 
 // [kind][mode][variant]
 extern KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
+// [kind]: the single-CTA kernel for n <= kTinyMax
+extern const void *g_tiny_kernels[kNumKinds];
 
 void register_all_kernels();
 

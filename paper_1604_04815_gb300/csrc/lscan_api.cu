@@ -24,6 +24,7 @@
 namespace lscan {
 
 KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
+const void *g_tiny_kernels[kNumKinds] = {};
 
 void register_i32_add();
 void register_i32_max();
@@ -227,6 +228,21 @@ static bool ranges_partially_overlap(const void *x, size_t xb, const void *y, si
 
 lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
                          cudaStream_t cs) {
+    if (ls.tiny) {
+        // at most one tile: one CTA, no carry, no scratch
+        TinyParams tp;
+        tp.x = ls.x;
+        tp.y = ls.y;
+        tp.n = static_cast<int32_t>(ls.n);
+        tp.inclusive = ls.inclusive ? 1 : 0;
+        tp.carry_in = ls.carry_in;
+        void *args[] = {&tp};
+        if (cudaLaunchKernel(g_tiny_kernels[ls.kind], dim3(1), dim3(kTinyThreads), args, 0,
+                             cs) != cudaSuccess)
+            return LSCAN_ERR_CUDA;
+        g_launches.fetch_add(1);
+        return LSCAN_OK;
+    }
     const KernelEntry &e = g_kernels[ls.kind][ls.mode][ls.variant];
     if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
     int dev = 0;
@@ -317,12 +333,18 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     ls->max_ctas = opts ? opts->max_ctas : 0;
     ls->status_words = static_cast<size_t>(n_tiles) * e.car_words;
     ls->carry_in = carry_in;
+    // arrays of at most one tile take the single-CTA kernel when the tile
+    // configuration is left to the library
+    ls->tiny = mode == MODE_SINGLE && cfg == 0 && n > 0 && n <= kTinyMax &&
+               g_tiny_kernels[kind] != nullptr;
+    if (ls->tiny) ls->status_words = 0;
     return LSCAN_OK;
 }
 
 lscan_status run_planned(const LaunchSpec &ls, void *stream) {
     if (ls.n == 0) return LSCAN_OK;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (ls.tiny) return launch_scan(ls, DevBuffers{nullptr, nullptr}, cs);
     std::lock_guard<std::mutex> lk(g_mu);
     Scratch *sc = nullptr;
     lscan_status st = get_scratch(stream, ls.status_words, &sc);

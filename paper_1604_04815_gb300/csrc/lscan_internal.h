@@ -27,6 +27,7 @@ struct LaunchSpec {
     int max_ctas = 0;
     size_t status_words = 0;
     const void *carry_in = nullptr;  // MODE_SINGLE only
+    bool tiny = false;               // single-CTA kernel, no scratch
 };
 
 // Device scratch a launch uses (control block + status words).

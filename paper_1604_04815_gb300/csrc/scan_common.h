@@ -68,6 +68,19 @@ struct ScanParams {
     const void *carry_in;  // MODE_SINGLE: one output-type element or null
 };
 
+// Single-CTA kernel for arrays of at most one tile (no inter-tile carry).
+constexpr int kTinyThreads = 256;
+constexpr int kTinyItems = 16;
+constexpr int kTinyMax = kTinyThreads * kTinyItems;  // 4096 elements
+
+struct TinyParams {
+    const void *x;
+    void *y;
+    int32_t n;  // 1 .. kTinyMax
+    int32_t inclusive;
+    const void *carry_in;  // one output element or null
+};
+
 // Per-launch constants the wait loops need.
 struct WaitCtx {
     uint32_t *ctl;

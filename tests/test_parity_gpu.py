@@ -478,3 +478,38 @@ def test_carry_in_is_read_at_each_graph_replay():
             assert np.array_equal(to_host(y), want)
     finally:
         g.close()
+
+
+# ------------------------------------------------ single-CTA tiny arrays
+@pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
+@pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
+def test_tiny_arrays(kind, inclusive):
+    """n <= 4096 with config 0 takes the single-CTA kernel (one launch, no
+    carry); 4097 goes back to the persistent kernel.  Also unaligned, in
+    place and with a carry-in."""
+    import oracle
+    op, dtype, prec, ob = kind
+    for i, n in enumerate([1, 2, 31, 257, 1000, 4095, 4096, 4097]):
+        x = _input(op, dtype, n, seed=900 + i)
+        before = _lib.lscan_launch_count()
+        y = run_c_abi(op, dtype, to_device(x, dtype), inclusive, prec=prec,
+                      config=0, out_bf16=ob)
+        assert _lib.lscan_launch_count() == before + 1
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                       out_bf16=ob)
+    # unaligned input and output
+    n = 3000
+    x = _input(op, dtype, n, seed=950)
+    xd = to_device(x, dtype, pad_front=1)
+    odt = (torch.bfloat16 if ob else torch.float32) if (
+        op == "add" and dtype == "bf16") else xd.dtype
+    yb = torch.empty(n + 1, dtype=odt, device="cuda")
+    y = run_c_abi(op, dtype, xd, inclusive, prec=prec, out_bf16=ob,
+                  y_dev=yb[1:])
+    assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
+                   out_bf16=ob)
+    # in place (same element size only)
+    if not (op == "add" and dtype == "bf16"):
+        xd = to_device(x, dtype)
+        y = run_c_abi(op, dtype, xd, inclusive, prec=prec, y_dev=xd)
+        assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64")
