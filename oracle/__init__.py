@@ -15,6 +15,7 @@ Python API (numpy in, numpy out):
     abs_prefix(dtype, x, inclusive=True)           -> np.ndarray (float64)
     abs_segprefix(dtype, x, offsets, inclusive=True)
     bf16_to_double(bits)                           -> float
+    select_flagged(x, flags)                       -> x[flags != 0] in order
 op in {"add", "max"}; dtype in {"i32", "f32", "bf16", "i64", "f64"}; bf16
 data are uint16 bit patterns.  Output dtype: i32 add/max -> int32, f32/bf16
 add -> float64 (the FP64 reference), f32 max -> float32, bf16 max -> uint16
@@ -51,6 +52,8 @@ def _load():
                                           ctypes.c_int]
         lib.oracle_abs_segprefix.argtypes = [ctypes.c_int, vp, vp, vp, i64,
                                              ctypes.c_int]
+        lib.oracle_select_flagged.argtypes = [vp, vp, vp, i64, ctypes.c_int]
+        lib.oracle_select_flagged.restype = i64
         lib.oracle_bf16_to_double.argtypes = [ctypes.c_uint16]
         lib.oracle_bf16_to_double.restype = ctypes.c_double
         for f in (lib.oracle_scan, lib.oracle_segscan, lib.oracle_abs_prefix,
@@ -126,6 +129,22 @@ def abs_segprefix(dtype, x, offsets, inclusive=True):
     if rc != 0:
         raise ValueError("oracle_abs_segprefix rejected its arguments")
     return s
+
+
+def select_flagged(x, flags):
+    """Stream compaction: the elements of x whose flag is nonzero, in order
+    (a consumer of the scan: each output index is the exclusive prefix sum of
+    the flags)."""
+    x = np.ascontiguousarray(x)
+    f = np.ascontiguousarray(flags, dtype=np.uint8)
+    if f.shape[0] != x.shape[0] or x.ndim != 1:
+        raise ValueError("x and flags must be 1-D arrays of the same length")
+    y = np.empty_like(x)
+    k = _load().oracle_select_flagged(x.ctypes.data, f.ctypes.data,
+                                      y.ctypes.data, x.shape[0], x.itemsize)
+    if k < 0:
+        raise ValueError("oracle_select_flagged rejected its arguments")
+    return y[:k]
 
 
 def bf16_to_double(bits):

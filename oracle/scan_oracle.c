@@ -200,6 +200,20 @@ int oracle_segscan(int op, int dtype, const void *x, void *y,
     return 0;
 }
 
+int64_t oracle_select_flagged(const void *x, const uint8_t *flags, void *y,
+                              int64_t n, int elem_size) {
+    if (n < 0 || elem_size <= 0) return -1;
+    int64_t k = 0; /* selected so far = exclusive prefix sum of the flags */
+    for (int64_t j = 0; j < n; ++j) {
+        if (flags[j] != 0) {
+            memcpy((char *)y + k * elem_size, (const char *)x + j * elem_size,
+                   (size_t)elem_size);
+            ++k;
+        }
+    }
+    return k;
+}
+
 int oracle_abs_prefix(int dtype, const void *x, double *s, int64_t n,
                       int inclusive) {
     if (n < 0) return -1;

@@ -78,6 +78,13 @@ int oracle_abs_prefix(int dtype, const void *x, double *s, int64_t n,
 int oracle_abs_segprefix(int dtype, const void *x, double *s,
                          const int64_t *offsets, int64_t n_seg, int inclusive);
 
+/* Stream compaction (a consumer of the scan; not in the paper): copies, in
+ * order, every element x[j] (elem_size bytes) whose flag[j] is nonzero to
+ * y[0..count) and returns count (-1 on bad arguments).  The output index of
+ * a selected element is the exclusive prefix sum of the flags. */
+int64_t oracle_select_flagged(const void *x, const uint8_t *flags, void *y,
+                              int64_t n, int elem_size);
+
 /* bf16 bit pattern -> double (exact). */
 double oracle_bf16_to_double(uint16_t bits);
 

@@ -447,3 +447,31 @@ def test_abs_prefix_f64(oracle_mod):
                           [1.5, 3.75, 3.75, 3.875])
     assert np.array_equal(oracle_mod.abs_prefix("f64", x, False),
                           [0.0, 1.5, 3.75, 3.75])
+
+
+# ------------------------------------------------------- stream compaction
+def test_golden_select_flagged(oracle_mod):
+    g = golden("select_flagged.txt")
+    x = np.array([int(v) for v in g["x"]], dtype=np.int32)
+    f = np.array([int(v) for v in g["flags"]], dtype=np.uint8)
+    assert np.array_equal(oracle_mod.select_flagged(x, f),
+                          np.array([int(v) for v in g["selected"]], np.int32))
+    # output index = exclusive scan of the 0/1 flags (the oracle's own scan)
+    pos = oracle_mod.scan("add", "i32", (f != 0).astype(np.int32), False)
+    assert np.array_equal(pos, [int(v) for v in g["positions"]])
+
+
+@pytest.mark.parametrize("dtype", [np.int16, np.int32, np.float32, np.int64,
+                                   np.float64])
+@pytest.mark.parametrize("p_keep", [0.0, 0.03, 0.5, 1.0])
+def test_select_flagged_matches_mask_and_keeps_bits(oracle_mod, dtype, p_keep):
+    rng = np.random.default_rng(int(p_keep * 100) + np.dtype(dtype).itemsize)
+    n = 1000
+    x = rng.integers(-1000, 1000, size=n).astype(dtype)
+    f = (rng.random(n) < p_keep).astype(np.uint8) * rng.integers(1, 256, n,
+                                                                 dtype=np.uint8)
+    got = oracle_mod.select_flagged(x, f)
+    want = x[f != 0]
+    assert got.dtype == x.dtype and np.array_equal(got.view(np.uint8),
+                                                   want.view(np.uint8))
+    assert got.shape[0] == int(np.count_nonzero(f))
