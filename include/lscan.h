@@ -317,6 +317,18 @@ lscan_status lscan_tune_load(const char *path);
  * bf16 adds). */
 lscan_status lscan_tune_reset(void);
 
+/* Stream compaction (a consumer of the scan; not in the paper): y receives,
+ * in order, every x[j] whose flags[j] is nonzero, and *d_count (device
+ * int64, 8-byte aligned) the number kept.  One pass: the flags are scanned
+ * as 0/1 counts with the single-pass carry chain (Section 4.3) and each kept
+ * element is written once, at its index = the exclusive prefix sum of the
+ * flags.  x, y: n elements of dtype (any type: the bits are moved); flags: n
+ * bytes; y must not overlap x or flags.  n = 0 sets *d_count to 0.
+ * Asynchronous on stream; device waits report through lscan_stream_status. */
+lscan_status lscan_select_flagged(lscan_dtype dtype, const void *x,
+                                  const uint8_t *flags, void *y, int64_t n,
+                                  int64_t *d_count, void *stream);
+
 /* Describes a tile configuration: writes items per thread, consumer threads
  * per CTA, pipeline stages and tile length L for dtype `dtype`. */
 lscan_status lscan_config_info(int32_t config, lscan_dtype dtype,

@@ -115,6 +115,29 @@ def batched(x, offsets, op="add", inclusive=True, out=None, *, n_total=None,
     return out
 
 
+def select_flagged(x, flags, out=None, *, stream=None):
+    """Stream compaction: the elements of x whose flag (uint8/bool) is
+    nonzero, in order, in one pass.  Returns (out, count): out has len(x)
+    elements, the first count[0] of them selected; count is a one-element
+    int64 CUDA tensor (read it after the stream has reached it)."""
+    _check_input(x)
+    if (not isinstance(flags, torch.Tensor) or not flags.is_cuda
+            or flags.dtype not in (torch.uint8, torch.bool)
+            or flags.shape != x.shape or not flags.is_contiguous()):
+        raise TypeError("flags must be a contiguous uint8/bool CUDA tensor "
+                        "shaped like x")
+    if out is None:
+        out = torch.empty_like(x)
+    elif out.dtype != x.dtype or out.shape != x.shape or not out.is_contiguous():
+        raise ValueError("out has the wrong dtype, shape or layout")
+    count = torch.empty(1, dtype=torch.int64, device=x.device)
+    st = _lib.lscan_select_flagged(_DT[x.dtype], x.data_ptr(), flags.data_ptr(),
+                                   out.data_ptr(), x.shape[0],
+                                   count.data_ptr(), _stream_ptr(stream))
+    _lib.check(st, "lscan_select_flagged")
+    return out, count
+
+
 def stream_status(stream=None):
     """Synchronise the stream and raise if the device latched an error."""
     _lib.check(_lib.lscan_stream_status(_stream_ptr(stream)),

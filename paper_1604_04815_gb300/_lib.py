@@ -38,7 +38,7 @@ EXPORTED = [
     "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
     "lscan_server_hold",
     "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
-    "lscan_tune_reset",
+    "lscan_tune_reset", "lscan_select_flagged",
 ]
 
 
@@ -95,6 +95,7 @@ def load():
         "lscan_graph_create_batched": [i32, i32, i32, vp, vp, vp, i64, i64,
                                        optp, ctypes.POINTER(vp)],
         "lscan_scan_noalloc": [i32, i32, i32, vp, vp, i64, vp],
+        "lscan_select_flagged": [i32, vp, vp, vp, i64, vp, vp],
         "lscan_graph_launch": [vp, vp],
         "lscan_graph_status": [vp],
         "lscan_stream_status": [vp],
@@ -185,6 +186,10 @@ def lscan_scan(op, dtype, inclusive, x, y, n, opts=None, stream=None):
 
 def lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream=None):
     return load().lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream)
+
+
+def lscan_select_flagged(dtype, x, flags, y, n, d_count, stream=None):
+    return load().lscan_select_flagged(dtype, x, flags, y, n, d_count, stream)
 
 
 def lscan_batched(op, dtype, inclusive, x, y, d_offsets, n_seg, n_total,

@@ -26,6 +26,13 @@ struct Cfgs<8> {
     using C2 = TileCfg<8, 8, 3, 1, 3>;
     using C3 = TileCfg<8, 16, 2, 1, 2>;
 };
+// flags of a stream compaction: 4096 flags per tile (16 per thread keeps
+// the counts in registers at 3 CTAs/SM), no output staging
+template <>
+struct Cfgs<1> {
+    using G = TileCfg<16, 8, 4, 0, 3>;
+    using C1 = TileCfg<16, 8, 4, 0, 3>;
+};
 template <>
 struct Cfgs<2> {
     using G = TileCfg<16, 8, 4, 1, 3>;
@@ -57,6 +64,14 @@ void fill_mode(int kind) {
     fill_entry<K, typename C::C1, MODE, true>(kind, 1);
     fill_entry<K, typename C::C2, MODE, true>(kind, 2);
     fill_entry<K, typename C::C3, MODE, true>(kind, 3);
+}
+
+// stream compaction: single arrays only, plain-load and one bulk-copy variant
+template <class K>
+void fill_select(int kind) {
+    using C = Cfgs<1>;
+    fill_entry<K, typename C::G, MODE_SINGLE, false>(kind, 0);
+    fill_entry<K, typename C::C1, MODE_SINGLE, true>(kind, 1);
 }
 
 template <class K>

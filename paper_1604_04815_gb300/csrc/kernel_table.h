@@ -10,7 +10,7 @@ namespace lscan {
 // aligned; variants 1..kNumTmaCfg are bulk-copy (TMA) tile configurations.
 constexpr int kNumTmaCfg = 3;
 constexpr int kNumVariants = 1 + kNumTmaCfg;
-constexpr int kNumKinds = 17;
+constexpr int kNumKinds = 20;
 
 struct KernelEntry {
     const void *fn = nullptr;

@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <type_traits>
 
 namespace lscan {
 
@@ -345,6 +346,37 @@ struct KF64Add {
     __device__ static Car car_of_out(Out o) { return o; }
 };
 
+// Stream compaction (a consumer of the scan, not in the paper): the scanned
+// input is a byte of flags per element (nonzero = keep), the scan counts
+// kept elements (uint32 in a tile, uint64 across tiles), and the output
+// stage writes each kept value of type V to its index.  Out = V.
+template <class V>
+struct KSelect {
+    static constexpr bool kTieOrdered = false;
+    static constexpr bool kSelect = true;
+    using In = uint8_t;
+    using Out = V;
+    using Acc = uint32_t;
+    using Car = uint64_t;
+    using CarA = uint64_t;
+    __device__ static Acc ident() { return 0u; }
+    __device__ static Acc load(In f) { return f != 0 ? 1u : 0u; }
+    __device__ static Acc op(Acc a, Acc b) { return a + b; }
+    __device__ static Car cident() { return 0ull; }
+    __device__ static Car to_car(Acc a) { return a; }
+    __device__ static Car cop(Car a, Car b) { return a + b; }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) { return c + tb; }
+    __device__ static CarA base_local(Acc tb) { return tb; }
+    __device__ static Out fin(CarA, Acc) { return Out{}; }  // not used
+    __device__ static Car car_of_out(Out) { return 0ull; }  // no carry-in
+};
+
+template <class K, class = void>
+struct is_select : std::false_type {};
+template <class K>
+struct is_select<K, std::void_t<decltype(K::kSelect)>> : std::bool_constant<K::kSelect> {};
+
 // ------------------------------------------------- kind ids (host + device)
 enum KindId : int {
     KIND_I32_ADD = 0,
@@ -364,6 +396,9 @@ enum KindId : int {
     KIND_I64_MAX,
     KIND_F64_MAX,
     KIND_F64_ADD,
+    KIND_SEL16,  // stream compaction of 2-, 4- and 8-byte values
+    KIND_SEL32,
+    KIND_SEL64,
     KIND_COUNT
 };
 

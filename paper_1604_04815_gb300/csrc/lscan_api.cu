@@ -43,6 +43,7 @@ void register_i64_add();
 void register_i64_max();
 void register_f64_max();
 void register_f64_add();
+void register_select();
 
 void register_all_kernels() {
     register_i32_add();
@@ -62,6 +63,7 @@ void register_all_kernels() {
     register_i64_max();
     register_f64_max();
     register_f64_add();
+    register_select();
 }
 
 namespace {
@@ -272,6 +274,8 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.inclusive = ls.inclusive ? 1 : 0;
     p.carry_mode = ls.carry_mode;
     p.carry_in = ls.carry_in;
+    p.values = ls.values;
+    p.count_out = ls.count_out;
     void *args[] = {&p};
     cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
                                       dim3(e.threads), args, e.smem, cs);
@@ -490,6 +494,47 @@ lscan_status lscan_debug_skip_publish(int64_t tile) {
 }
 
 int32_t lscan_num_configs(void) { return kNumTmaCfg; }
+
+lscan_status lscan_select_flagged(lscan_dtype dtype, const void *x, const uint8_t *flags,
+                                  void *y, int64_t n, int64_t *d_count, void *stream) {
+    std::call_once(g_reg_once, register_all_kernels);
+    const int vsz = dtype_size(dtype);
+    if (vsz == 0 || n < 0 || d_count == nullptr ||
+        reinterpret_cast<uintptr_t>(d_count) % 8 != 0)
+        return LSCAN_ERR_INVALID;
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (n == 0)
+        return cudaMemsetAsync(d_count, 0, sizeof(int64_t), cs) == cudaSuccess ? LSCAN_OK
+                                                                             : LSCAN_ERR_CUDA;
+    if (x == nullptr || flags == nullptr || y == nullptr) return LSCAN_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(x) % vsz != 0 || reinterpret_cast<uintptr_t>(y) % vsz != 0)
+        return LSCAN_ERR_INVALID;
+    const size_t vb = static_cast<size_t>(n) * vsz;
+    // y is written out of step with the reads: no overlap at all
+    const auto overlap = [](const void *a, size_t an, const void *b, size_t bn) {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+        return a0 < b0 + bn && b0 < a0 + an;
+    };
+    if (overlap(y, vb, x, vb) || overlap(y, vb, flags, static_cast<size_t>(n)))
+        return LSCAN_ERR_INVALID;
+    LaunchSpec ls;
+    ls.kind = vsz == 2 ? KIND_SEL16 : vsz == 4 ? KIND_SEL32 : KIND_SEL64;
+    ls.mode = MODE_SINGLE;
+    ls.variant = reinterpret_cast<uintptr_t>(flags) % 16 == 0 ? 1 : 0;
+    const KernelEntry &e = g_kernels[ls.kind][MODE_SINGLE][ls.variant];
+    if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
+    const int64_t n_tiles = (n + e.tile - 1) / e.tile;
+    if (n_tiles > (int64_t{1} << 31) - 1) return LSCAN_ERR_INVALID;
+    ls.x = flags;
+    ls.y = y;
+    ls.n = n;
+    ls.inclusive = true;
+    ls.carry_mode = CARRY_LOOKBACK;
+    ls.status_words = static_cast<size_t>(n_tiles) * e.car_words;
+    ls.values = x;
+    ls.count_out = reinterpret_cast<unsigned long long *>(d_count);
+    return run_planned(ls, stream);
+}
 
 lscan_status lscan_config_info(int32_t config, lscan_dtype dtype, int32_t *items,
                                int32_t *threads, int32_t *stages, int32_t *tile) {

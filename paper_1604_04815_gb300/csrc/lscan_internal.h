@@ -28,6 +28,8 @@ struct LaunchSpec {
     size_t status_words = 0;
     const void *carry_in = nullptr;  // MODE_SINGLE only
     bool tiny = false;               // single-CTA kernel, no scratch
+    const void *values = nullptr;    // stream compaction: values, count
+    unsigned long long *count_out = nullptr;
 };
 
 // Device scratch a launch uses (control block + status words).

@@ -66,6 +66,9 @@ struct ScanParams {
     int32_t inclusive;
     int32_t carry_mode;  // CarryMode
     const void *carry_in;  // MODE_SINGLE: one output-type element or null
+    // stream compaction (x = flags): the values, and where the count goes
+    const void *values;
+    unsigned long long *count_out;
 };
 
 // Single-CTA kernel for arrays of at most one tile (no inter-tile carry).

@@ -178,13 +178,19 @@ __device__ __forceinline__ void unpack_chunks(const uint4 (&t)[C], E (&e)[ITEMS]
         } else if constexpr (sizeof(E) == 4) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) e[4 * c + q] = word_to<E>(w[q]);
-        } else {
-            static_assert(sizeof(E) == 2, "2-, 4- or 8-byte elements");
+        } else if constexpr (sizeof(E) == 2) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 e[8 * c + 2 * q] = static_cast<E>(w[q] & 0xffffu);
                 e[8 * c + 2 * q + 1] = static_cast<E>(w[q] >> 16);
             }
+        } else {
+            static_assert(sizeof(E) == 1, "1-, 2-, 4- or 8-byte elements");
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    e[16 * c + 4 * q + b] = static_cast<E>((w[q] >> (8 * b)) & 0xffu);
         }
     }
 }
@@ -1090,6 +1096,44 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             const CarA cin = carry_s[cslot];
             const bool stop = !okc || stop_s[cslot] != 0u;
 
+            if constexpr (is_select<K>::value) {
+                // stream compaction: v[i] counts the kept elements of this
+                // thread up to i; a kept element goes to carry + thread base
+                // + v[i] - 1, each written once
+                using V = Out;
+                const CarA Bs = K::base(cin, tbv);  // kept before this thread
+                const int64_t ts = t * static_cast<int64_t>(TILE);
+                const V *xv = static_cast<const V *>(p.values) + ts + e0;
+                V *yo = static_cast<V *>(p.y);
+                const bool vec =
+                    full_tile && (reinterpret_cast<uintptr_t>(p.values) & 15u) == 0u;
+                // values in 16-byte chunks (whole chunks when aligned)
+                constexpr int EPC = 16 / int(sizeof(V));
+#pragma unroll
+                for (int j = 0; j < ITEMS / EPC; ++j) {
+                    V vals[EPC];
+                    if (vec) {
+                        const uint4 qa[1] = {reinterpret_cast<const uint4 *>(xv)[j]};
+                        unpack_chunks<V, EPC, 1>(qa, vals);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < EPC; ++u)
+                            if (e0 + j * EPC + u < nt) vals[u] = xv[j * EPC + u];
+                    }
+#pragma unroll
+                    for (int u = 0; u < EPC; ++u) {
+                        const int i = j * EPC + u;
+                        const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
+                        if (e0 + i < nt && kept != 0u) yo[Bs + v[i] - 1u] = vals[u];
+                    }
+                }
+                // the owner of the array's last element writes the count
+                // (elements past the end load as flag 0, so v[ITEMS - 1]
+                // counts up to the last element)
+                if (t == p.n_tiles - 1 && nt - 1 >= e0 && nt - 1 < e0 + ITEMS)
+                    *p.count_out = static_cast<unsigned long long>(Bs + v[ITEMS - 1]);
+                return stop;
+            } else {
             // ---- apply carry and write y once (Section 4.4) ----
             const CarA B = K::base(cin, tbv);            // carry (+) thread base
             const CarA BL = K::base_local(tbv);          // head earlier in tile
@@ -1149,6 +1193,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     if (e0 + i < nt) ty[e0 + i] = o[i];
             }
             return stop;
+            }
             };
             if constexpr (SEG) {
                 stop_next = inner ? finish_tile(std::true_type{}) : finish_tile(std::false_type{});

@@ -87,6 +87,18 @@ def test_host_argument_checks(lib):
     o = L.make_options(carry_in=base * 8)
     assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2,
                            base * 4, 3, 10, o) == L.LSCAN_ERR_INVALID
+    # stream compaction: bad counts, missing or misaligned count pointer,
+    # unknown dtype (all refused before any device work)
+    sel = L.lscan_select_flagged
+    assert sel(L.LSCAN_I32, base, base * 2, base * 4, -1, base * 8) == \
+        L.LSCAN_ERR_INVALID
+    assert sel(L.LSCAN_I32, base, base * 2, base * 4, 10, None) == \
+        L.LSCAN_ERR_INVALID
+    assert sel(L.LSCAN_I32, base, base * 2, base * 4, 10, base * 8 + 4) == \
+        L.LSCAN_ERR_INVALID
+    assert sel(9, base, base * 2, base * 4, 10, base * 8) == L.LSCAN_ERR_INVALID
+    assert sel(L.LSCAN_I32, base, base * 2, base, 10, base * 8) == \
+        L.LSCAN_ERR_INVALID                        # y overlaps x
     # batched: negative counts, missing offsets
     assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2, None,
                            3, 10) == L.LSCAN_ERR_INVALID
