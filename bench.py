@@ -388,6 +388,7 @@ def run_gpu(args, ws, rank, local):
     # ---- the paper's data types (Table 2) and the small-array latency ----
     dtypes = None if args.no_dtypes else bench_dtypes(args, dev, stream, peak)
     small = None if args.no_small else bench_small(args, dev, stream)
+    select = None if args.no_select else bench_select(args, dev, stream, peak)
 
     # ---- serving: Poisson stream through the continuous-batching server ----
     serving = None
@@ -418,6 +419,7 @@ def run_gpu(args, ws, rank, local):
         "batched": batched,
         "dtypes": dtypes,
         "small": small,
+        "select": select,
         "serving": serving,
         "clocks": clk,
     }
@@ -472,6 +474,38 @@ def bench_dtypes(args, dev, stream, peak, log2n=27):
             del x, y
     lscan.stream_status(stream)
     return out
+
+
+def bench_select(args, dev, stream, peak, log2n=28):
+    """Stream compaction of int32 values by byte flags, half of them kept,
+    in one pass.  Algorithmic bytes: n flags + 4n values read + 4k kept
+    values written."""
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    n = 1 << log2n
+    g = torch.Generator(device=dev)
+    g.manual_seed(9)
+    x = torch.randint(-1000, 1001, (n,), device=dev, dtype=torch.int32,
+                      generator=g)
+    flags = (torch.rand(n, device=dev, generator=g) < 0.5).to(torch.uint8)
+    out = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        def run():
+            lscan.select_flagged(x, flags, out=out, stream=stream)
+        for _ in range(3):
+            run()
+        t = _time_launches(stream, run, 10)
+        _, count = lscan.select_flagged(x, flags, out=out, stream=stream)
+    lscan.stream_status(stream)
+    k = int(count.item())
+    ok = k == int(flags.sum().item()) and bool(
+        torch.equal(out[:k], x[flags.bool()]))
+    nbytes = n + 4 * n + 4 * k
+    gbs = nbytes / t / 1e9
+    return {"n": n, "dtype": "i32", "kept": k, "us": round(t * 1e6, 1),
+            "gbs": round(gbs, 1), "frac_measured": round(gbs / peak, 4),
+            "geps": round(n / t / 1e9, 2), "result_check": ok}
 
 
 def bench_small(args, dev, stream):
@@ -698,6 +732,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dtypes", action="store_true")
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-select", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")

@@ -26,12 +26,14 @@ struct Cfgs<8> {
     using C2 = TileCfg<8, 8, 3, 1, 3>;
     using C3 = TileCfg<8, 16, 2, 1, 2>;
 };
-// flags of a stream compaction: 4096 flags per tile (16 per thread keeps
-// the counts in registers at 3 CTAs/SM), no output staging
+// flags of a stream compaction: 4096 flags per tile, 16 per thread, whose
+// values are loaded early and held in registers (2 CTAs/SM leave room for
+// them; a 6-stage ring keeps 12 tiles per SM in flight); one output buffer
+// in which each tile's kept values are compacted before a coalesced copy
 template <>
 struct Cfgs<1> {
-    using G = TileCfg<16, 8, 4, 0, 3>;
-    using C1 = TileCfg<16, 8, 4, 0, 3>;
+    using G = TileCfg<16, 8, 6, 1, 2>;
+    using C1 = TileCfg<16, 8, 6, 1, 2>;
 };
 template <>
 struct Cfgs<2> {

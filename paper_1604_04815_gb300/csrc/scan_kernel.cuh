@@ -77,7 +77,11 @@ struct Layout {
     using In = typename K::In;
     using Out = typename K::Out;
     static constexpr int kIn = TMA ? Cfg::STAGES * Cfg::TILE * int(sizeof(In)) : 0;
-    static constexpr int kOut = TMA ? Cfg::OSTAGES * Cfg::TILE * int(sizeof(Out)) : 0;
+    // output staging: bulk-copy variants, and stream compaction in every
+    // variant (it compacts each tile there before a coalesced copy)
+    static constexpr int kOut = (TMA || is_select<K>::value)
+                                    ? Cfg::OSTAGES * Cfg::TILE * int(sizeof(Out))
+                                    : 0;
     static constexpr int kBits =
         MODE != MODE_SINGLE ? Cfg::STAGES * Cfg::TILE / 8 : 0;
     static constexpr int off_in = 0;
@@ -1019,6 +1023,25 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+            // stream compaction: start loading this thread's values now, so
+            // they arrive while the tile is scanned and its carry awaited
+            constexpr int SELN = is_select<K>::value ? ITEMS : 1;
+            Out selv[SELN];
+            if constexpr (is_select<K>::value) {
+                const Out *xv = static_cast<const Out *>(p.values) +
+                                t * static_cast<int64_t>(TILE) + e0;
+                if (full_tile && (reinterpret_cast<uintptr_t>(p.values) & 15u) == 0u) {
+                    constexpr int VC = ITEMS * int(sizeof(Out)) / 16;
+                    uint4 q[VC];
+#pragma unroll
+                    for (int j = 0; j < VC; ++j) q[j] = reinterpret_cast<const uint4 *>(xv)[j];
+                    unpack_chunks<Out, ITEMS, VC>(q, selv);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < ITEMS; ++i)
+                        if (e0 + i < nt) selv[i] = xv[i];
+                }
+            }
             // the rest of the tile, compiled with and without segment heads
             auto finish_tile = [&](auto seg_tag) -> bool {
             constexpr bool SG = decltype(seg_tag)::value;
@@ -1100,33 +1123,24 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 // stream compaction: v[i] counts the kept elements of this
                 // thread up to i; a kept element goes to carry + thread base
                 // + v[i] - 1, each written once
-                using V = Out;
+                // compact the tile's kept values in shared memory (index in
+                // the tile = thread base + v[i] - 1), then copy them to
+                // y[carry ..) with coalesced stores
                 const CarA Bs = K::base(cin, tbv);  // kept before this thread
-                const int64_t ts = t * static_cast<int64_t>(TILE);
-                const V *xv = static_cast<const V *>(p.values) + ts + e0;
-                V *yo = static_cast<V *>(p.y);
-                const bool vec =
-                    full_tile && (reinterpret_cast<uintptr_t>(p.values) & 15u) == 0u;
-                // values in 16-byte chunks (whole chunks when aligned)
-                constexpr int EPC = 16 / int(sizeof(V));
+                static_assert(L::kOut >= TILE * int(sizeof(Out)),
+                              "compaction needs a whole tile of staging");
+                Out *stg = reinterpret_cast<Out *>(smem + L::off_out);
 #pragma unroll
-                for (int j = 0; j < ITEMS / EPC; ++j) {
-                    V vals[EPC];
-                    if (vec) {
-                        const uint4 qa[1] = {reinterpret_cast<const uint4 *>(xv)[j]};
-                        unpack_chunks<V, EPC, 1>(qa, vals);
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < EPC; ++u)
-                            if (e0 + j * EPC + u < nt) vals[u] = xv[j * EPC + u];
-                    }
-#pragma unroll
-                    for (int u = 0; u < EPC; ++u) {
-                        const int i = j * EPC + u;
-                        const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
-                        if (e0 + i < nt && kept != 0u) yo[Bs + v[i] - 1u] = vals[u];
-                    }
+                for (int i = 0; i < ITEMS; ++i) {
+                    const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
+                    if (e0 + i < nt && kept != 0u) stg[tbv + v[i] - 1u] = selv[i];
                 }
+                const Acc tile_kept = shfl_idx_any(bv, CW - 1);  // block total
+                named_bar_sync(3, CT);
+                Out *yo = static_cast<Out *>(p.y) + cin;
+                for (int j = tid; j < static_cast<int>(tile_kept); j += CT) yo[j] = stg[j];
+                // (the next tile writes stg only after its block-scan barrier,
+                // which every consumer thread reaches after this copy)
                 // the owner of the array's last element writes the count
                 // (elements past the end load as flag 0, so v[ITEMS - 1]
                 // counts up to the last element)
