@@ -896,12 +896,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                         unpack_chunks<In, EPC, 1>(qa, e);
 #pragma unroll
                         for (int u = 0; u < EPC; ++u) {
-                            const int idx = c * EPC + u;
-                            if (!SG || idx >= start) ra[u].add_in_order(K::load(e[u]), idx);
+                            // accumulator u only sees position u of each
+                            // chunk: it tracks the chunk index c
+                            if (!SG || c * EPC + u >= start)
+                                ra[u].add_in_order(K::load(e[u]), c);
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < EPC; ++u) r.add(ra[u].v, ra[u].i);
+                    for (int u = 0; u < EPC; ++u)
+                        r.add(ra[u].v, ra[u].i == INT32_MAX ? INT32_MAX : ra[u].i * EPC + u);
                 } else {
                     for (int i = lane; i < nt; i += 32)
                         if (!SG || i >= start) r.add(K::load(tx[i]), i);
