@@ -290,7 +290,7 @@ def run_gpu(args, ws, rank, local):
                 _lib.LSCAN_ADD if op == "add" else _lib.LSCAN_MAX,
                 _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32, 1,
                 xs[c].data_ptr(), ys[c].data_ptr(), N,
-                opts=_lib.make_options(carry=args.carry), reps=5, stream=sp)
+                opts=_lib.make_options(carry=args.carry), reps=3, stream=sp)
             _lib.check(st, "lscan_autotune")
             info = _lib.lscan_config_info(best, _lib.LSCAN_I32)
             tuned[c] = {"config": best, "items": info["items"],
