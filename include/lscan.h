@@ -135,13 +135,11 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
  * critical path where cudaMalloc (which may synchronise or fail) is not
  * acceptable.  It runs the same single-array scan as lscan_scan with default
  * options, but its scratch (control block + per-tile status words) is a
- * fixed array compiled into the library: 1 MiB + 512 B that every GPU which
+ * fixed array compiled into the library: 2 MiB + 512 B that every GPU which
  * loads the library keeps until the process exits.
- *  - n is limited by that array: at most 131072 status words, one per tile
- *    for int32, max and plain-carry scans, two per tile for FP64-carry and
- *    compensated float adds; with the default 4096-element tile that is
- *    2^29 and 2^28 elements.  Larger n returns LSCAN_ERR_INVALID without
- *    launching.
+ *  - n is limited by that array: at most 262144 status words, two per tile
+ *    (every kind); with the default 4096-element tile that is 2^29
+ *    elements.  Larger n returns LSCAN_ERR_INVALID without launching.
  *  - The first call on a device looks up the array and clears it with
  *    cudaMemsetAsync on `stream`; make that first call before any capture.
  *  - Every call shares the array (it keeps the last call's contents; each

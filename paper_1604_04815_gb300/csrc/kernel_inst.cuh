@@ -54,7 +54,7 @@ void fill_entry(int kind, int variant) {
     e.items = Cfg::ITEMS;
     e.cwarps = Cfg::CWARPS;
     e.stages = Cfg::STAGES;
-    e.car_words = int(sizeof(typename K::Car) / 4);
+    e.car_words = StatusIO<K>::SLOT;  // status words per tile
     e.in_size = int(sizeof(typename K::In));
     e.out_size = int(sizeof(typename K::Out));
 }

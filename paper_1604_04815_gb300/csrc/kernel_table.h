@@ -20,7 +20,7 @@ struct KernelEntry {
     int items = 0;     // elements per consumer thread
     int cwarps = 0;    // consumer warps
     int stages = 0;    // tile-ring depth
-    int car_words = 0; // 64-bit status words per tile
+    int car_words = 0; // 64-bit status words per tile slot
     int in_size = 0;
     int out_size = 0;
 };

@@ -38,8 +38,8 @@
 namespace lscan {
 namespace {
 
-// 512 B control block + 131072 status words: 1 MiB + 512 B per device.
-constexpr size_t kNoAllocStatusWords = size_t{1} << 17;
+// 512 B control block + 262144 status words: 2 MiB + 512 B per device.
+constexpr size_t kNoAllocStatusWords = size_t{1} << 18;
 constexpr size_t kNoAllocScratchWords = CTL_WORDS / 2 + kNoAllocStatusWords;
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
