@@ -54,7 +54,8 @@ void fill_entry(int kind, int variant) {
     e.items = Cfg::ITEMS;
     e.cwarps = Cfg::CWARPS;
     e.stages = Cfg::STAGES;
-    e.car_words = StatusIO<K>::SLOT;  // status words per tile
+    static_assert(status_slot_words<K, Cfg::TILE>() <= kMaxSlotWords, "status slot");
+    e.car_words = status_slot_words<K, Cfg::TILE>();  // status words per tile
     e.in_size = int(sizeof(typename K::In));
     e.out_size = int(sizeof(typename K::Out));
 }

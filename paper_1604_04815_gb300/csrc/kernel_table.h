@@ -11,6 +11,9 @@ namespace lscan {
 constexpr int kNumTmaCfg = 3;
 constexpr int kNumVariants = 1 + kNumTmaCfg;
 constexpr int kNumKinds = 20;
+// most status words any kernel uses per tile (fixed-size scratch is sized
+// with it)
+constexpr int kMaxSlotWords = 4;
 
 struct KernelEntry {
     const void *fn = nullptr;

@@ -301,7 +301,8 @@ bool launch_batch_locked(lscan_server *srv, int si) {
                         cudaMemcpyHostToDevice, sl.stream);
         if (++sl.launches >= (1ull << 30) - 1) {  // keep the epoch tag from wrapping
             cudaMemsetAsync(sl.ctl, 0, CTL_WORDS * sizeof(uint32_t), sl.stream);
-            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * 2 * sizeof(uint64_t), sl.stream);
+            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * kMaxSlotWords * sizeof(uint64_t),
+                            sl.stream);
             sl.launches = 0;
         }
         cudaEventRecord(sl.ev_start, sl.stream);
@@ -390,7 +391,7 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     }
     auto up = [](size_t b) { return (b + kPoolAlign - 1) / kPoolAlign * kPoolAlign; };
     const size_t ctl_b = up(CTL_WORDS * sizeof(uint32_t));
-    const size_t st_b = up(kMaxBatchTiles * 2 * sizeof(uint64_t));
+    const size_t st_b = up(kMaxBatchTiles * kMaxSlotWords * sizeof(uint64_t));
     const size_t desc_b = up(kMaxBatchRequests * sizeof(SegDesc));
     const size_t first_b = up((kMaxBatchRequests + 1) * sizeof(int64_t));
     const size_t slot_b = ctl_b + st_b + desc_b + first_b;

@@ -289,19 +289,26 @@ __device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
 }
 
 // ------------------------------------------------------------ status words
-template <class K>
+// Words per tile slot.  Every carry warp polls, and the reducers and carry
+// warps publish to, the same few status lines near the frontier; the L2
+// slices holding them then slow the streaming traffic that maps there, so
+// fewer tiles per 128-byte line pay.  Measured on GB300 at 2^28: a 32-bit
+// carry (int32 add, 16 KiB tiles) with 1/2/4/8 words per tile
+// 5256/5667/5668/5545 GB/s; a two-word FP64 carry with 32 KiB tiles (fp32
+// add, config 3) 2 words 5336, 4 words 5487, 8 words 5457 (means of 3),
+// but with 16 KiB tiles 4 words lost (bf16 add, config 2: 4892 -> 4684).
+template <class K, int TILE>
+constexpr int status_slot_words() {
+    constexpr int W = int(sizeof(typename K::Car) / 4);
+    constexpr int TILE_BYTES = TILE * int(sizeof(typename K::In));
+    return W == 1 ? 2 : (TILE_BYTES >= 32768 ? 2 * W : W);
+}
+
+template <class K, int SLOT>
 struct StatusIO {
     using Car = typename K::Car;
     static constexpr int W = int(sizeof(Car) / 4);
-    // Words per tile slot: a 32-bit carry still takes a 16-byte slot.  Every
-    // carry warp polls, and the reducers and carry warps publish to, the
-    // same few status lines near the frontier; the L2 slices holding them
-    // then slow the streaming traffic that maps there.  Fewer tiles per
-    // 128-byte line relieve them.  Measured on GB300 (int32 add, 2^28,
-    // 4096-element tiles): 1 word per tile 5256 GB/s, 2 words 5667, 4 words
-    // 5668, 8 words 5545; two-word (FP64) carries stay packed (4 words: config
-    // 3 +1 %, config 2 -11 %).
-    static constexpr int SLOT = W > 2 ? W : 2;
+    static_assert(SLOT >= W, "a slot holds the carry's words");
 
     __device__ static void publish(uint64_t *status, int64_t t, uint32_t tag,
                                    Car c) {
@@ -413,7 +420,7 @@ struct CarryFold {
     }
 };
 
-template <class K>
+template <class K, int SLOT>
 __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
                                     int64_t t, uint32_t ebase, int lane) {
     using Car = typename K::Car;
@@ -431,7 +438,7 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
             const int64_t idx = base - 32 * j - lane;
             st[j] = ST_INCLUSIVE;  // before tile 0: identity, inclusive
             val[j] = K::cident();
-            if (idx >= 0) st[j] = StatusIO<K>::read(p.status, idx, ebase, val[j]);
+            if (idx >= 0) st[j] = StatusIO<K, SLOT>::read(p.status, idx, ebase, val[j]);
             if (gave_up && st[j] == ST_INVALID) {
                 st[j] = ST_INCLUSIVE;
                 val[j] = K::cident();
@@ -504,17 +511,17 @@ __device__ typename K::Car lookback(const ScanParams &p, const WaitCtx &wc,
 }
 
 // Chained hand-off (Algorithm 4): wait for tile t-1's inclusive prefix.
-template <class K>
+template <class K, int SLOT>
 __device__ typename K::Car chained_wait(const ScanParams &p, const WaitCtx &wc,
                                         int64_t t, uint32_t ebase, int lane) {
     using Car = typename K::Car;
     Car v = K::cident();
     if (lane == 0) {
-        uint32_t st = StatusIO<K>::read(p.status, t - 1, ebase, v);
+        uint32_t st = StatusIO<K, SLOT>::read(p.status, t - 1, ebase, v);
         if (st != ST_INCLUSIVE) {
             const uint64_t t0 = global_timer_ns();
             while (true) {
-                st = StatusIO<K>::read(p.status, t - 1, ebase, v);
+                st = StatusIO<K, SLOT>::read(p.status, t - 1, ebase, v);
                 if (st == ST_INCLUSIVE) break;
                 if (wait_over(wc, global_timer_ns() - t0)) {
                     note_gave_up(wc, DEV_ERR_CARRY_WAIT);
@@ -614,6 +621,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr bool SEG = MODE != MODE_SINGLE;  // segment heads exist
     constexpr int NC = Cfg::NCARRY;
     constexpr int CR = L::CR;
+    constexpr int SLOT = status_slot_words<K, TILE>();  // status words per tile
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
@@ -933,7 +941,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                                     ? K::cop(carry_in_of<K>(p), agg)
                                     : agg;
                 if (t != p.skip_tile)
-                    StatusIO<K>::publish(p.status, t,
+                    StatusIO<K, SLOT>::publish(p.status, t,
                                          ebase | ((t == 0 || has_head) ? ST_INCLUSIVE
                                                                         : ST_AGGREGATE),
                                          pub);
@@ -974,15 +982,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             if (!__all_sync(0xffffffffu, okr) && lane == 0) *abort_s = 1;
             Car excl = K::cident();
             if (t > 0 && !head0)
-                excl = p.carry_mode == CARRY_CHAINED ? chained_wait<K>(p, wc, t, ebase, lane)
-                                                     : lookback<K>(p, wc, t, ebase, lane);
+                excl = p.carry_mode == CARRY_CHAINED
+                           ? chained_wait<K, SLOT>(p, wc, t, ebase, lane)
+                           : lookback<K, SLOT>(p, wc, t, ebase, lane);
             else if (!SEG && t == 0)
                 excl = carry_in_of<K>(p);
             if (lane == 0) {
                 const bool has_head = SEG && head_r[c] != 0u;
                 // tile 0 and tiles holding a head got theirs from the reducer
                 if (t > 0 && !has_head && t != p.skip_tile)
-                    StatusIO<K>::publish(p.status, t, ebase | ST_INCLUSIVE,
+                    StatusIO<K, SLOT>::publish(p.status, t, ebase | ST_INCLUSIVE,
                                          K::cop(excl, agg_r[c]));
                 carry_s[c] = K::to_apply(excl);
                 stop_s[c] = *abort_s;  // one snapshot for every consumer warp
