@@ -298,7 +298,7 @@ __device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
 // add, config 3) 2 words 5336, 4 words 5487, 8 words 5457 (means of 3),
 // but with 16 KiB tiles 4 words lost (bf16 add, config 2: 4892 -> 4684).
 template <class K, int TILE>
-constexpr int status_slot_words() {
+__host__ __device__ constexpr int status_slot_words() {
     constexpr int W = int(sizeof(typename K::Car) / 4);
     constexpr int TILE_BYTES = TILE * int(sizeof(typename K::In));
     return W == 1 ? 2 : (TILE_BYTES >= 32768 ? 2 * W : W);
@@ -774,22 +774,35 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 tx = x + ts;
                 ty = y + ts;
             }
-            const bool bulk = TMA && nt == TILE;
+            // A full tile is one bulk copy; a partial tile (the end of an
+            // array) a bulk copy of its 16-byte-aligned prefix plus the last
+            // few bytes copied by the lanes, so that it is read from shared
+            // memory like a full tile.
+            const uint32_t tbytes = static_cast<uint32_t>(nt) * uint32_t(sizeof(In));
+            const uint32_t bulk_bytes = TMA ? (tbytes & ~15u) : 0u;
             if (lane == 0) {
                 slot_x[s] = tx;
                 slot_y[s] = ty;
                 slot_nt[s] = nt;
-                if (bulk) {
+                if (bulk_bytes > 0u) {
                     // start the copy now; the slot's phase also needs the
                     // arrival below, made once the head bitmap is written
-                    constexpr uint32_t bytes = TILE * sizeof(In);
-                    mbar_expect_tx(&full[s], bytes);
-                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bytes, &full[s]);
+                    mbar_expect_tx(&full[s], bulk_bytes);
+                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bulk_bytes, &full[s]);
                     armed_mask |= 1u << s;
                     par_mask = (par_mask & ~(1u << s)) |
                                (static_cast<uint32_t>((k / ST) & 1) << s);
                 } else {
                     armed_mask &= ~(1u << s);
+                }
+            }
+            if constexpr (TMA) {
+                if (bulk_bytes < tbytes) {
+                    In *sin = reinterpret_cast<In *>(smem + L::off_in + s * TILE * sizeof(In));
+                    for (int i = static_cast<int>(bulk_bytes / sizeof(In)) + lane; i < nt; i += 32)
+                        sin[i] = tx[i];
+                    // these generic writes precede the slot's next bulk copy
+                    fence_proxy_async_smem();
                 }
             }
             if constexpr (MODE == MODE_LIST) {
@@ -923,8 +936,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     for (int u = 0; u < EPC; ++u)
                         r.add(ra[u].v, ra[u].i == INT32_MAX ? INT32_MAX : ra[u].i * EPC + u);
                 } else {
+                    // partial tile: from the slot (bulk variants) or global
+                    const In *src = TMA ? reinterpret_cast<const In *>(
+                                              smem + L::off_in + s * TILE * sizeof(In))
+                                        : tx;
                     for (int i = lane; i < nt; i += 32)
-                        if (!SG || i >= start) r.add(K::load(tx[i]), i);
+                        if (!SG || i >= start) r.add(K::load(src[i]), i);
                 }
             };
             if (inner) {
@@ -1029,9 +1046,13 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i) v[i] = K::load(xv[i]);
             } else {
+                // partial tile: from the slot (bulk variants) or global
+                const In *src = TMA ? reinterpret_cast<const In *>(
+                                          smem + L::off_in + s * TILE * sizeof(In))
+                                    : tx;
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i)
-                    v[i] = (e0 + i < nt) ? K::load(tx[e0 + i]) : K::ident();
+                    v[i] = (e0 + i < nt) ? K::load(src[e0 + i]) : K::ident();
             }
             // A tile whose only segment head is its first element takes the
             // unsegmented code: its carry is the identity (the carry warp
@@ -1222,6 +1243,22 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
                     bulk_commit();
                 }
+            } else if (TMA && OS >= 1) {
+                // partial tile: through this warp's staging region, then
+                // coalesced stores of its valid elements
+                constexpr int WE = 32 * ITEMS;  // elements per warp region
+                Out *region = reinterpret_cast<Out *>(
+                    smem + L::off_out + (OS == 2 ? (k & 1) : 0) * (TILE * sizeof(Out)) +
+                    warp * WE * sizeof(Out));
+                if (lane == 0) bulk_wait_read<0>();  // earlier bulk stores read it
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) region[lane * ITEMS + i] = o[i];
+                __syncwarp();
+                const int wbase = warp * WE;
+                const int valid = nt - wbase < WE ? nt - wbase : WE;
+                for (int j = lane; j < valid; j += 32) ty[wbase + j] = region[j];
+                __syncwarp();  // read before the next tile writes the region
             } else {
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i)
