@@ -128,6 +128,37 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
                         const void *x, void *y, int64_t n,
                         const lscan_options *opts, void *stream);
 
+/* Single-array scan of an array in HOST memory (not in the paper, whose
+ * arrays are on the device).  hx: n input elements in host memory; hy: n
+ * output elements in host memory (element types as for lscan_scan); hy == hx
+ * is allowed when the two element sizes are equal, partial overlap returns
+ * LSCAN_ERR_INVALID.  Page-locked memory (cudaHostAlloc / cudaHostRegister)
+ * gets full copy bandwidth and overlap; pageable memory is accepted, but its
+ * copies are staged by the CUDA driver and overlap less.
+ *  - The array moves in chunks of `chunk` elements (0 = 2^23) through three
+ *    device slots: chunk k is copied in while chunk k-1 is scanned on
+ *    `stream` and chunk k-2 is copied out, on two internal streams.  Chunk
+ *    k > 0 starts from the inclusive total of chunks 0..k-1, handed on in
+ *    the kind's carry type (FP64 for the float adds with an FP64 carry), so
+ *    the results meet the same rules and bounds as lscan_scan over the whole
+ *    array.
+ *  - opts as for lscan_scan; opts->carry_in (a DEVICE pointer to one output
+ *    element) is the carry-in of chunk 0.
+ *  - Asynchronous on stream: the copies start after the work already queued
+ *    on stream, and work queued on stream afterwards runs after the last
+ *    element of hy is written.  hx and hy must stay valid until then.
+ *  - The device slots (3 x chunk x (input + output element size) bytes) are
+ *    owned by the library per (device, stream), grow on demand (after the
+ *    previous call's copies finish) and are freed by lscan_shutdown.
+ *  - Not capturable: returns LSCAN_ERR_UNSUPPORTED while stream is being
+ *    captured.  Device-side carry timeouts latch on stream as for
+ *    lscan_scan (lscan_stream_status).  After LSCAN_ERR_CUDA or
+ *    LSCAN_ERR_NOMEM the contents of hy are unspecified. */
+lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int inclusive,
+                             const void *hx, void *hy, int64_t n,
+                             const lscan_options *opts, int64_t chunk,
+                             void *stream);
+
 /* The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory when they scan: a memory-pool or
  * allocator implementation that is itself servicing an allocation, code under

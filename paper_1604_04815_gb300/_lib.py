@@ -27,6 +27,7 @@ LSCAN_CARRY_AUTO, LSCAN_CARRY_LOOKBACK, LSCAN_CARRY_CHAINED = 0, 1, 2
 # every symbol include/lscan.h declares (checked by the ABI test)
 EXPORTED = [
     "lscan_inclusive", "lscan_exclusive", "lscan_scan", "lscan_batched",
+    "lscan_scan_host",
     "lscan_graph_create_scan", "lscan_graph_create_batched",
     "lscan_graph_launch", "lscan_graph_status", "lscan_graph_destroy",
     "lscan_stream_status", "lscan_reserve", "lscan_shutdown",
@@ -89,6 +90,7 @@ def load():
         "lscan_inclusive": [i32, i32, vp, vp, i64, vp],
         "lscan_exclusive": [i32, i32, vp, vp, i64, vp],
         "lscan_scan": [i32, i32, i32, vp, vp, i64, optp, vp],
+        "lscan_scan_host": [i32, i32, i32, vp, vp, i64, optp, i64, vp],
         "lscan_batched": [i32, i32, i32, vp, vp, vp, i64, i64, optp, vp],
         "lscan_graph_create_scan": [i32, i32, i32, vp, vp, i64, optp,
                                     ctypes.POINTER(vp)],
@@ -182,6 +184,13 @@ def lscan_scan(op, dtype, inclusive, x, y, n, opts=None, stream=None):
     return load().lscan_scan(op, dtype, inclusive, x, y, n,
                              ctypes.byref(opts) if opts is not None else None,
                              stream)
+
+
+def lscan_scan_host(op, dtype, inclusive, hx, hy, n, opts=None, chunk=0,
+                    stream=None):
+    return load().lscan_scan_host(op, dtype, inclusive, hx, hy, n,
+                                  ctypes.byref(opts) if opts is not None
+                                  else None, chunk, stream)
 
 
 def lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream=None):

@@ -238,6 +238,9 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
         tp.n = static_cast<int32_t>(ls.n);
         tp.inclusive = ls.inclusive ? 1 : 0;
         tp.carry_in = ls.carry_in;
+        tp.carry_in_car = ls.carry_in_car ? 1 : 0;
+        tp.reserved = 0;
+        tp.total_out = ls.total_out;
         void *args[] = {&tp};
         if (cudaLaunchKernel(g_tiny_kernels[ls.kind], dim3(1), dim3(kTinyThreads), args, 0,
                              cs) != cudaSuccess)
@@ -274,6 +277,9 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.inclusive = ls.inclusive ? 1 : 0;
     p.carry_mode = ls.carry_mode;
     p.carry_in = ls.carry_in;
+    p.carry_in_car = ls.carry_in_car ? 1 : 0;
+    p.reserved = 0;
+    p.total_out = ls.mode == MODE_SINGLE ? ls.total_out : nullptr;
     p.values = ls.values;
     p.count_out = ls.count_out;
     void *args[] = {&p};
@@ -433,7 +439,8 @@ lscan_status lscan_stream_status(void *stream) {
 lscan_status lscan_reserve(void *stream, int64_t max_elems) {
     if (max_elems < 0) return LSCAN_ERR_INVALID;
     std::call_once(g_reg_once, register_all_kernels);
-    // smallest tile of any configuration x the widest carry (2 words)
+    // smallest tile of any configuration (1024), 2 status words per such
+    // tile: 4-word slots come only with tiles of >= 4096 elements
     int64_t min_tile = INT64_MAX;
     for (int k = 0; k < kNumKinds; ++k)
         for (int m = 0; m < MODE_COUNT; ++m)
@@ -447,6 +454,7 @@ lscan_status lscan_reserve(void *stream, int64_t max_elems) {
 }
 
 void lscan_shutdown(void) {
+    shutdown_host_pipes();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

@@ -27,6 +27,8 @@ struct LaunchSpec {
     int max_ctas = 0;
     size_t status_words = 0;
     const void *carry_in = nullptr;  // MODE_SINGLE only
+    bool carry_in_car = false;       // carry_in holds the kind's carry type
+    void *total_out = nullptr;       // MODE_SINGLE: inclusive total, carry type
     bool tiny = false;               // single-CTA kernel, no scratch
     const void *values = nullptr;    // stream compaction: values, count
     unsigned long long *count_out = nullptr;
@@ -54,6 +56,7 @@ int tuned_variant(int kind, int mode, int64_t n);
 
 std::mutex &api_mutex();
 void shutdown_graphs_locked();
+void shutdown_host_pipes();  // frees the staging of lscan_scan_host
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
 void set_tuned_variant(int kind, int mode, int size_cls, int variant);

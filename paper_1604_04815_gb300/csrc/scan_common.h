@@ -65,7 +65,11 @@ struct ScanParams {
     int64_t skip_tile;  // fault injection: never publish this tile (-1: off)
     int32_t inclusive;
     int32_t carry_mode;  // CarryMode
-    const void *carry_in;  // MODE_SINGLE: one output-type element or null
+    const void *carry_in;  // MODE_SINGLE: one element (type: carry_in_car) or null
+    int32_t carry_in_car;  // 1: carry_in holds the kind's carry type, 0: output type
+    int32_t reserved;
+    void *total_out;       // MODE_SINGLE: gets x_0 (+) ... (+) x_{n-1} (+ carry-in),
+                           // in the carry type, or null
     // stream compaction (x = flags): the values, and where the count goes
     const void *values;
     unsigned long long *count_out;
@@ -81,7 +85,10 @@ struct TinyParams {
     void *y;
     int32_t n;  // 1 .. kTinyMax
     int32_t inclusive;
-    const void *carry_in;  // one output element or null
+    const void *carry_in;  // one element (type: carry_in_car) or null
+    int32_t carry_in_car;  // 1: carry_in holds the kind's carry type, 0: output type
+    int32_t reserved;
+    void *total_out;       // gets the inclusive total in the carry type, or null
 };
 
 // Per-launch constants the wait loops need.

@@ -391,11 +391,13 @@ __device__ __forceinline__ bool wait_phase(uint64_t *bar, uint32_t parity,
 // still (3455 GB/s): the groups near the frontier are always fresh.
 constexpr int kLookbackWindows = 1;
 
-// The carry-in of a single-array scan: the caller's output-type element, or
-// the operator's identity.
+// The carry-in of a single-array scan: the caller's output-type element, a
+// carry-type value (the total a previous chunk of the same array handed on),
+// or the operator's identity.
 template <class K>
 __device__ __forceinline__ typename K::Car carry_in_of(const ScanParams &p) {
     if (p.carry_in == nullptr) return K::cident();
+    if (p.carry_in_car) return *static_cast<const typename K::Car *>(p.carry_in);
     return K::car_of_out(*static_cast<const typename K::Out *>(p.carry_in));
 }
 
@@ -1010,6 +1012,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 if (t > 0 && !has_head && t != p.skip_tile)
                     StatusIO<K, SLOT>::publish(p.status, t, ebase | ST_INCLUSIVE,
                                          K::cop(excl, agg_r[c]));
+                // the last tile's inclusive prefix is the array's total (the
+                // carry-in of the next chunk when an array is scanned in chunks)
+                if (!SEG && t == p.n_tiles - 1 && p.total_out != nullptr)
+                    *static_cast<Car *>(p.total_out) = K::cop(excl, agg_r[c]);
                 carry_s[c] = K::to_apply(excl);
                 stop_s[c] = *abort_s;  // one snapshot for every consumer warp
                 mbar_arrive(&carried[c]);

@@ -69,8 +69,15 @@ __global__ void __launch_bounds__(kTinyThreads) lscan_tiny_kernel(const TinyPara
     const Acc tbv = K::op(wev, lv);
 
     typename K::Car cin = K::cident();
-    if (p.carry_in != nullptr) cin = K::car_of_out(*static_cast<const Out *>(p.carry_in));
+    if (p.carry_in != nullptr)
+        cin = p.carry_in_car ? *static_cast<const typename K::Car *>(p.carry_in)
+                             : K::car_of_out(*static_cast<const Out *>(p.carry_in));
     const CarA B = K::base(K::to_apply(cin), tbv);
+    // the last thread's inclusive value covers the whole array (identities
+    // pad it past n): the total handed to the next chunk of a chunked scan
+    if (p.total_out != nullptr && tid == kTinyThreads - 1)
+        *static_cast<typename K::Car *>(p.total_out) =
+            K::cop(cin, K::to_car(K::op(tbv, v[kTinyItems - 1])));
 #pragma unroll
     for (int i = 0; i < kTinyItems; ++i) {
         if (e0 + i >= n) break;

@@ -108,6 +108,33 @@ def test_host_argument_checks(lib):
     assert L.strerror(L.LSCAN_ERR_TIMEOUT) == "device wait ran out of time"
 
 
+def test_host_scan_argument_checks(lib):
+    """lscan_scan_host refuses bad arguments before any CUDA call (the
+    pointers here are never dereferenced)."""
+    L = lib
+    f = L.lscan_scan_host
+    base = 1 << 20
+    add, i32, bf16 = L.LSCAN_ADD, L.LSCAN_I32, L.LSCAN_BF16
+    assert f(add, i32, 1, base, base * 2, -1) == L.LSCAN_ERR_INVALID
+    assert f(add, i32, 1, base, base * 2, 10, None, -5) == L.LSCAN_ERR_INVALID
+    assert f(add, i32, 1, None, base * 2, 10) == L.LSCAN_ERR_INVALID
+    assert f(add, i32, 1, base, None, 10) == L.LSCAN_ERR_INVALID
+    assert f(add, i32, 1, base + 2, base * 2, 10) == L.LSCAN_ERR_INVALID
+    assert f(add, i32, 1, base, base + 4, 10) == L.LSCAN_ERR_INVALID
+    # bf16 add writes fp32: the same start is an overlap, not in place
+    assert f(add, bf16, 1, base, base, 10) == L.LSCAN_ERR_INVALID
+    assert f(9, i32, 1, base, base * 2, 10) == L.LSCAN_ERR_INVALID
+    assert f(add, 7, 1, base, base * 2, 10) == L.LSCAN_ERR_INVALID
+    o = L.make_options(out_dtype=L.LSCAN_BF16)
+    assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_UNSUPPORTED
+    o = L.make_options(config=7)
+    assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_INVALID
+    o = L.make_options(carry_in=base + 2)
+    assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_INVALID
+    # nothing to do
+    assert f(add, i32, 1, None, None, 0) == L.LSCAN_OK
+
+
 def test_options_struct_layout(lib):
     """lscan_options: five int32 settings, one reserved int32, then the
     carry-in pointer at byte 24 (32 bytes in all)."""

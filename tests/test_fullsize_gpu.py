@@ -32,3 +32,29 @@ def test_full_size(case):
     ratio = assert_matches(op, dtype, x, got, True, "f64")
     if op == "add" and dtype == "f32":
         print(f"fp32 add N=2^28 max err/S_j = {ratio:.3e}")
+
+
+@pytest.mark.parametrize("case", ["i32_add", "i32_max", "f32_add"])
+def test_full_size_from_host(case):
+    """The same arrays from pinned host memory through lscan_scan_host with
+    the default chunking, as bench.py's end-to-end leg runs them."""
+    from paper_1604_04815_gb300 import _lib, build
+    from gpu_util import LDT, LOP
+    build.build()
+    if case == "i32_add":
+        op, dtype, x = "add", "i32", workloads.large_i32_add(N)
+    elif case == "i32_max":
+        op, dtype, x = "max", "i32", workloads.large_i32_max(N)
+    else:
+        op, dtype, x = "add", "f32", workloads.large_f32_add(N)
+    hx = torch.from_numpy(x).pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    s = torch.cuda.current_stream().cuda_stream
+    st = _lib.lscan_scan_host(LOP[op], LDT[dtype], 1, hx.data_ptr(),
+                              hy.data_ptr(), N, None, 0, s)
+    assert st == _lib.LSCAN_OK
+    torch.cuda.current_stream().synchronize()
+    assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
+    got = hy.numpy().copy()
+    del hx, hy
+    assert_matches(op, dtype, x, got, True, "f64")
