@@ -10,7 +10,9 @@
 //  * Loads (Section 4.1 step 1, Section 4.5).  One producer warp per CTA
 //    issues cp.async.bulk copies of whole tiles into a STAGES-deep shared
 //    memory ring, up to STAGES-1 tiles ahead, so HBM reads stay in flight
-//    while the consumer warps wait on a carry.  x is read exactly once.
+//    while the consumer warps wait on a carry (the ragged last tile of an
+//    array: a bulk copy of its 16-byte-aligned prefix, the last few bytes
+//    copied by the producer lanes).  x is read exactly once.
 //  * Intra-warp local scan (Section 4.1, Algorithm 2).  Each thread holds
 //    ITEMS consecutive elements (read from shared memory as 16-byte vectors,
 //    XOR-rotated so that each quarter-warp touches 32 distinct banks), scans
@@ -32,8 +34,9 @@
 //  * Intra-block global scan (Section 4.4, Algorithm 5).  Each element gets
 //    carry (+) block offset (+) lane offset (+) own prefix, and y is written
 //    exactly once: staged per warp in shared memory and stored with
-//    cp.async.bulk (full tiles), or with plain stores (ragged last tile and
-//    unaligned pointers).
+//    cp.async.bulk (full tiles) or with coalesced plain stores from the same
+//    staging (the ragged last tile); unaligned pointers take plain stores
+//    straight from registers.
 //  * Batched mode (MODE_SEGMENTED, not in the paper).  The producer warp
 //    marks segment heads of its tile in a bitmap (warp-parallel lower_bound
 //    on the offsets); the scan operator is lifted to (head flag, value); a
