@@ -8,6 +8,7 @@ torch is used for device memory and streams only.
     y = lscan.inclusive(x)                 # add, x: int32/float32/bfloat16
     y = lscan.exclusive(x, op="max")
     y = lscan.batched(x, offsets)          # offsets: int64 cuda tensor [S+1]
+    y = lscan.scan_host(x_cpu)             # x_cpu in (pinned) host memory
 """
 import torch
 
@@ -84,6 +85,39 @@ def scan(x, op="add", inclusive=True, out=None, *, precision=None,
                          x.data_ptr(), out.data_ptr(), x.shape[0], opts,
                          _stream_ptr(stream))
     _lib.check(st, "lscan_scan")
+    return out
+
+
+def scan_host(x, op="add", inclusive=True, out=None, *, chunk=0,
+              precision=None, carry=None, config=0, max_ctas=0, out_dtype=None,
+              stream=None, synchronize=True):
+    """Scan of a 1-D CPU tensor through the library's host-buffer entry point
+    (chunked copy-in, scan and copy-out, overlapped on the device).  Pinned
+    tensors (Tensor.pin_memory()) get full copy bandwidth.  out: optional
+    CPU tensor of the output dtype (may be x itself when the element sizes
+    match).  With synchronize=False the call returns once the work is queued
+    on stream; x and out must then stay alive until the stream reaches it."""
+    if not isinstance(x, torch.Tensor) or x.is_cuda:
+        raise TypeError("x must be a CPU tensor")
+    if x.dtype not in _DT:
+        raise TypeError(f"unsupported dtype {x.dtype}")
+    if x.dim() != 1 or not x.is_contiguous():
+        raise ValueError("x must be a contiguous 1-D tensor")
+    odt = out_dtype_for(op, x.dtype, out_dtype)
+    if out is None:
+        out = torch.empty(x.shape[0], dtype=odt, pin_memory=x.is_pinned())
+    elif (out.is_cuda or out.dtype != odt or out.shape != x.shape
+          or not out.is_contiguous()):
+        raise ValueError("out has the wrong device, dtype, shape or layout")
+    opts = _options(op, x.dtype, out_dtype, precision, carry, config, max_ctas)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = _lib.lscan_scan_host(_OPS[op], _DT[x.dtype], int(bool(inclusive)),
+                              x.data_ptr(), out.data_ptr(), x.shape[0], opts,
+                              int(chunk), stream.cuda_stream)
+    _lib.check(st, "lscan_scan_host")
+    if synchronize:
+        stream.synchronize()
     return out
 
 

@@ -169,3 +169,22 @@ def test_work_queued_after_sees_the_output():
     d.copy_(hy, non_blocking=True)
     got = d.cpu().numpy()
     assert np.array_equal(got, oracle.scan("add", "i32", x, True))
+
+
+def test_torch_front_scan_host():
+    """paper_1604_04815_gb300.scan_host: CPU tensors in and out, bf16 add
+    writing fp32, and the in-place form."""
+    import paper_1604_04815_gb300 as lscan
+    n = 70001
+    xb = _input("add", "bf16", n, seed=60)
+    hb = _host_tensor(xb, "bf16")
+    yb = lscan.scan_host(hb, chunk=20000)
+    assert yb.dtype == torch.float32 and not yb.is_cuda
+    assert_matches("add", "bf16", xb, yb.numpy(), True, "f64")
+    xi = _input("max", "i32", n, seed=61)
+    hi = _host_tensor(xi, "i32")
+    out = lscan.scan_host(hi, op="max", inclusive=False, out=hi, chunk=9000)
+    assert out.data_ptr() == hi.data_ptr()
+    assert_matches("max", "i32", xi, hi.numpy(), False)
+    with pytest.raises(TypeError):
+        lscan.scan_host(hi.cuda())
