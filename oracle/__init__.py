@@ -16,6 +16,7 @@ Python API (numpy in, numpy out):
     abs_segprefix(dtype, x, offsets, inclusive=True)
     bf16_to_double(bits)                           -> float
     select_flagged(x, flags)                       -> x[flags != 0] in order
+    radix_offsets(keys, digit_bits)                -> int64 [P, 2^digit_bits]
 op in {"add", "max"}; dtype in {"i32", "f32", "bf16", "i64", "f64"}; bf16
 data are uint16 bit patterns.  Output dtype: i32 add/max -> int32, f32/bf16
 add -> float64 (the FP64 reference), f32 max -> float32, bf16 max -> uint16
@@ -54,6 +55,9 @@ def _load():
                                              ctypes.c_int]
         lib.oracle_select_flagged.argtypes = [vp, vp, vp, i64, ctypes.c_int]
         lib.oracle_select_flagged.restype = i64
+        lib.oracle_radix_offsets.argtypes = [vp, ctypes.c_int, i64,
+                                             ctypes.c_int, vp]
+        lib.oracle_radix_offsets.restype = ctypes.c_int
         lib.oracle_bf16_to_double.argtypes = [ctypes.c_uint16]
         lib.oracle_bf16_to_double.restype = ctypes.c_double
         for f in (lib.oracle_scan, lib.oracle_segscan, lib.oracle_abs_prefix,
@@ -145,6 +149,25 @@ def select_flagged(x, flags):
     if k < 0:
         raise ValueError("oracle_select_flagged rejected its arguments")
     return y[:k]
+
+
+def radix_offsets(keys, digit_bits):
+    """Radix-sort digit offsets (a consumer of the scan): for unsigned keys
+    (uint32 or uint64), out[p, v] = number of keys whose digit p (digit_bits
+    wide, lowest first) is below v -- the exclusive scan of the digit-p
+    histogram, where bucket v starts in a counting-sort pass on digit p."""
+    k = np.ascontiguousarray(keys)
+    if k.dtype not in (np.uint32, np.uint64) or k.ndim != 1:
+        raise TypeError("keys must be a 1-D uint32 or uint64 array")
+    kb = k.dtype.itemsize
+    P = -(-8 * kb // int(digit_bits)) if 1 <= digit_bits <= 8 else 0
+    out = np.empty((max(P, 1), 1 << max(0, min(int(digit_bits), 8))),
+                   dtype=np.int64)
+    rc = _load().oracle_radix_offsets(k.ctypes.data, kb, k.shape[0],
+                                      int(digit_bits), out.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle_radix_offsets rejected its arguments")
+    return out
 
 
 def bf16_to_double(bits):

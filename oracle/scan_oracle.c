@@ -13,6 +13,7 @@
 #include "scan_oracle.h"
 
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 double oracle_bf16_to_double(uint16_t bits) {
@@ -212,6 +213,36 @@ int64_t oracle_select_flagged(const void *x, const uint8_t *flags, void *y,
         }
     }
     return k;
+}
+
+int oracle_radix_offsets(const void *keys, int key_bytes, int64_t n,
+                         int digit_bits, int64_t *offsets) {
+    if ((key_bytes != 4 && key_bytes != 8) || digit_bits < 1 || digit_bits > 8 ||
+        n < 0)
+        return -1;
+    const int key_bits = 8 * key_bytes;
+    const int P = (key_bits + digit_bits - 1) / digit_bits;
+    const int B = 1 << digit_bits;
+    const uint64_t mask = (uint64_t)B - 1u;
+    /* histogram of every digit position ... */
+    int64_t *count = (int64_t *)calloc((size_t)P * (size_t)B, sizeof(int64_t));
+    if (count == NULL) return -1;
+    for (int64_t j = 0; j < n; ++j) {
+        const uint64_t k = key_bytes == 4 ? (uint64_t)((const uint32_t *)keys)[j]
+                                          : ((const uint64_t *)keys)[j];
+        for (int p = 0; p < P; ++p)
+            ++count[(size_t)p * B + ((k >> (p * digit_bits)) & mask)];
+    }
+    /* ... then its exclusive scan over the digit values (Section 1) */
+    for (int p = 0; p < P; ++p) {
+        int64_t acc = 0;
+        for (int v = 0; v < B; ++v) {
+            offsets[(size_t)p * B + v] = acc;
+            acc += count[(size_t)p * B + v];
+        }
+    }
+    free(count);
+    return 0;
 }
 
 int oracle_abs_prefix(int dtype, const void *x, double *s, int64_t n,

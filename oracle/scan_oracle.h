@@ -85,6 +85,17 @@ int oracle_abs_segprefix(int dtype, const void *x, double *s,
 int64_t oracle_select_flagged(const void *x, const uint8_t *flags, void *y,
                               int64_t n, int elem_size);
 
+/* Radix-sort digit offsets (a consumer of the scan; not in the paper).
+ * keys: n unsigned integers of key_bytes (4 or 8) bytes.  Digit p of a key
+ * (p = 0 .. P-1, P = ceil(8 * key_bytes / digit_bits), lowest digit first)
+ * is (key >> (p * digit_bits)) & (2^digit_bits - 1).  With B = 2^digit_bits,
+ * offsets[p * B + v] is the number of keys whose digit p is less than v: the
+ * exclusive prefix sum over v of the digit-p histogram, i.e. where bucket v
+ * starts in a stable counting-sort pass on digit p.  Returns 0, or -1 on bad
+ * arguments (key_bytes not 4 or 8, digit_bits outside 1..8, n < 0). */
+int oracle_radix_offsets(const void *keys, int key_bytes, int64_t n,
+                         int digit_bits, int64_t *offsets);
+
 /* bf16 bit pattern -> double (exact). */
 double oracle_bf16_to_double(uint16_t bits);
 

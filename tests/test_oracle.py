@@ -475,3 +475,84 @@ def test_select_flagged_matches_mask_and_keeps_bits(oracle_mod, dtype, p_keep):
     assert got.dtype == x.dtype and np.array_equal(got.view(np.uint8),
                                                    want.view(np.uint8))
     assert got.shape[0] == int(np.count_nonzero(f))
+
+
+# ------------------------------------------------- radix-sort digit offsets
+def _digit(k, p, b):
+    return (int(k) >> (p * b)) & ((1 << b) - 1)
+
+
+def test_golden_radix_offsets(oracle_mod):
+    g = golden("radix_offsets.txt")
+    keys = np.array([int(v, 16) for v in g["keys"]], dtype=np.uint32)
+    got = oracle_mod.radix_offsets(keys, 8)
+    assert got.shape == (4, 256)
+    at = [int(v) for v in g["at_v"]]
+    for p in range(4):
+        assert [int(got[p, v]) for v in at] == [int(v) for v in g[f"p{p}"]]
+
+
+@pytest.mark.parametrize("kdt", [np.uint32, np.uint64])
+@pytest.mark.parametrize("b", [1, 3, 4, 5, 8])
+def test_radix_offsets_brute_force(oracle_mod, kdt, b):
+    """The definition itself, key by key: how many keys have a smaller
+    digit p than v (no histogram, no running sum)."""
+    rng = np.random.default_rng(b * 10 + np.dtype(kdt).itemsize)
+    kb = 8 * np.dtype(kdt).itemsize
+    keys = rng.integers(0, 2 ** kb, size=37, dtype=kdt)
+    got = oracle_mod.radix_offsets(keys, b)
+    P = -(-kb // b)
+    assert got.shape == (P, 1 << b)
+    for p in range(P):
+        digits = [_digit(k, p, b) for k in keys]
+        for v in range(1 << b):
+            assert got[p, v] == sum(1 for d in digits if d < v), (p, v)
+
+
+@pytest.mark.parametrize("b", [2, 5, 8])
+def test_radix_offsets_closed_form_identity_keys(oracle_mod, b):
+    """keys 0 .. 2^m - 1: the w = clamp(m - p b, 0, b) low bits of digit p
+    take every value equally often, so offsets[p][v] = min(v, 2^w) 2^(m-w)."""
+    m = 13
+    n = 1 << m
+    got = oracle_mod.radix_offsets(np.arange(n, dtype=np.uint32), b)
+    for p in range(got.shape[0]):
+        w = min(max(m - p * b, 0), b)
+        want = [min(v, 1 << w) * (n >> w) for v in range(1 << b)]
+        assert got[p].tolist() == want, p
+
+
+def test_radix_offsets_equal_keys_and_empty(oracle_mod):
+    k = np.uint64(0xDEADBEEF01234567)
+    got = oracle_mod.radix_offsets(np.full(100, k, dtype=np.uint64), 8)
+    for p in range(8):
+        d = _digit(k, p, 8)
+        assert got[p].tolist() == [0] * (d + 1) + [100] * (255 - d)
+    assert not oracle_mod.radix_offsets(np.zeros(0, np.uint32), 4).any()
+
+
+@pytest.mark.parametrize("kdt", [np.uint32, np.uint64])
+def test_radix_offsets_place_a_stable_counting_sort(oracle_mod, kdt):
+    """Scattering each key to offsets[p][digit] + (keys with the same digit
+    before it) must give numpy's stable sort by that digit, for every p."""
+    rng = np.random.default_rng(7)
+    kb = 8 * np.dtype(kdt).itemsize
+    keys = rng.integers(0, 2 ** kb, size=5000, dtype=kdt)
+    b = 6
+    off = oracle_mod.radix_offsets(keys, b)
+    for p in range(off.shape[0]):
+        d = ((keys >> kdt(p * b)) & kdt((1 << b) - 1)).astype(np.int64)
+        nxt = off[p].copy()
+        out = np.empty_like(keys)
+        for j in range(keys.shape[0]):
+            out[nxt[d[j]]] = keys[j]
+            nxt[d[j]] += 1
+        assert np.array_equal(out, keys[np.argsort(d, kind="stable")]), p
+
+
+def test_radix_offsets_rejects_bad_arguments(oracle_mod):
+    with pytest.raises(TypeError):
+        oracle_mod.radix_offsets(np.zeros(4, np.int32), 8)
+    for b in (0, 9):
+        with pytest.raises(ValueError):
+            oracle_mod.radix_offsets(np.zeros(4, np.uint32), b)
