@@ -15,6 +15,8 @@ Also reported on the same line:
                copy-out overlapped), all copies inside the timed region
   batched      4096 log-uniform arrays (lengths 1..2^20) in one persistent
                launch replayed from a CUDA graph, vs 4096 plain launches
+  select       stream compaction (a scan consumer), 2^28 int32, half kept
+  radix        radix-sort digit offsets (a scan consumer), 2^28 uint32 keys
   cpu_baseline the sequential CPU oracle timed on a bounded sample
   clocks       nvidia-smi samples taken during the timed region
 
@@ -415,6 +417,8 @@ def run_gpu(args, ws, rank, local):
     dtypes = None if args.no_dtypes else bench_dtypes(args, dev, stream, peak)
     small = None if args.no_small else bench_small(args, dev, stream)
     select = None if args.no_select else bench_select(args, dev, stream, peak)
+    radix = None if args.no_radix else bench_radix(args, dev, stream, peak,
+                                                   args.log2n)
 
     # ---- serving: Poisson stream through the continuous-batching server ----
     serving = None
@@ -446,6 +450,7 @@ def run_gpu(args, ws, rank, local):
         "dtypes": dtypes,
         "small": small,
         "select": select,
+        "radix": radix,
         "serving": serving,
         "clocks": clk,
     }
@@ -532,6 +537,35 @@ def bench_select(args, dev, stream, peak, log2n=28):
     return {"n": n, "dtype": "i32", "kept": k, "us": round(t * 1e6, 1),
             "gbs": round(gbs, 1), "frac_measured": round(gbs / peak, 4),
             "geps": round(n / t / 1e9, 2), "result_check": ok}
+
+
+def bench_radix(args, dev, stream, peak, log2n=28):
+    """Radix-sort digit offsets of 2^log2n uniform uint32 keys with 8-bit
+    digits (4 positions x 256 buckets) in one pass.  Algorithmic bytes: the
+    keys, 4 B each (the 8 KiB of counters and offsets are negligible)."""
+    import torch
+
+    import paper_1604_04815_gb300 as lscan
+    n = 1 << log2n
+    g = torch.Generator(device=dev)
+    g.manual_seed(10)
+    keys = torch.randint(0, 2 ** 32, (n,), device=dev, dtype=torch.int64,
+                         generator=g).to(torch.int32)
+    out = torch.empty((4, 256), dtype=torch.int64, device=dev)
+    with torch.cuda.stream(stream):
+        def run():
+            lscan.radix_offsets(keys, 8, out=out, stream=stream)
+        for _ in range(3):
+            run()
+        t = _time_launches(stream, run, 10)
+        # sanity check on the device (not a parity claim): the offsets of
+        # digit 0 against torch's own histogram of that digit
+        h0 = torch.bincount((keys & 255).long(), minlength=256)
+        ok = bool(torch.equal(out[0], torch.cumsum(h0, 0) - h0))
+    gbs = 4 * n / t / 1e9
+    return {"n": n, "key": "u32", "digit_bits": 8, "us": round(t * 1e6, 1),
+            "gbs": round(gbs, 1), "frac_measured": round(gbs / peak, 4),
+            "gkeys_per_s": round(n / t / 1e9, 2), "result_check": ok}
 
 
 def bench_small(args, dev, stream):
@@ -755,6 +789,7 @@ def main():
     ap.add_argument("--config", type=int, default=0)
     ap.add_argument("--carry", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-radix", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="elements per chunk of lscan_scan_host (0 = 2^23)")
     ap.add_argument("--no-batched", action="store_true")

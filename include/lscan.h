@@ -358,6 +358,29 @@ lscan_status lscan_select_flagged(lscan_dtype dtype, const void *x,
                                   const uint8_t *flags, void *y, int64_t n,
                                   int64_t *d_count, void *stream);
 
+/* Radix-sort digit offsets (a consumer of the scan; not in the paper, which
+ * lists radix sort among the applications of scan in Section 1).  keys: n
+ * unsigned integers of key_bytes (4 or 8) bytes in device memory, aligned
+ * to key_bytes (16-byte-aligned keys are read with 16-byte loads).  Digit p
+ * (p = 0 .. P-1, P = ceil(8 * key_bytes / digit_bits), lowest digit first)
+ * of a key is (key >> (p * digit_bits)) & (2^digit_bits - 1).  With
+ * B = 2^digit_bits, one pass over the keys writes
+ *     d_offsets[p * B + v] = number of keys whose digit p is below v,
+ * the exclusive scan of the digit-p histogram: where bucket v starts in a
+ * stable counting-sort pass on digit p.  d_offsets: P * B int64 in device
+ * memory, 8-byte aligned, not overlapping the keys.  Signed or float keys
+ * are mapped to order-preserving unsigned keys by the caller.
+ *  - digit_bits 1..8; 0 <= n <= 2^32 - 1; n = 0 writes zeros.  Otherwise
+ *    LSCAN_ERR_INVALID, before any device work.
+ *  - Scratch (2048 64-bit counters and a done word per (device, stream)) is
+ *    owned by the library, zeroed when allocated and left zeroed by each
+ *    launch; freed by lscan_shutdown.  Allocating it during stream capture
+ *    returns LSCAN_ERR_BUSY (call once outside capture first).
+ *  - Asynchronous on stream; one kernel launch, no device-side waits. */
+lscan_status lscan_radix_offsets(const void *keys, int32_t key_bytes, int64_t n,
+                                 int32_t digit_bits, int64_t *d_offsets,
+                                 void *stream);
+
 /* Describes a tile configuration: writes items per thread, consumer threads
  * per CTA, pipeline stages and tile length L for dtype `dtype`. */
 lscan_status lscan_config_info(int32_t config, lscan_dtype dtype,

@@ -149,6 +149,33 @@ def batched(x, offsets, op="add", inclusive=True, out=None, *, n_total=None,
     return out
 
 
+def radix_offsets(keys, digit_bits=8, out=None, *, stream=None):
+    """Radix-sort digit offsets of a 1-D CUDA tensor of keys (int32/uint32
+    or int64/uint64, read as unsigned), in one pass: out[p, v] = number of
+    keys whose digit p (digit_bits wide, lowest first) is below v, i.e. where
+    bucket v starts in a counting-sort pass on digit p.  Returns an int64
+    CUDA tensor of shape (ceil(key_bits / digit_bits), 2^digit_bits)."""
+    if (not isinstance(keys, torch.Tensor) or not keys.is_cuda
+            or keys.dim() != 1 or not keys.is_contiguous()):
+        raise TypeError("keys must be a contiguous 1-D CUDA tensor")
+    kb = keys.element_size()
+    if kb not in (4, 8) or keys.is_floating_point():
+        raise TypeError("keys must be 32- or 64-bit integers")
+    if not 1 <= int(digit_bits) <= 8:
+        raise ValueError("digit_bits must be 1..8")
+    shape = (-(-8 * kb // int(digit_bits)), 1 << int(digit_bits))
+    if out is None:
+        out = torch.empty(shape, dtype=torch.int64, device=keys.device)
+    elif (out.dtype != torch.int64 or tuple(out.shape) != shape
+          or not out.is_contiguous() or not out.is_cuda):
+        raise ValueError("out has the wrong dtype, shape or layout")
+    st = _lib.lscan_radix_offsets(keys.data_ptr(), kb, keys.shape[0],
+                                  int(digit_bits), out.data_ptr(),
+                                  _stream_ptr(stream))
+    _lib.check(st, "lscan_radix_offsets")
+    return out
+
+
 def select_flagged(x, flags, out=None, *, stream=None):
     """Stream compaction: the elements of x whose flag (uint8/bool) is
     nonzero, in order, in one pass.  Returns (out, count): out has len(x)

@@ -39,7 +39,7 @@ EXPORTED = [
     "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
     "lscan_server_hold",
     "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
-    "lscan_tune_reset", "lscan_select_flagged",
+    "lscan_tune_reset", "lscan_select_flagged", "lscan_radix_offsets",
 ]
 
 
@@ -98,6 +98,8 @@ def load():
                                        optp, ctypes.POINTER(vp)],
         "lscan_scan_noalloc": [i32, i32, i32, vp, vp, i64, vp],
         "lscan_select_flagged": [i32, vp, vp, vp, i64, vp, vp],
+        "lscan_radix_offsets": [vp, ctypes.c_int32, i64, ctypes.c_int32, vp,
+                                vp],
         "lscan_graph_launch": [vp, vp],
         "lscan_graph_status": [vp],
         "lscan_stream_status": [vp],
@@ -199,6 +201,12 @@ def lscan_scan_noalloc(op, dtype, inclusive, x, y, n, stream=None):
 
 def lscan_select_flagged(dtype, x, flags, y, n, d_count, stream=None):
     return load().lscan_select_flagged(dtype, x, flags, y, n, d_count, stream)
+
+
+def lscan_radix_offsets(keys, key_bytes, n, digit_bits, d_offsets,
+                        stream=None):
+    return load().lscan_radix_offsets(keys, key_bytes, n, digit_bits,
+                                      d_offsets, stream)
 
 
 def lscan_batched(op, dtype, inclusive, x, y, d_offsets, n_seg, n_total,

@@ -455,6 +455,7 @@ lscan_status lscan_reserve(void *stream, int64_t max_elems) {
 
 void lscan_shutdown(void) {
     shutdown_host_pipes();
+    shutdown_radix();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

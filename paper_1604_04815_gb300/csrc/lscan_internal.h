@@ -57,6 +57,7 @@ int tuned_variant(int kind, int mode, int64_t n);
 std::mutex &api_mutex();
 void shutdown_graphs_locked();
 void shutdown_host_pipes();  // frees the staging of lscan_scan_host
+void shutdown_radix();       // frees the counters of lscan_radix_offsets
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
 void set_tuned_variant(int kind, int mode, int size_cls, int variant);

@@ -17,6 +17,8 @@ that and the workload list of this library:
                    uniform in [0, 1), seed 5
   serving        : Poisson arrivals, sizes round(2^(10 + 14 U)), dtype
                    int32/fp32/bf16 at 50/35/15 %, op add/max at 50/50, seed 6
+  radix_keys     : uint32 keys, N = 2^28, uniform over all 2^32 values (the
+                   usual radix-sort benchmark input), seed 7
 
 bf16 arrays are carried as uint16 bit patterns.
 """
@@ -30,6 +32,7 @@ SEEDS = {
     "precision": 4,
     "batched": 5,
     "serving": 6,
+    "radix_keys": 7,
 }
 
 
@@ -65,6 +68,11 @@ def large_i32_max(n=1 << 28, seed=SEEDS["large_i32_max"]):
 def large_f32_add(n=1 << 28, seed=SEEDS["large_f32_add"]):
     rng = np.random.default_rng(seed)
     return rng.random(size=n, dtype=np.float32)
+
+
+def radix_keys(n=1 << 28, seed=SEEDS["radix_keys"]):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 2 ** 32, size=n, dtype=np.uint32)
 
 
 def precision(n=1 << 26, seed=SEEDS["precision"]):

@@ -193,3 +193,22 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     assert json.loads(out.read_text())["entries"] == [[5, 0, 27, 2]]
     assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_autotune(0, 0, 1, 16, 32, 0)[0] == lib.LSCAN_ERR_INVALID
+
+
+def test_radix_offsets_argument_checks(lib):
+    """lscan_radix_offsets refuses bad arguments before any CUDA call."""
+    L = lib
+    f = L.lscan_radix_offsets
+    base = 1 << 20
+    out = base * 64
+    assert f(base, 2, 10, 8, out) == L.LSCAN_ERR_INVALID     # key size
+    assert f(base, 4, 10, 0, out) == L.LSCAN_ERR_INVALID     # digit bits
+    assert f(base, 4, 10, 9, out) == L.LSCAN_ERR_INVALID
+    assert f(base, 4, -1, 8, out) == L.LSCAN_ERR_INVALID
+    assert f(base, 4, 1 << 32, 8, out) == L.LSCAN_ERR_INVALID
+    assert f(base, 4, 10, 8, None) == L.LSCAN_ERR_INVALID
+    assert f(base, 4, 10, 8, out + 4) == L.LSCAN_ERR_INVALID  # misaligned
+    assert f(None, 4, 10, 8, out) == L.LSCAN_ERR_INVALID
+    assert f(base + 2, 4, 10, 8, out) == L.LSCAN_ERR_INVALID
+    assert f(base + 4, 8, 10, 8, out) == L.LSCAN_ERR_INVALID
+    assert f(base, 4, 1000, 8, base + 64) == L.LSCAN_ERR_INVALID  # overlap
