@@ -359,7 +359,8 @@ lscan_status lscan_select_flagged(lscan_dtype dtype, const void *x,
                                   int64_t *d_count, void *stream);
 
 /* Radix-sort digit offsets (a consumer of the scan; not in the paper, which
- * lists radix sort among the applications of scan in Section 1).  keys: n
+ * lists parallel sorting among the applications of scan in Section 1; radix
+ * sort is the sort built on it).  keys: n
  * unsigned integers of key_bytes (4 or 8) bytes in device memory, aligned
  * to key_bytes (16-byte-aligned keys are read with 16-byte loads).  Digit p
  * (p = 0 .. P-1, P = ceil(8 * key_bytes / digit_bits), lowest digit first)

@@ -1,11 +1,11 @@
 // radix_offsets.cu -- radix-sort digit offsets in one pass over the keys.
 //
-// Not in the paper: radix sort is one of the applications of scan it lists
-// (Section 1).  A radix-sort pass on digit p moves each key to the start of
-// its bucket plus its rank among the keys with the same digit before it; the
-// bucket starts are the exclusive scan of the digit-p histogram.  This
-// kernel produces them for every digit position at once, reading the keys
-// once:
+// Not in the paper, which lists parallel sorting among the applications of
+// scan (Section 1); radix sort is the sort built on it.  A radix-sort pass
+// on digit p moves each key to the start of its bucket plus its rank among
+// the keys with the same digit before it; the bucket starts are the
+// exclusive scan of the digit-p histogram.  This kernel produces them for
+// every digit position at once, reading the keys once:
 //  * Histograms.  A persistent grid streams the keys with 16-byte loads
 //    (grid-stride, four vectors in flight per thread) and counts every digit
 //    of every key into its warp's copy of the P x B counters in shared
