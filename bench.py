@@ -412,9 +412,13 @@ def run_gpu(args, ws, rank, local):
                "h2d_bytes_per_step": sum(x.nbytes for x in host.values()),
                "d2h_bytes_per_step": sum(x.nbytes for x in host.values()),
                "steps": ksteps, "result_check": bool(ok),
-               "path": "lscan_scan_host from pinned host buffers: chunks of "
-                       f"{args.e2e_chunk or 1 << 23} elements, copy-in, scan "
-                       "and copy-out overlapped on three streams"}
+               "path": "lscan_scan_host from pinned host buffers: " +
+                       (f"chunks of {args.e2e_chunk} elements"
+                        if args.e2e_chunk else
+                        "chunks of 2^20 doubling to 2^23 elements and halving "
+                        "again at the end") +
+                       ", copy-in, scan and copy-out overlapped on three "
+                       "streams"}
         del hx, hy
 
     # ---- batched: one graph-replayed persistent launch vs 4096 launches ----
@@ -800,7 +804,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-radix", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=0,
-                    help="elements per chunk of lscan_scan_host (0 = 2^23)")
+                    help="elements per chunk of lscan_scan_host (0 = the "
+                         "library's ramped schedule)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-dtypes", action="store_true")
     ap.add_argument("--no-small", action="store_true")

@@ -135,9 +135,12 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
  * LSCAN_ERR_INVALID.  Page-locked memory (cudaHostAlloc / cudaHostRegister)
  * gets full copy bandwidth and overlap; pageable memory is accepted, but its
  * copies are staged by the CUDA driver and overlap less.
- *  - The array moves in chunks of `chunk` elements (0 = 2^23) through three
- *    device slots: chunk k is copied in while chunk k-1 is scanned on
- *    `stream` and chunk k-2 is copied out, on two internal streams.  Chunk
+ *  - The array moves in chunks of `chunk` elements through three device
+ *    slots: chunk k is copied in while chunk k-1 is scanned on `stream` and
+ *    chunk k-2 is copied out, on two internal streams.  chunk = 0 lets the
+ *    library choose: chunks that double from 2^20 to 2^23 elements at the
+ *    start and halve again over the last 2^24, so that the first copy-in
+ *    and the last copy-out, which overlap nothing, are short.  Chunk
  *    k > 0 starts from the inclusive total of chunks 0..k-1, handed on in
  *    the kind's carry type (FP64 for the float adds with an FP64 carry), so
  *    the results meet the same rules and bounds as lscan_scan over the whole
@@ -147,7 +150,8 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
  *  - Asynchronous on stream: the copies start after the work already queued
  *    on stream, and work queued on stream afterwards runs after the last
  *    element of hy is written.  hx and hy must stay valid until then.
- *  - The device slots (3 x chunk x (input + output element size) bytes) are
+ *  - The device slots (3 x chunk (2^23 for chunk = 0) x (input + output
+ *    element size) bytes) are
  *    owned by the library per (device, stream), grow on demand (after the
  *    previous call's copies finish) and are freed by lscan_shutdown.
  *  - Not capturable: returns LSCAN_ERR_UNSUPPORTED while stream is being

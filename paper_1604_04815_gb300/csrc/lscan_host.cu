@@ -25,6 +25,22 @@ namespace {
 
 constexpr int kSlots = 3;  // in flight: copy-in, scan, copy-out
 constexpr int64_t kDefaultChunk = int64_t{1} << 23;
+constexpr int64_t kRampChunk = int64_t{1} << 20;  // first and last chunks
+
+// Length of chunk k when `remaining` elements are left.  Fixed chunks of C,
+// or (ramp) chunks that double from kRampChunk up to C and halve again over
+// the last 2 C elements: the first copy-in and the last copy-out overlap
+// nothing, so they are kept short.
+int64_t chunk_len(int64_t k, int64_t remaining, int64_t C, bool ramp) {
+    if (!ramp || C <= kRampChunk) return remaining < C ? remaining : C;
+    int64_t up = kRampChunk << (k < 16 ? k : 16);
+    if (up > C) up = C;
+    const int64_t half = (remaining + 1) / 2;
+    const int64_t down = remaining <= kRampChunk ? remaining
+                                                 : (half > kRampChunk ? half : kRampChunk);
+    const int64_t m = up < down ? up : down;
+    return m < remaining ? m : remaining;
+}
 
 struct HostPipe {
     int device = -1;
@@ -200,12 +216,11 @@ extern "C" lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int incl
     const char *bx = static_cast<const char *>(hx);
     char *by = static_cast<char *>(hy);
     char *car = static_cast<char *>(p->car);
-    const int64_t n_chunks = (n + C - 1) / C;
     int last = 0;
-    for (int64_t k = 0; k < n_chunks; ++k) {
+    int64_t off = 0;
+    for (int64_t k = 0; off < n; ++k) {
         const int s = static_cast<int>(k % kSlots);
-        const int64_t off = k * C;
-        const int64_t m = (n - off) < C ? (n - off) : C;
+        const int64_t m = chunk_len(k, n - off, C, chunk == 0);
         // copy in once the slot's previous chunk has been copied out (which
         // also orders it after that chunk's scan)
         if (cudaStreamWaitEvent(p->h2d, p->out_done[s], 0) != cudaSuccess ||
@@ -226,7 +241,7 @@ extern "C" lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int incl
             ls.carry_in = car + 16 * ((k - 1) & 1);
             ls.carry_in_car = true;
         }
-        ls.total_out = k + 1 < n_chunks ? car + 16 * (k & 1) : nullptr;
+        ls.total_out = off + m < n ? car + 16 * (k & 1) : nullptr;
         st = run_planned(ls, stream);
         if (st != LSCAN_OK) return st;
         // copy out after the scan
@@ -237,6 +252,7 @@ extern "C" lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int incl
             cudaEventRecord(p->out_done[s], p->d2h) != cudaSuccess)
             return LSCAN_ERR_CUDA;
         last = s;
+        off += m;
     }
     // join: work queued on the stream later runs after the last copy-out
     // (the copy-outs run in order on one stream)

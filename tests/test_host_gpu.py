@@ -87,8 +87,10 @@ def test_chunked_matches_oracle(kind, inclusive):
     op, dtype, prec, ob = kind
     # (n, chunk): chunks that split tiles with a ragged last chunk, chunks
     # for the single-CTA kernel, one chunk larger than n, and the default
+    # schedule (one chunk, then chunks ramping up from 2^20 and down again)
     for i, (n, chunk) in enumerate([(47123, 10000), (10001, 3000), (777, 5000),
-                                    (1, 0), (65537, 0)]):
+                                    (1, 0), (65537, 0),
+                                    (3 * 2 ** 20 + 12345, 0)]):
         x = _input(op, dtype, n, seed=900 + i)
         hx = _host_tensor(x, dtype)
         hy = torch.empty(n, dtype=out_torch_dtype(op, dtype, ob)).pin_memory()
