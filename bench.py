@@ -42,9 +42,10 @@ if ROOT not in sys.path:
 N = 1 << 28
 METRIC = ("scan GB/s & % of HBM peak, batched vs per-array; "
           "p50/p99 served latency")
-WORKLOAD = ("single-array inclusive scans, N=2^28 each: int32 add (uniform "
-            "[-2^15,2^15]), int32 max (full int32 range), fp32 add (uniform "
-            "[0,1), FP64 carry)")
+def _workload(n):
+    return (f"single-array inclusive scans, N=2^{n.bit_length() - 1} each: "
+            "int32 add (uniform [-2^15,2^15]), int32 max (full int32 range), "
+            "fp32 add (uniform [0,1), FP64 carry)")
 CASES = [  # (name, op, dtype)
     ("i32_add", "add", "i32"),
     ("i32_max", "max", "i32"),
@@ -109,10 +110,10 @@ _TRAFFIC = {
 }
 
 
-def _traffic_for(kernel_case, config):
-    """DRAM bytes per launch measured on the current kernel sources and tile
-    configuration, or None."""
-    if _TRAFFIC["kernel_source_hash"] != _kernel_source_hash():
+def _traffic_for(kernel_case, config, n):
+    """DRAM bytes per launch measured on the current kernel sources, tile
+    configuration and size (N = 2^28 only), or None."""
+    if n != 1 << 28 or _TRAFFIC["kernel_source_hash"] != _kernel_source_hash():
         return None
     return _TRAFFIC["bytes_per_launch"].get((kernel_case, config))
 
@@ -253,7 +254,7 @@ def run_reference(args, ws, rank):
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N,
+        "config": {"workload": _workload(N), "n": N,
                    "sample": "first 2^26 elements of each array per step"},
         "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1,
                          "kind": "oracle",
@@ -357,7 +358,7 @@ def run_gpu(args, ws, rank, local):
                 "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4),
                 "traffic": _traffic_for(
-                    dom, args.config or tuned.get(dom, {}).get("config")),
+                    dom, args.config or tuned.get(dom, {}).get("config"), N),
                 "kernel": dom,
                 "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": 2 * N * 4}
@@ -429,7 +430,8 @@ def run_gpu(args, ws, rank, local):
     # ---- the paper's data types (Table 2) and the small-array latency ----
     dtypes = None if args.no_dtypes else bench_dtypes(args, dev, stream, peak)
     small = None if args.no_small else bench_small(args, dev, stream)
-    select = None if args.no_select else bench_select(args, dev, stream, peak)
+    select = None if args.no_select else bench_select(args, dev, stream, peak,
+                                                      args.log2n)
     radix = None if args.no_radix else bench_radix(args, dev, stream, peak,
                                                    args.log2n)
 
@@ -448,7 +450,7 @@ def run_gpu(args, ws, rank, local):
         "ms_per_step": round(1e3 * elapsed_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32/f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": N, "tile_config": args.config or tuned,
+        "config": {"workload": _workload(N), "n": N, "tile_config": args.config or tuned,
                    "carry": ["auto", "lookback", "chained"][args.carry],
                    "l2": "inputs 1 GiB per array > 129 MB L2; no flush",
                    "parallelism": f"replicas x{ws}"},
