@@ -58,3 +58,44 @@ def test_full_size_from_host(case):
     got = hy.numpy().copy()
     del hx, hy
     assert_matches(op, dtype, x, got, True, "f64")
+
+
+@pytest.mark.parametrize("dtype", ["i32", "f32"])
+def test_full_size_batched_graph(dtype):
+    """The batched workload bench.py times: 4096 arrays with log-uniform
+    lengths in [1, 2^20] (3.1e8 elements) in one persistent segmented launch
+    replayed from a CUDA graph; every element against the oracle after the
+    second replay (each replay re-arms its own scratch)."""
+    import paper_1604_04815_gb300 as lscan
+    x, off = workloads.batched(dtype)
+    xd = torch.from_numpy(x).cuda()
+    od = torch.from_numpy(off).cuda()
+    yd = torch.empty_like(xd)
+    g = lscan.Graph.batched(xd, od, yd)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    g.status()
+    got = yd.cpu().numpy()
+    g.close()
+    del xd, od, yd
+    torch.cuda.empty_cache()
+    assert_matches("add", dtype, x, got, True, "f64", offsets=off)
+
+
+def test_full_size_select():
+    """Stream compaction as bench.py times it: 2^28 int32 values, byte flags,
+    about half kept; compared with the oracle's compaction."""
+    import oracle
+    import paper_1604_04815_gb300 as lscan
+    rng = np.random.default_rng(11)
+    x = rng.integers(-1000, 1001, size=N, dtype=np.int32)
+    f = (rng.random(N) < 0.5).astype(np.uint8)
+    xd = torch.from_numpy(x).cuda()
+    fd = torch.from_numpy(f).cuda()
+    out, count = lscan.select_flagged(xd, fd)
+    k = int(count.item())
+    lscan.stream_status()
+    want = oracle.select_flagged(x, f)
+    assert k == want.shape[0]
+    assert np.array_equal(out[:k].cpu().numpy(), want)
