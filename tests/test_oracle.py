@@ -241,6 +241,22 @@ def test_brute_force_f32_exact_within_fp64(oracle_mod, n):
         assert err <= Fraction(n) * Fraction(2) ** -53 * Fraction(float(s[j]))
 
 
+@pytest.mark.parametrize("n", [1, 5, 31, 64])
+def test_brute_force_bf16_add_exact_within_fp64(oracle_mod, n):
+    """bf16 add: the FP64 reference of the decoded inputs against the exact
+    rational prefix of (bits << 16) read as IEEE singles."""
+    rng = np.random.default_rng(250 + n)
+    b = rng.integers(0, 1 << 16, size=n, dtype=np.uint16)
+    b = b[((b >> 7) & 0xFF) != 0xFF]  # no Inf/NaN
+    vals = [struct.unpack("<f", struct.pack("<I", int(v) << 16))[0] for v in b]
+    exact = _brute("add", [Fraction(v) for v in vals])
+    got = oracle_mod.scan("add", "bf16", b)
+    s = np.cumsum(np.abs(np.array(vals, dtype=np.float64)))
+    for j in range(len(vals)):
+        err = abs(Fraction(float(got[j])) - exact[j])
+        assert err <= Fraction(len(vals)) * Fraction(2) ** -53 * Fraction(float(s[j]))
+
+
 @pytest.mark.parametrize("n", [1, 9, 64])
 def test_brute_force_max_first_occurrence(oracle_mod, n):
     """Max-scan bits are those of the FIRST occurrence of the prefix max."""
