@@ -80,3 +80,17 @@ def test_reference_arm_under_torchrun_prints_once():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_reported_only_for_the_measured_sources_and_size(monkeypatch):
+    """roofline.traffic is the ncu figure only for N = 2^28 and the kernel
+    sources it was taken on; any other size or a changed source is null."""
+    b = _bench()
+    key = next(iter(b._TRAFFIC["bytes_per_launch"]))
+    want = b._TRAFFIC["bytes_per_launch"][key]
+    if b._kernel_source_hash() == b._TRAFFIC["kernel_source_hash"]:
+        assert b._traffic_for(key[0], key[1], 1 << 28) == want
+    assert b._traffic_for(key[0], key[1], 1 << 26) is None
+    monkeypatch.setitem(b._TRAFFIC, "kernel_source_hash", "0" * 16)
+    assert b._traffic_for(key[0], key[1], 1 << 28) is None
+    assert "N=2^26" in b._workload(1 << 26)
