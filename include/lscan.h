@@ -150,10 +150,10 @@ lscan_status lscan_scan(lscan_op op, lscan_dtype dtype, int inclusive,
  *  - Asynchronous on stream: the copies start after the work already queued
  *    on stream, and work queued on stream afterwards runs after the last
  *    element of hy is written.  hx and hy must stay valid until then.
- *  - The device slots (3 x chunk (2^23 for chunk = 0) x (input + output
- *    element size) bytes) are
- *    owned by the library per (device, stream), grow on demand (after the
- *    previous call's copies finish) and are freed by lscan_shutdown.
+ *  - The device slots, 3 x chunk (at most 2^23 for chunk = 0) x (input +
+ *    output element size) bytes, are owned by the library per (device,
+ *    stream), grow on demand (after the previous call's copies finish) and
+ *    are freed by lscan_shutdown.
  *  - Not capturable: returns LSCAN_ERR_UNSUPPORTED while stream is being
  *    captured.  Device-side carry timeouts latch on stream as for
  *    lscan_scan (lscan_stream_status).  After LSCAN_ERR_CUDA or
@@ -172,9 +172,10 @@ lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int inclusive,
  * options, but its scratch (control block + per-tile status words) is a
  * fixed array compiled into the library: 2 MiB + 512 B that every GPU which
  * loads the library keeps until the process exits.
- *  - n is limited by that array: at most 262144 status words, two per tile
- *    (every kind); with the default 4096-element tile that is 2^29
- *    elements.  Larger n returns LSCAN_ERR_INVALID without launching.
+ *  - n is limited by that array: at most 262144 status words, 2 or 4 per
+ *    tile by kind and tile configuration; for int32 with its default
+ *    4096-element tiles that is 2^29 elements, for the 8-byte types 2^28.
+ *    Larger n returns LSCAN_ERR_INVALID without launching.
  *  - The first call on a device looks up the array and clears it with
  *    cudaMemsetAsync on `stream`; make that first call before any capture.
  *  - Every call shares the array (it keeps the last call's contents; each
