@@ -10,9 +10,10 @@
 // fixed scratch area compiled into the library instead.
 //
 // The scratch is the same thing the regular path allocates: a control block
-// (tile ticket, finished-CTA count, epoch, error word) and one status word per
-// tile.  It lives in a file-scope __device__ array, so every GPU that loads
-// the library holds kNoAllocScratchBytes of it until the process exits.
+// (tile ticket, finished-CTA count, epoch, error word) and a status slot of 2
+// or 4 words per tile.  It lives in a file-scope __device__ array, so every
+// GPU that loads the library holds its 2 MiB + 512 B until the process
+// exits.
 //
 // Rules for callers (also stated in include/lscan.h):
 //  - The first call on each device looks up the array's device address and
