@@ -360,6 +360,49 @@ def test_abs_prefix_properties(oracle_mod):
     np.testing.assert_array_equal(ss[10:], oracle_mod.abs_prefix("f32", x[10:]))
 
 
+def test_golden_abs_prefix_bf16_and_i32(oracle_mod):
+    """The bf16 branch decodes bit patterns and the int32 branch widens
+    before taking |x| (|INT32_MIN| = 2^31)."""
+    g = golden("abs_prefix.txt")
+    xb = np.array([int(v, 16) for v in g["bf16_x"]], dtype=np.uint16)
+    for incl, key in ((True, "bf16_inclusive"), (False, "bf16_exclusive")):
+        want = np.array([float(v) for v in g[key]])
+        assert np.array_equal(oracle_mod.abs_prefix("bf16", xb, incl), want)
+    xi = np.array([int(v) for v in g["i32_x"]], dtype=np.int32)
+    for incl, key in ((True, "i32_inclusive"), (False, "i32_exclusive")):
+        want = np.array([float(v) for v in g[key]])
+        assert np.array_equal(oracle_mod.abs_prefix("i32", xi, incl), want)
+
+
+@pytest.mark.parametrize("n", [1, 17, 300])
+def test_abs_prefix_bf16_i32_brute_force(oracle_mod, n):
+    """Exact rational / integer sums of |x_i| with an independent decode
+    (struct) of the bf16 bits; every partial sum here is exact in FP64."""
+    import struct
+    from fractions import Fraction
+    rng = np.random.default_rng(n)
+    # random signs and mantissas, biased exponents 120..135: the sums span
+    # fewer than 53 bits, so each FP64 partial sum is exact
+    sign = rng.integers(0, 2, size=n) << 15
+    expo = rng.integers(120, 136, size=n) << 7
+    mant = rng.integers(0, 128, size=n)
+    xb = (sign | expo | mant).astype(np.uint16)
+    vals = [abs(Fraction(struct.unpack(">f", struct.pack(">I", int(b) << 16))[0]))
+            for b in xb]
+    got = oracle_mod.abs_prefix("bf16", xb)
+    acc = Fraction(0)
+    for j, v in enumerate(vals):
+        acc += v
+        assert Fraction(got[j]) == acc
+    xi = rng.integers(-(1 << 31), 1 << 31, size=n, dtype=np.int32)
+    xi[0] = -(1 << 31)
+    got = oracle_mod.abs_prefix("i32", xi, inclusive=False)
+    acc = 0
+    for j, v in enumerate(xi.tolist()):
+        assert got[j] == acc
+        acc += abs(v)
+
+
 # ------------------------------------------------------ int64 and double
 def test_golden_i64_wrap(oracle_mod):
     g = golden("scan_i64_wrap.txt")
