@@ -45,7 +45,7 @@ METRIC = ("scan GB/s & % of HBM peak, batched vs per-array; "
 def _workload(n):
     return (f"single-array inclusive scans, N=2^{n.bit_length() - 1} each: "
             "int32 add (uniform [-2^15,2^15]), int32 max (full int32 range), "
-            "fp32 add (uniform [0,1), FP64 carry)")
+            "fp32 add (uniform [0,1), double-float carry)")
 CASES = [  # (name, op, dtype)
     ("i32_add", "add", "i32"),
     ("i32_max", "max", "i32"),
@@ -92,8 +92,8 @@ def _kernel_source_hash():
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
-# the bench's kernels at N = 2^28, from one single-pass ncu capture of this
-# bench (summary and command: profiles/dram_traffic_bench_n2e28.md).  Valid
+# the bench's kernels at N = 2^28, from one ncu capture of this bench's
+# kernels (the summary and its command are kept with the profiles).  Valid
 # only for the kernel sources it was taken on: any change to csrc/ makes the
 # reported traffic null until it is measured again (files listed in
 # _NOT_SCAN_SOURCES excepted).
@@ -302,15 +302,24 @@ def run_gpu(args, ws, rank, local):
     tuned = {}
     if args.config == 0:
         for c, op, dt in CASES:
-            st, best, ms = _lib.lscan_autotune(
+            st, res = _lib.lscan_autotune(
                 _lib.LSCAN_ADD if op == "add" else _lib.LSCAN_MAX,
                 _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32, 1,
                 xs[c].data_ptr(), ys[c].data_ptr(), N,
-                opts=_lib.make_options(carry=args.carry), reps=3, stream=sp)
+                opts=_lib.make_options(carry=args.carry), reps=args.tune_reps,
+                stream=sp)
             _lib.check(st, "lscan_autotune")
+            best = res["config"]
             info = _lib.lscan_config_info(best, _lib.LSCAN_I32)
             tuned[c] = {"config": best, "items": info["items"],
-                        "threads": info["threads"], "tile": info["tile"]}
+                        "threads": info["threads"], "tile": info["tile"],
+                        "stages": info["stages"],
+                        "tuned_ms": round(res["ms"], 4),
+                        "default_config": res["default_config"],
+                        "default_ms": round(res["default_ms"], 4),
+                        "gain_vs_default": round(
+                            res["default_ms"] / res["ms"], 4),
+                        "configs_timed": res["n_timed"]}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             for c, op, dt in CASES:
@@ -422,6 +431,12 @@ def run_gpu(args, ws, rank, local):
                        "streams"}
         del hx, hy
 
+    # the host link's own ceiling for the same traffic
+    if e2e is not None and not args.no_link:
+        link = host_link_ceiling(dev)
+        e2e["host_link"] = link
+        e2e["frac_of_duplex_copy"] = round(e2e["value"] / link["duplex_gbs"], 4)
+
     # ---- batched: one graph-replayed persistent launch vs 4096 launches ----
     batched = None
     if not args.no_batched:
@@ -429,6 +444,10 @@ def run_gpu(args, ws, rank, local):
 
     # ---- the paper's data types (Table 2) and the small-array latency ----
     dtypes = None if args.no_dtypes else bench_dtypes(args, dev, stream, peak)
+    precision = None if args.no_precision else bench_precision(
+        args, dev, stream, peak, min(26, args.log2n))
+    bf16 = None if args.no_bf16 else bench_bf16(args, dev, stream, peak,
+                                                args.log2n)
     small = None if args.no_small else bench_small(args, dev, stream)
     select = None if args.no_select else bench_select(args, dev, stream, peak,
                                                       args.log2n)
@@ -437,10 +456,9 @@ def run_gpu(args, ws, rank, local):
 
     # ---- serving: Poisson stream through the continuous-batching server ----
     serving = None
-    if args.serving_full:
-        serving = bench_serving(args, dev, peak, 20000, [0.5, 0.8, 0.95])
-    elif not args.no_serving:
-        serving = bench_serving(args, dev, peak, args.serving_requests, [0.8])
+    if not args.no_serving:
+        serving = bench_serving(args, dev, peak, args.serving_requests,
+                                [float(f) for f in args.serving_loads.split(",")])
 
     if rank != 0:
         return 0
@@ -463,6 +481,8 @@ def run_gpu(args, ws, rank, local):
         "e2e": e2e,
         "batched": batched,
         "dtypes": dtypes,
+        "precision": precision,
+        "bf16": bf16,
         "small": small,
         "select": select,
         "radix": radix,
@@ -520,6 +540,160 @@ def bench_dtypes(args, dev, stream, peak, log2n=27):
             del x, y
     lscan.stream_status(stream)
     return out
+
+
+PREC_PATHS = ("plain", "f64", "df", "comp")
+
+
+def bench_precision(args, dev, stream, peak, log2n=26):
+    """The precision workload: N = 2^26 values s * exp(2 Z) (log-normal with
+    random signs, cancellation-heavy), fp32 and bf16 inputs, every carry
+    path (plain fp32, FP64, double-float, compensated).  Per result: GB/s of
+    the timed launches and max_j |err_j| / S_j and max_j |err_j| against an
+    FP64 reference taken outside the timed region (numpy's sequential
+    float64 cumsum of the exactly widened inputs; S_j = the float64 cumsum of
+    |x_i|).  Gates: 1e-5 for plain/FP64/double-float, 2.5e-7 compensated."""
+    import torch
+
+    from paper_1604_04815_gb300 import _lib, workloads
+    n = 1 << log2n
+    x32, xb = workloads.precision(n)
+    codes = {"plain": _lib.LSCAN_PREC_F32_CARRY,
+             "f64": _lib.LSCAN_PREC_F64_CARRY,
+             "df": _lib.LSCAN_PREC_DF_CARRY,
+             "comp": _lib.LSCAN_PREC_COMPENSATED}
+    gate = {"plain": 1e-5, "f64": 1e-5, "df": 1e-5, "comp": 2.5e-7}
+    out = {"n": n, "input": "s*exp(2Z), Z~N(0,1), s=+-1, seed 4",
+           "reference": "float64 cumsum of the widened inputs (numpy, "
+                        "sequential)"}
+    sp = stream.cuda_stream
+    for name, host, dcode, in_b in (
+            ("f32", x32, _lib.LSCAN_F32, 4),
+            ("bf16", xb, _lib.LSCAN_BF16, 2)):
+        x64 = (host.astype(np.float64) if name == "f32" else
+               workloads.bf16_bits_to_f32(host).astype(np.float64))
+        ref = np.cumsum(x64)
+        S = np.cumsum(np.abs(x64))
+        del x64
+        if name == "f32":
+            xd = torch.from_numpy(host).to(dev)
+        else:
+            xd = torch.from_numpy(host.view(np.int16)).to(dev)
+        yd = torch.empty(n, dtype=torch.float32, device=dev)
+        res = {}
+        for path in PREC_PATHS:
+            o = _lib.make_options(precision=codes[path])
+
+            def run():
+                st = _lib.lscan_scan(_lib.LSCAN_ADD, dcode, 1, xd.data_ptr(),
+                                     yd.data_ptr(), n, o, sp)
+                if st:
+                    raise RuntimeError(_lib.strerror(st))
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    run()
+                t = _time_launches(stream, run, 10)
+            _lib.check(_lib.lscan_stream_status(sp), "precision")
+            err = np.abs(yd.cpu().numpy().astype(np.float64) - ref)
+            pos = S > 0
+            ratio = float(np.max(err[pos] / S[pos]))
+            gbs = (in_b + 4) * n / t / 1e9
+            res[path] = {"gbs": round(gbs, 1),
+                         "frac_measured": round(gbs / peak, 4),
+                         "max_err_over_S": float(f"{ratio:.3e}"),
+                         "max_abs_err": float(f"{float(np.max(err)):.3e}"),
+                         "bound": gate[path], "within_bound": ratio <= gate[path]}
+        out[name + "_to_f32"] = res
+        del xd, yd, ref, S
+    return out
+
+
+def bench_bf16(args, dev, stream, peak, log2n=28):
+    """bf16 scans at N = 2^28 (uniform [-1, 1) for max, [0, 1) for add):
+    max (bf16 out), add with the default carry to fp32 and to bf16 output.
+    Algorithmic bytes: input + output, once each."""
+    import torch
+
+    from paper_1604_04815_gb300 import _lib
+    n = 1 << log2n
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    sp = stream.cuda_stream
+    out = {"n": n}
+    xm = (torch.rand(n, device=dev, generator=g) * 2 - 1).to(torch.bfloat16)
+    xa = torch.rand(n, device=dev, generator=g).to(torch.bfloat16)
+    for name, x, op, odt in (("max", xm, _lib.LSCAN_MAX, torch.bfloat16),
+                             ("add_to_f32", xa, _lib.LSCAN_ADD, torch.float32),
+                             ("add_to_bf16", xa, _lib.LSCAN_ADD,
+                              torch.bfloat16)):
+        y = torch.empty(n, dtype=odt, device=dev)
+        o = _lib.make_options(out_dtype=_lib.LSCAN_BF16
+                              if (op == _lib.LSCAN_ADD and odt ==
+                                  torch.bfloat16) else 0)
+
+        def run():
+            st = _lib.lscan_scan(op, _lib.LSCAN_BF16, 1, x.data_ptr(),
+                                 y.data_ptr(), n, o, sp)
+            if st:
+                raise RuntimeError(_lib.strerror(st))
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                run()
+            t = _time_launches(stream, run, 10)
+        gbs = (2 + y.element_size()) * n / t / 1e9
+        out[name] = {"us": round(t * 1e6, 1), "gbs": round(gbs, 1),
+                     "frac_measured": round(gbs / peak, 4)}
+        del y
+    _lib.check(_lib.lscan_stream_status(sp), "bf16")
+    return out
+
+
+def host_link_ceiling(dev, nbytes=1 << 30, reps=3):
+    """Plain pinned copies on the same box: host->device alone, device->host
+    alone, and both at once on two streams.  The duplex figure in the scan
+    metric (bytes in + bytes out per second) is the ceiling of an end-to-end
+    scan of host arrays."""
+    import torch
+    h_in = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_out = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def timed(fn):
+        best = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        return best
+    with torch.cuda.stream(s1):
+        d_a.copy_(h_in, non_blocking=True)
+    torch.cuda.synchronize()
+
+    def h2d():
+        with torch.cuda.stream(s1):
+            d_a.copy_(h_in, non_blocking=True)
+
+    def d2h():
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_b, non_blocking=True)
+
+    def both():
+        h2d()
+        d2h()
+    t_in, t_out, t_both = timed(h2d), timed(d2h), timed(both)
+    res = {"h2d_gbs": round(nbytes / t_in / 1e9, 1),
+           "d2h_gbs": round(nbytes / t_out / 1e9, 1),
+           "duplex_gbs": round(2 * nbytes / t_both / 1e9, 1),
+           "bytes_each_way": nbytes,
+           "method": "torch copy_ of pinned uint8 buffers, best of "
+                     f"{reps}, wall clock around a device synchronize"}
+    del h_in, h_out, d_a, d_b
+    return res
 
 
 def bench_select(args, dev, stream, peak, log2n=28):
@@ -656,11 +830,12 @@ def bench_batched(args, dev, stream, peak):
         od = torch.from_numpy(off).to(dev)
         tuned_cfg = None
         if args.config == 0:
-            st, tuned_cfg, _ = _lib.lscan_autotune(
+            st, res = _lib.lscan_autotune(
                 _lib.LSCAN_ADD, _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32,
                 1, xd.data_ptr(), yd.data_ptr(), total, od.data_ptr(),
-                len(off) - 1, reps=3, stream=sp)
+                len(off) - 1, reps=args.tune_reps, stream=sp)
             _lib.check(st, "lscan_autotune (batched)")
+            tuned_cfg = res["config"]
         g = lscan.Graph.batched(xd, od, yd)
         reps = max(3, args.steps)
         for _ in range(3):
@@ -750,7 +925,12 @@ def bench_serving(args, dev, peak, n_req, fracs, seed=6):
         base.append([r["op"], t, True, lk.data_ptr() + off * es, r["n"]])
     n_streams = getattr(args, "serving_streams", 2)
     srv = lscan.Server(budget_bytes=16 << 30, n_streams=n_streams)
+    small_max = getattr(args, "serving_small_max", 1 << 16)
+    bulk_tiles = getattr(args, "serving_bulk_tiles", 8192)
+    srv.set_lanes(small_max, bulk_tiles)
     out = {"requests": n_req, "budget_gib": 16, "n_streams": n_streams,
+           "lanes": {"small_max_elems": small_max,
+                     "bulk_batch_tiles": bulk_tiles},
            "mean_elems": float(np.mean([r["n"] for r in mix]))}
     try:
         # warm-up (kernels, scratch, pool) on a short closed-loop burst
@@ -780,13 +960,18 @@ def bench_serving(args, dev, peak, n_req, fracs, seed=6):
                         "count": int(m.sum()),
                         "p50_us": round(float(np.percentile(lat[m], 50)), 1),
                         "p99_us": round(float(np.percentile(lat[m], 99)), 1)}
+            small = per.get(f"2^{SIZE_CLASSES[0][0]}-2^{SIZE_CLASSES[0][1]}")
+            large = per.get(f"2^{SIZE_CLASSES[-1][0]}-2^{SIZE_CLASSES[-1][1]}")
             runs.append({"load": f, "offered_req_per_s": round(rate, 1),
                          "gbs": round(nbytes / (wall / 1e6) / 1e9, 1),
                          "p50_us": round(float(np.percentile(lat, 50)), 1),
                          "p99_us": round(float(np.percentile(lat, 99)), 1),
                          "mean_batch": round(float(np.mean(
                              [s["batch_requests"] for s in stats])), 1),
-                         "all_ok": ok, "size_classes": per})
+                         "all_ok": ok, "size_classes": per,
+                         "large_over_small_p50": round(
+                             large["p50_us"] / small["p50_us"], 2)
+                         if small and large else None})
         out["runs"] = runs
     finally:
         srv.close()
@@ -802,6 +987,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lscan", choices=["lscan", "reference"])
     ap.add_argument("--config", type=int, default=0)
+    ap.add_argument("--tune-reps", type=int, default=5,
+                    help="timed launches per configuration in the autotuner "
+                         "(median kept)")
     ap.add_argument("--carry", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-radix", action="store_true")
@@ -812,13 +1000,22 @@ def main():
     ap.add_argument("--no-dtypes", action="store_true")
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-select", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-link", action="store_true",
+                    help="skip the plain pinned-copy ceiling of the e2e leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=3000)
+    ap.add_argument("--serving-requests", type=int, default=20000)
+    ap.add_argument("--serving-loads", default="0.5,0.8,0.95",
+                    help="offered loads as fractions of the saturation rate")
     ap.add_argument("--serving-streams", type=int, default=2)
-    ap.add_argument("--serving-full", action="store_true",
-                    help="20000 requests per load level, loads 0.5/0.8/0.95")
+    ap.add_argument("--serving-small-max", type=int, default=1 << 16,
+                    help="largest request (elements) of the small lane; 0 = "
+                         "one lane")
+    ap.add_argument("--serving-bulk-tiles", type=int, default=8192,
+                    help="tiles per bulk-lane batch")
     ap.add_argument("--log2n", type=int, default=28,
                     help="array size 2^k (28 = the benchmarked workload; "
                          "smaller only for profiler captures)")

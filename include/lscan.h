@@ -75,12 +75,22 @@ typedef enum {
 
 /* Float-add precision of the cross-tile carry chain (the one step whose
  * rounding error grows with N / L).  Integer and max scans are exact and
- * ignore this field. */
+ * ignore this field.  Bounds against the exact prefix, with
+ * S_j = sum of |x_i| over the scanned prefix: |err_j| <= 1e-5 S_j for the
+ * F32 (measured, not guaranteed: its worst case grows with the number of
+ * carry hops), F64 and DF paths; <= 2.5e-7 S_j for COMPENSATED. */
 typedef enum {
-    LSCAN_PREC_DEFAULT = 0,     /* = LSCAN_PREC_F64_CARRY */
+    LSCAN_PREC_DEFAULT = 0,     /* = LSCAN_PREC_DF_CARRY */
     LSCAN_PREC_F32_CARRY = 1,   /* fp32 in tile, fp32 carry chain (plain) */
     LSCAN_PREC_F64_CARRY = 2,   /* fp32 in tile, FP64 carry chain */
-    LSCAN_PREC_COMPENSATED = 3  /* fp32 hi/lo pairs in tile, FP64 carry */
+    LSCAN_PREC_COMPENSATED = 3, /* compensated in tile (an exact two-sum per
+                                   element into an fp32 hi/lo pair),
+                                   double-float carry */
+    LSCAN_PREC_DF_CARRY = 4     /* fp32 in tile, double-float carry chain: a
+                                   normalised fp32 hi/lo pair (48-bit
+                                   significand) added with two-sum
+                                   arithmetic; no FP64 instruction on the
+                                   carry path */
 } lscan_precision;
 
 /* Inter-tile carry protocol (Section 4.3). */
@@ -172,21 +182,36 @@ lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int inclusive,
  * options, but its scratch (control block + per-tile status words) is a
  * fixed array compiled into the library: 2 MiB + 512 B that every GPU which
  * loads the library keeps until the process exits.
- *  - n is limited by that array: at most 262144 status words, 2 or 4 per
- *    tile by kind and tile configuration; for int32 with its default
- *    4096-element tiles that is 2^29 elements, for the 8-byte types 2^28.
- *    Larger n returns LSCAN_ERR_INVALID without launching.
- *  - The first call on a device looks up the array and clears it with
- *    cudaMemsetAsync on `stream`; make that first call before any capture.
+ *  - n is limited by that array: at most 262144 status words.  Launches use
+ *    tile configuration 2 whatever the tuning table says (16 KiB input
+ *    tiles; 2 status words per tile for every kind of lscan_scan), so the
+ *    limit is 2^29 elements for int32 and fp32 (4096-element tiles), 2^30 for
+ *    bf16 input (8192-element tiles) and 2^28 for int64 and double
+ *    (2048-element tiles); with x or y not 16-byte aligned the plain-load
+ *    configuration's tiles are half as long and so is the limit (2^28 int32).
+ *    Larger n returns LSCAN_ERR_INVALID without launching.  Arrays of at most
+ *    4096 elements take the single-CTA kernel and use no scratch.
+ *  - The first call on a device is a set-up call: it looks up the array (under
+ *    CUDA's lazy module loading, the moment the driver loads the module and
+ *    places the array) and clears it with cudaMemsetAsync on `stream`.  Make
+ *    that first call at initialisation, outside any context that must not
+ *    allocate, and before any stream capture.
  *  - Every call shares the array (it keeps the last call's contents; each
  *    launch re-arms it for the next one).  Calls that overlap on the GPU race
  *    on it: keep them on one stream or synchronise between them.
  *  - It allocates nothing (no cudaMalloc, cudaFree or allocating library
- *    call).  Device-side wait timeouts are not reported, but every wait is
- *    bounded, so a call cannot hang. */
+ *    call).  Every device-side wait is bounded, so a call cannot hang; a wait
+ *    that ran out latches the array's error word, which
+ *    lscan_noalloc_status() reports. */
 lscan_status lscan_scan_noalloc(lscan_op op, lscan_dtype dtype, int inclusive,
                                 const void *x, void *y, int64_t n,
                                 void *stream);
+/* Waits for `stream`, then returns and clears the error word of the current
+ * device's fixed array used by lscan_scan_noalloc: LSCAN_OK,
+ * LSCAN_ERR_TIMEOUT (a device wait of some no-allocation launch ran out:
+ * its output is wrong) or LSCAN_ERR_CUDA.  Reads by symbol, allocating
+ * nothing.  (The paper has no counterpart.) */
+lscan_status lscan_noalloc_status(void *stream);
 
 /* Batched scan of n_seg independent arrays stored back to back in x (and y):
  * segment s is elements [offsets[s], offsets[s+1]).  d_offsets is a DEVICE
@@ -228,12 +253,14 @@ void lscan_graph_destroy(lscan_graph *g);
  * paper; the serving pattern of this library).  The server owns ONE device
  * allocation of hbm_budget_bytes: per-stream scratch plus a pool for request
  * outputs and client buffers, so nothing is allocated while serving.
- * Requests wait in a FIFO admission queue until the pool can hold their
- * output; a scheduler thread keeps two launch slots per stream busy (the
- * second queued behind the first, so the device does not wait for the host
- * between launches), each running one persistent launch over the admitted
- * requests of one (op, dtype, inclusive) kind -- up to 65536 tiles -- so
- * kinds overlap on the device and later arrivals join the next launch.
+ * Requests wait in a FIFO admission queue (one per size-class lane, see
+ * lscan_server_set_lanes) until the pool can hold their output; a scheduler
+ * thread keeps two launch slots per stream busy (the second queued behind
+ * the first, so the device does not wait for the host between launches),
+ * each running one persistent launch over the admitted requests of one
+ * (op, dtype, inclusive) kind and lane -- up to 8192 tiles for the bulk
+ * lane by default -- so kinds overlap on the device and later arrivals join
+ * the next launch.  n_streams bulk streams plus one small-lane stream.
  * While batches are in flight the scheduler thread polls their completion
  * events (it sleeps when the server is idle).  Times are microseconds on the
  * host's steady clock since server creation; launch and completion times
@@ -266,6 +293,15 @@ void lscan_server_destroy(lscan_server *srv);
  * batched by kind.  Lets a client gather a burst into few launches.
  * Destroying a held server still runs everything it admitted. */
 lscan_status lscan_server_hold(lscan_server *srv, int hold);
+/* Size-class lanes.  Requests of at most small_max_elems elements (default
+ * 2^16) have their own admission queue and two launch slots on a stream of
+ * the device's greatest priority, and are batched only with each other;
+ * bulk batches hold at most bulk_batch_tiles tiles (default 8192, 1 ..
+ * 65536), so a small batch waits at most about one capped bulk launch for
+ * SM slots.  small_max_elems = 0 puts every request in the bulk lane.
+ * Applies to requests submitted afterwards.  (Not in the paper.) */
+lscan_status lscan_server_set_lanes(lscan_server *srv, int64_t small_max_elems,
+                                   int64_t bulk_batch_tiles);
 /* Client buffers from the pool (count against the budget); NOMEM if full. */
 lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr);
 lscan_status lscan_server_free(lscan_server *srv, void *dptr);
@@ -328,27 +364,45 @@ lscan_status lscan_set_wait_limit_ns(uint64_t ns);
 lscan_status lscan_debug_skip_publish(int64_t tile);
 
 /* Autotuner (not in the paper, whose K and T are fixed per dtype, Section
- * 5.1).  Times every bulk-copy tile configuration (items per thread x CTA
- * size x ring depth) on the caller's buffers -- a single-array scan, or a
- * batched one when d_offsets is given -- with `reps` timed launches each on
- * `stream`, records the fastest for this (op, dtype, precision/output kind,
- * mode, log2(n) class), and returns it (1-based) and its time in ms.  y is
- * overwritten with the scan of x.  LSCAN_ERR_UNSUPPORTED if the buffers are
- * not 16-byte aligned (only the plain-load configuration applies). */
+ * 5.1).  Times every bulk-copy tile configuration built for the mode --
+ * items per thread x consumer warps x ring stages x tiles per ticket x
+ * status-slot width, lscan_num_configs() of them for single arrays, the
+ * first six for batched scans -- on the caller's buffers (a single-array
+ * scan, or a batched one when d_offsets is given): two untimed launches,
+ * then `reps` launches each timed with CUDA events on `stream`, the median
+ * kept.  The paper's chained carry (Algorithm 4) is then timed at the
+ * fastest configuration when the array has at most 4096 tiles (beyond that
+ * its one L2 round trip per tile in series cannot compete).  The fastest
+ * (configuration, carry) is recorded for this (op, dtype, precision/output
+ * kind, mode, log2(n) class) and used by later calls that leave config and
+ * carry at 0.  y is overwritten with the scan of x.  LSCAN_ERR_UNSUPPORTED
+ * if the buffers are not 16-byte aligned (only the plain-load
+ * configuration applies).  out (may be NULL) receives the measurements. */
+#define LSCAN_TUNE_MAX_CONFIGS 32
+typedef struct lscan_tune_result {
+    int32_t config;          /* fastest configuration (1-based) */
+    int32_t carry;           /* its lscan_carry (LOOKBACK or CHAINED) */
+    float ms;                /* its median launch time, ms */
+    int32_t default_config;  /* the built-in default for this kind and mode */
+    float default_ms;        /* the default's median time, ms */
+    int32_t n_timed;         /* configurations timed */
+    float chained_ms;        /* chained carry at `config`, 0 if not timed */
+    float ms_by_config[LSCAN_TUNE_MAX_CONFIGS]; /* look-back, per config
+                                 (index config - 1); 0 = not built */
+} lscan_tune_result;
 lscan_status lscan_autotune(lscan_op op, lscan_dtype dtype, int inclusive,
                             const void *x, void *y, int64_t n,
                             const int64_t *d_offsets, int64_t n_seg,
                             const lscan_options *opts, int reps, void *stream,
-                            int32_t *best_config, float *best_ms);
+                            lscan_tune_result *out);
 /* The tuning table as JSON ({"lscan_tune": 1, "entries": [[kind, mode,
- * size_class, config], ...]}, only entries that differ from the defaults);
+ * size_class, config, carry], ...]}, only entries that differ from the
+ * defaults; four-field entries load with carry 0 = auto);
  * it is also loaded automatically from $LSCAN_TUNE_FILE on first use. */
 lscan_status lscan_tune_save(const char *path);
 lscan_status lscan_tune_load(const char *path);
 /* Back to the built-in defaults: each kind's fastest configuration on a
- * 2^28-element array (2 for most; 3 for fp32 add with the FP64 carry and
- * for bf16 add with the FP64 carry and bf16 output; 1 for the compensated
- * bf16 adds). */
+ * 2^28-element array on GB300, with the look-back carry. */
 lscan_status lscan_tune_reset(void);
 
 /* Stream compaction (a consumer of the scan; not in the paper): y receives,

@@ -299,6 +299,14 @@ class Server:
         return _lib.device_view(stats["y"], stats["n"],
                                 out_dtype_for(op, dtype))
 
+    def set_lanes(self, small_max_elems=1 << 16, bulk_batch_tiles=8192):
+        """Size-class lanes: requests of at most small_max_elems elements get
+        their own high-priority stream; bulk batches hold at most
+        bulk_batch_tiles tiles."""
+        _lib.check(_lib.load().lscan_server_set_lanes(
+            self._h, int(small_max_elems), int(bulk_batch_tiles)),
+            "lscan_server_set_lanes")
+
     def hold(self, on=True):
         """Queue requests without launching (on) / launch what queued (off)."""
         _lib.check(_lib.load().lscan_server_hold(self._h, int(bool(on))),

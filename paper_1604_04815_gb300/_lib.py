@@ -21,7 +21,7 @@ LSCAN_ERR_NOMEM = 5
 LSCAN_ERR_BUSY = 6
 LSCAN_ERR_DEVICE = 7
 LSCAN_PREC_DEFAULT, LSCAN_PREC_F32_CARRY, LSCAN_PREC_F64_CARRY, \
-    LSCAN_PREC_COMPENSATED = 0, 1, 2, 3
+    LSCAN_PREC_COMPENSATED, LSCAN_PREC_DF_CARRY = 0, 1, 2, 3, 4
 LSCAN_CARRY_AUTO, LSCAN_CARRY_LOOKBACK, LSCAN_CARRY_CHAINED = 0, 1, 2
 
 # every symbol include/lscan.h declares (checked by the ABI test)
@@ -34,10 +34,11 @@ EXPORTED = [
     "lscan_strerror", "lscan_version", "lscan_launch_count",
     "lscan_set_wait_limit_ns", "lscan_debug_skip_publish",
     "lscan_config_info", "lscan_num_configs", "lscan_scan_noalloc",
+    "lscan_noalloc_status",
     "lscan_server_create", "lscan_server_destroy", "lscan_server_alloc",
     "lscan_server_free", "lscan_server_submit", "lscan_server_wait",
     "lscan_server_poll", "lscan_server_release", "lscan_server_replay",
-    "lscan_server_hold",
+    "lscan_server_hold", "lscan_server_set_lanes",
     "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
     "lscan_tune_reset", "lscan_select_flagged", "lscan_radix_offsets",
 ]
@@ -62,6 +63,17 @@ class lscan_trace_req(ctypes.Structure):
                 ("inclusive", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("x", ctypes.c_void_p), ("n", ctypes.c_int64),
                 ("arrival_us", ctypes.c_double)]
+
+
+LSCAN_TUNE_MAX_CONFIGS = 32
+
+
+class lscan_tune_result(ctypes.Structure):
+    _fields_ = [("config", ctypes.c_int32), ("carry", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("default_config", ctypes.c_int32),
+                ("default_ms", ctypes.c_float), ("n_timed", ctypes.c_int32),
+                ("chained_ms", ctypes.c_float),
+                ("ms_by_config", ctypes.c_float * LSCAN_TUNE_MAX_CONFIGS)]
 
 
 class LscanError(RuntimeError):
@@ -109,8 +121,8 @@ def load():
         "lscan_config_info": [ctypes.c_int32, i32] +
                              [ctypes.POINTER(ctypes.c_int32)] * 4,
         "lscan_autotune": [i32, i32, i32, vp, vp, i64, vp, i64, optp, i32, vp,
-                           ctypes.POINTER(ctypes.c_int32),
-                           ctypes.POINTER(ctypes.c_float)],
+                           ctypes.POINTER(lscan_tune_result)],
+        "lscan_noalloc_status": [vp],
         "lscan_tune_save": [ctypes.c_char_p],
         "lscan_tune_load": [ctypes.c_char_p],
         "lscan_tune_reset": [],
@@ -124,6 +136,7 @@ def load():
                               ctypes.POINTER(lscan_req_stats)],
         "lscan_server_release": [vp, ctypes.c_uint64],
         "lscan_server_hold": [vp, ctypes.c_int],
+        "lscan_server_set_lanes": [vp, i64, i64],
         "lscan_server_replay": [vp, ctypes.POINTER(lscan_trace_req), i64,
                                 ctypes.POINTER(lscan_req_stats),
                                 ctypes.POINTER(ctypes.c_double)],
@@ -256,14 +269,24 @@ def lscan_num_configs():
 
 def lscan_autotune(op, dtype, inclusive, x, y, n, d_offsets=None, n_seg=0,
                    opts=None, reps=5, stream=None):
-    """Returns (status, best config, best ms)."""
-    best = ctypes.c_int32()
-    ms = ctypes.c_float()
+    """Returns (status, result dict): the fastest configuration and carry,
+    its median ms, the default configuration's median ms and every timed
+    configuration's median ms (keyed by configuration number)."""
+    r = lscan_tune_result()
     st = load().lscan_autotune(op, dtype, inclusive, x, y, n, d_offsets, n_seg,
                                ctypes.byref(opts) if opts is not None
-                               else None, reps, stream, ctypes.byref(best),
-                               ctypes.byref(ms))
-    return st, best.value, ms.value
+                               else None, reps, stream, ctypes.byref(r))
+    res = dict(config=r.config, carry=r.carry, ms=r.ms,
+               default_config=r.default_config, default_ms=r.default_ms,
+               n_timed=r.n_timed, chained_ms=r.chained_ms,
+               ms_by_config={i + 1: r.ms_by_config[i]
+                             for i in range(LSCAN_TUNE_MAX_CONFIGS)
+                             if r.ms_by_config[i] > 0})
+    return st, res
+
+
+def lscan_noalloc_status(stream=None):
+    return load().lscan_noalloc_status(stream)
 
 
 def lscan_tune_save(path):

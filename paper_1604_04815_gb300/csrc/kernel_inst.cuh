@@ -1,30 +1,98 @@
 // kernel_inst.cuh -- explicit instantiation of the scan kernel for one kind.
 #pragma once
+#include <utility>
+
 #include "kernel_table.h"
 #include "scan_kernel.cuh"
 #include "tiny_kernel.cuh"
 
 namespace lscan {
 
-// Tile configurations by input element size: <items/thread, consumer warps,
-// ring stages, output staging buffers, CTAs per SM the registers must fit>.
-// Variant 0 (G) loads straight from global memory; C1..C3 stream 8, 16 and
-// 32 KiB input tiles through the bulk-copy ring (for every element size).
+// Tile configurations by input element size, the autotuner's search space.
+// TileCfg<items/thread, consumer warps, ring stages, output staging buffers,
+// CTAs per SM the registers must fit, carry warps, tiles per ticket (run),
+// status words per tile slot (0: 2 for a one-word carry, more for wide
+// carries with 32 KiB tiles)>.
+//  - G loads straight from global memory (pointers not 16-byte aligned).
+//  - List: the bulk-copy configurations 1..N of a single-array scan; the
+//    first kMultiCfg are also built for batched (segmented, list) scans.
+//    Every list names input tiles of 8, 16, 32 or 64 KiB: ITEMS scales
+//    inversely with the element size, so a configuration number means the
+//    same bytes per tile for every type (bf16 entry 12 excepted, below).
+// Configurations whose shared memory does not fit one CTA are skipped when
+// the table is filled (their entry stays empty).
+template <class... Cs>
+struct CfgList {};
+
 template <int ISZ>
 struct Cfgs;
 template <>
 struct Cfgs<4> {
     using G = TileCfg<8, 8, 4, 1, 3>;
-    using C1 = TileCfg<8, 8, 4, 1, 3>;
-    using C2 = TileCfg<16, 8, 3, 1, 3>;
-    using C3 = TileCfg<16, 16, 2, 1, 2>;
+    using List = CfgList<
+        TileCfg<8, 8, 4, 1, 3>,             //  1: 8 KiB tiles, 4 stages
+        TileCfg<16, 8, 3, 1, 3>,            //  2: 16 KiB, 3 stages
+        TileCfg<16, 16, 2, 1, 2>,           //  3: 32 KiB, 2 stages, 16 warps
+        TileCfg<16, 8, 3, 1, 3, 1, 1, 4>,   //  4: = 2, 32-byte status slots
+        TileCfg<16, 16, 2, 1, 2, 1, 1, 8>,  //  5: = 3, 64-byte slots
+        TileCfg<16, 16, 2, 1, 2, 1, 1, 16>, //  6: = 3, 128-byte slots
+        TileCfg<16, 8, 3, 1, 3, 1, 2, 4>,   //  7: = 4, runs of 2 tiles
+        TileCfg<32, 8, 2, 1, 2, 1, 1, 8>,   //  8: 32 KiB, 8 warps, 2 stages
+        TileCfg<16, 4, 4, 1, 4, 1, 1, 4>,   //  9: 8 KiB, 4 warps, 4 stages
+        TileCfg<32, 4, 3, 1, 3, 1, 1, 4>,   // 10: 16 KiB, 4 warps, 3 stages
+        TileCfg<16, 16, 3, 1, 1, 1, 1, 8>,  // 11: 32 KiB, 3 stages (1 CTA/SM)
+        TileCfg<32, 16, 2, 1, 1, 1, 1, 8>,  // 12: 64 KiB tiles
+        TileCfg<16, 8, 4, 1, 2, 1, 1, 4>,   // 13: 16 KiB, 4 stages
+        TileCfg<16, 16, 2, 1, 2, 1, 2, 8>,  // 14: = 5, runs of 2 tiles
+        TileCfg<32, 8, 3, 1, 1, 1, 1, 8>,   // 15: 32 KiB, 8 warps, 3 stages
+        TileCfg<8, 16, 3, 1, 2, 1, 1, 4>>;  // 16: 16 KiB, 16 warps, 3 stages
 };
 template <>
 struct Cfgs<8> {
     using G = TileCfg<4, 8, 4, 1, 3>;
-    using C1 = TileCfg<4, 8, 4, 1, 3>;
-    using C2 = TileCfg<8, 8, 3, 1, 3>;
-    using C3 = TileCfg<8, 16, 2, 1, 2>;
+    using List = CfgList<
+        TileCfg<4, 8, 4, 1, 3>,
+        TileCfg<8, 8, 3, 1, 3>,
+        TileCfg<8, 16, 2, 1, 2>,
+        TileCfg<8, 8, 3, 1, 3, 1, 1, 4>,
+        TileCfg<8, 16, 2, 1, 2, 1, 1, 8>,
+        TileCfg<8, 16, 2, 1, 2, 1, 1, 16>,
+        TileCfg<8, 8, 3, 1, 3, 1, 2, 4>,
+        TileCfg<16, 8, 2, 1, 2, 1, 1, 8>,
+        TileCfg<8, 4, 4, 1, 4, 1, 1, 4>,
+        TileCfg<16, 4, 3, 1, 3, 1, 1, 4>,
+        TileCfg<8, 16, 3, 1, 1, 1, 1, 8>,
+        TileCfg<16, 16, 2, 1, 1, 1, 1, 8>,
+        TileCfg<8, 8, 4, 1, 2, 1, 1, 4>,
+        TileCfg<8, 16, 2, 1, 2, 1, 2, 8>,
+        TileCfg<16, 8, 3, 1, 1, 1, 1, 8>,
+        TileCfg<4, 16, 3, 1, 2, 1, 1, 4>>;
+};
+// bf16: twice the items for the same bytes.  Items stay <= 32 (a thread's
+// segment-head bits fit one word), so where the 4-byte entry has 32 items
+// the bf16 entry doubles the warps instead, or (entries 8, 10, 15) takes
+// the same tile bytes with another slot width or run; entry 12 (64 KiB of
+// 4-byte input) is 32 KiB of bf16 with 3 stages and runs of 2.
+template <>
+struct Cfgs<2> {
+    using G = TileCfg<16, 8, 4, 1, 3>;
+    using List = CfgList<
+        TileCfg<16, 8, 4, 1, 3>,              //  1: 8 KiB
+        TileCfg<32, 8, 3, 1, 2>,              //  2: 16 KiB
+        TileCfg<32, 16, 2, 1, 1>,             //  3: 32 KiB
+        TileCfg<32, 8, 3, 1, 2, 1, 1, 4>,     //  4: 16 KiB, 32-byte slots
+        TileCfg<32, 16, 2, 1, 1, 1, 1, 8>,    //  5: 32 KiB, 64-byte slots
+        TileCfg<32, 16, 2, 1, 1, 1, 1, 16>,   //  6: 32 KiB, 128-byte slots
+        TileCfg<32, 8, 3, 1, 2, 1, 2, 4>,     //  7: 16 KiB, runs of 2
+        TileCfg<32, 16, 2, 1, 1, 1, 2, 16>,   //  8: 32 KiB, runs of 2
+        TileCfg<32, 4, 4, 1, 4, 1, 1, 4>,     //  9: 8 KiB, 4 warps
+        TileCfg<32, 8, 3, 1, 2, 1, 1, 8>,     // 10: 16 KiB, 64-byte slots
+        TileCfg<32, 16, 3, 1, 1, 1, 1, 8>,    // 11: 32 KiB, 3 stages
+        TileCfg<32, 16, 3, 1, 1, 1, 2, 8>,    // 12: 32 KiB, 3 stages, runs of 2
+        TileCfg<32, 8, 4, 1, 2, 1, 1, 4>,     // 13: 16 KiB, 4 stages
+        TileCfg<32, 16, 2, 1, 1, 1, 2, 8>,    // 14: 32 KiB, runs of 2
+        TileCfg<32, 16, 3, 1, 1, 1, 1, 16>,   // 15: 32 KiB, 3 stages, 128 B
+        TileCfg<16, 16, 3, 1, 2, 1, 1, 4>>;   // 16: 16 KiB, 16 warps
 };
 // flags of a stream compaction: 4096 flags per tile, 16 per thread, whose
 // values are loaded early and held in registers (2 CTAs/SM leave room for
@@ -35,38 +103,49 @@ struct Cfgs<1> {
     using G = TileCfg<16, 8, 6, 1, 2>;
     using C1 = TileCfg<16, 8, 6, 1, 2>;
 };
-template <>
-struct Cfgs<2> {
-    using G = TileCfg<16, 8, 4, 1, 3>;
-    using C1 = TileCfg<16, 8, 4, 1, 3>;
-    using C2 = TileCfg<32, 8, 3, 1, 2>;
-    using C3 = TileCfg<32, 16, 2, 1, 1>;
-};
+
+// shared memory one CTA may use (sm_100 family: 227 KiB)
+constexpr int kMaxSmemPerCta = 227 * 1024;
 
 template <class K, class Cfg, int MODE, bool TMA>
 void fill_entry(int kind, int variant) {
     using L = Layout<K, Cfg, MODE, TMA>;
-    KernelEntry &e = g_kernels[kind][MODE][variant];
-    e.fn = reinterpret_cast<const void *>(&lscan_kernel<K, Cfg, MODE, TMA>);
-    e.threads = Cfg::THREADS;
-    e.smem = L::bytes;
-    e.tile = Cfg::TILE;
-    e.items = Cfg::ITEMS;
-    e.cwarps = Cfg::CWARPS;
-    e.stages = Cfg::STAGES;
-    static_assert(status_slot_words<K, Cfg::TILE>() <= kMaxSlotWords, "status slot");
-    e.car_words = status_slot_words<K, Cfg::TILE>();  // status words per tile
-    e.in_size = int(sizeof(typename K::In));
-    e.out_size = int(sizeof(typename K::Out));
+    if constexpr (L::bytes <= kMaxSmemPerCta) {
+        KernelEntry &e = g_kernels[kind][MODE][variant];
+        e.fn = reinterpret_cast<const void *>(&lscan_kernel<K, Cfg, MODE, TMA>);
+        e.threads = Cfg::THREADS;
+        e.smem = L::bytes;
+        e.tile = Cfg::TILE;
+        e.items = Cfg::ITEMS;
+        e.cwarps = Cfg::CWARPS;
+        e.stages = Cfg::STAGES;
+        e.run = Cfg::RUN;
+        static_assert(status_slot_words<K, Cfg>() <= kMaxSlotWords, "status slot");
+        e.car_words = status_slot_words<K, Cfg>();  // status words per tile
+        e.in_size = int(sizeof(typename K::In));
+        e.out_size = int(sizeof(typename K::Out));
+    }
+}
+
+// configuration number V of a mode: batched modes take the first kMultiCfg
+// (the others are not instantiated for them)
+template <class K, class Cfg, int MODE, int V>
+void fill_numbered(int kind) {
+    if constexpr (MODE == MODE_SINGLE || V <= kMultiCfg)
+        fill_entry<K, Cfg, MODE, true>(kind, V);
+}
+
+template <class K, int MODE, class... Cs, size_t... I>
+void fill_list(int kind, CfgList<Cs...>, std::index_sequence<I...>) {
+    static_assert(sizeof...(Cs) == kNumTmaCfg, "one entry per configuration number");
+    (fill_numbered<K, Cs, MODE, int(I) + 1>(kind), ...);
 }
 
 template <class K, int MODE>
 void fill_mode(int kind) {
     using C = Cfgs<int(sizeof(typename K::In))>;
     fill_entry<K, typename C::G, MODE, false>(kind, 0);
-    fill_entry<K, typename C::C1, MODE, true>(kind, 1);
-    fill_entry<K, typename C::C2, MODE, true>(kind, 2);
-    fill_entry<K, typename C::C3, MODE, true>(kind, 3);
+    fill_list<K, MODE>(kind, typename C::List{}, std::make_index_sequence<kNumTmaCfg>{});
 }
 
 // stream compaction: single arrays only, plain-load and one bulk-copy variant

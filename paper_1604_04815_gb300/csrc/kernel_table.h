@@ -7,13 +7,15 @@
 namespace lscan {
 
 // Variant 0 is the plain-load path for pointers that are not 16-byte
-// aligned; variants 1..kNumTmaCfg are bulk-copy (TMA) tile configurations.
-constexpr int kNumTmaCfg = 3;
+// aligned; variants 1..kNumTmaCfg are bulk-copy (TMA) tile configurations
+// of single-array scans, of which batched scans have the first kMultiCfg.
+constexpr int kNumTmaCfg = 16;
+constexpr int kMultiCfg = 6;
 constexpr int kNumVariants = 1 + kNumTmaCfg;
-constexpr int kNumKinds = 20;
+constexpr int kNumKinds = 23;
 // most status words any kernel uses per tile (fixed-size scratch is sized
 // with it)
-constexpr int kMaxSlotWords = 4;
+constexpr int kMaxSlotWords = 16;
 
 struct KernelEntry {
     const void *fn = nullptr;
@@ -23,6 +25,7 @@ struct KernelEntry {
     int items = 0;     // elements per consumer thread
     int cwarps = 0;    // consumer warps
     int stages = 0;    // tile-ring depth
+    int run = 1;       // consecutive tiles per ticket
     int car_words = 0; // 64-bit status words per tile slot
     int in_size = 0;
     int out_size = 0;

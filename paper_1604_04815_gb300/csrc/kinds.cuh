@@ -13,17 +13,21 @@
 //   fp32/bf16 max : b > a ? b : a  (a tie keeps the earlier element's bits),
 //                identity -inf; bf16 widened exactly to fp32 and narrowed
 //                back exactly
-//   fp32/bf16 add, three precision paths for the carry chain:
+//   fp32/bf16 add, four precision paths for the carry chain:
 //     Plain : fp32 in tile, fp32 carry
 //     F64   : fp32 in tile, FP64 carry; the carry is split once per tile into
 //             an fp32 (hi, lo) pair and applied with fp32 two-sum arithmetic,
 //             so no per-element FP64 work is done
-//     Comp  : fp32 (hi, lo) pairs in tile (compensated two-sum arithmetic),
-//             FP64 carry, result rounded to fp32 once at the end
+//     DF    : fp32 in tile, double-float carry: a normalised fp32 (hi, lo)
+//             pair (48-bit significand) combined with two-sum arithmetic, so
+//             the carry path has no FP64 instruction (GB300's FP64 pipe is
+//             narrow and its latency sits on the carry chain)
+//     Comp  : compensated in tile (each element enters through an exact
+//             two-sum into an unnormalised (hi, lo) pair), double-float
+//             carry, each output rounded from hi + lo
 //
-// Two-sum (Knuth, TAOCP vol. 2, 4.2.2) and fast-two-sum (Dekker 1971) are
-// written with __fadd_rn / __fsub_rn so the compiler cannot contract or
-// reassociate them.
+// Two-sum (Knuth, TAOCP vol. 2, 4.2.2) is written with __fadd_rn / __fsub_rn
+// so the compiler cannot contract or reassociate it.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -51,17 +55,16 @@ __device__ __forceinline__ float2 two_sum(float a, float b) {
     float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
     return make_float2(s, e);
 }
-// requires |a| >= |b| or a == 0 (Dekker fast-two-sum)
-__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float e = __fsub_rn(b, __fsub_rn(s, a));
-    return make_float2(s, e);
-}
-// double-float addition (hi, lo) + (hi, lo); absolute error O(u^2 (|a|+|b|))
+// double-float addition (hi, lo) + (hi, lo), normalised result (hi the
+// rounded sum, lo its exact remainder).  The only roundings are those of the
+// low parts, so the absolute error is at most 2u (|s.y| + |a.y| + |b.y|):
+// O(u^2 (|a| + |b|)) for normalised inputs.  It ends in a two-sum rather than
+// Dekker's fast-two-sum, so inputs need not be normalised (the in-tile pairs
+// of the compensated path are not).
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     float2 s = two_sum(a.x, b.x);
     float e = __fadd_rn(s.y, __fadd_rn(a.y, b.y));
-    return fast_two_sum(s.x, e);
+    return two_sum(s.x, e);
 }
 // FP64 value -> fp32 (hi, lo) with hi + lo == d to ~2^-48 |d|
 __device__ __forceinline__ float2 split_f64(double d) {
@@ -223,35 +226,91 @@ struct KFAddF64 {
     }
 };
 
-// float add, compensated (hi, lo) in tile, FP64 carry
+// float add, fp32 in tile, double-float carry: the carry chain runs on
+// normalised fp32 (hi, lo) pairs (a 48-bit significand, FP64-class) with
+// two-sum arithmetic, so no FP64 instruction is on the carry path
+template <class InT, class OutT>
+struct KFAddDF {
+    static constexpr bool kTieOrdered = false;
+    using In = InT;
+    using Out = OutT;
+    using Acc = float;
+    using Car = float2;
+    using CarA = float2;
+    __device__ static Acc ident() { return 0.0f; }
+    __device__ static Acc load(In v) { return FloatIn<InT>::load(v); }
+    __device__ static Acc op(Acc a, Acc b) { return __fadd_rn(a, b); }
+    __device__ static Car cident() { return make_float2(0.0f, 0.0f); }
+    __device__ static Car to_car(Acc a) { return make_float2(a, 0.0f); }
+    __device__ static Car cop(Car a, Car b) { return df_add(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
+    __device__ static CarA base(CarA c, Acc tb) {
+        float2 s = two_sum(c.x, tb);
+        return make_float2(s.x, __fadd_rn(s.y, c.y));
+    }
+    __device__ static CarA base_local(Acc tb) { return make_float2(tb, 0.0f); }
+    __device__ static Out fin(CarA b, Acc v) {
+        return FloatOut<OutT>::cvt(__fadd_rn(b.x, __fadd_rn(v, b.y)));
+    }
+    __device__ static Car car_of_out(Out o) {
+        return make_float2(FloatIn<OutT>::load(o), 0.0f);
+    }
+};
+
+// float add, compensated in tile, double-float carry.
+// Per element (op_step, b a fresh element (x, 0)): (s, e) = two-sum(hi, x),
+// hi = s, lo += e -- hi + lo keeps every rounding error of the running sum;
+// only the additions into lo round, O(K u^2 S) over K elements.  Pairs
+// (thread totals, warp and tile totals, carries) combine with df_add.  The
+// output y = fl(fl(b.hi + hi) + fl(b.lo + lo)) rounds twice, so
+// |y_j - sum| <= 2u S_j + O(u^2 S_j), within the 2.5e-7 S_j (~4.2u) bound.
 template <class InT, class OutT>
 struct KFAddComp {
     static constexpr bool kTieOrdered = false;
     using In = InT;
     using Out = OutT;
     using Acc = float2;
-    using Car = double;
+    using Car = float2;
     using CarA = float2;
     __device__ static Acc ident() { return make_float2(0.0f, 0.0f); }
     __device__ static Acc load(In v) {
         return make_float2(FloatIn<InT>::load(v), 0.0f);
     }
     __device__ static Acc op(Acc a, Acc b) { return df_add(a, b); }
-    __device__ static Car cident() { return 0.0; }
-    __device__ static Car to_car(Acc a) {
-        return __dadd_rn(static_cast<double>(a.x), static_cast<double>(a.y));
+    // a (+) b where b is one element (b.y == 0)
+    __device__ static Acc op_step(Acc a, Acc b) {
+        const float2 s = two_sum(a.x, b.x);
+        return make_float2(s.x, __fadd_rn(a.y, s.y));
     }
-    __device__ static Car cop(Car a, Car b) { return __dadd_rn(a, b); }
-    __device__ static CarA to_apply(Car c) { return split_f64(c); }
+    __device__ static Car cident() { return make_float2(0.0f, 0.0f); }
+    __device__ static Car to_car(Acc a) { return df_add(a, make_float2(0.0f, 0.0f)); }
+    __device__ static Car cop(Car a, Car b) { return df_add(a, b); }
+    __device__ static CarA to_apply(Car c) { return c; }
     __device__ static CarA base(CarA c, Acc tb) { return df_add(c, tb); }
     __device__ static CarA base_local(Acc tb) { return tb; }
     __device__ static Out fin(CarA b, Acc v) {
-        return FloatOut<OutT>::cvt(df_add(b, v).x);
+        return FloatOut<OutT>::cvt(__fadd_rn(__fadd_rn(b.x, v.x), __fadd_rn(b.y, v.y)));
     }
     __device__ static Car car_of_out(Out o) {
-        return static_cast<double>(FloatIn<OutT>::load(o));
+        return make_float2(FloatIn<OutT>::load(o), 0.0f);
     }
 };
+
+// Step of a left fold that adds one freshly loaded element: K::op_step where
+// a kind has a cheaper form for that case, K::op otherwise.
+template <class K, class = void>
+struct has_op_step : std::false_type {};
+template <class K>
+struct has_op_step<K, std::void_t<decltype(K::op_step(typename K::Acc{}, typename K::Acc{}))>>
+    : std::true_type {};
+template <class K>
+__device__ __forceinline__ typename K::Acc op_step(typename K::Acc a, typename K::Acc b) {
+    if constexpr (has_op_step<K>::value) {
+        return K::op_step(a, b);
+    } else {
+        return K::op(a, b);
+    }
+}
 
 // 64-bit integers and doubles (the paper's other two types, Table 2)
 struct KI64Add {
@@ -396,6 +455,9 @@ enum KindId : int {
     KIND_I64_MAX,
     KIND_F64_MAX,
     KIND_F64_ADD,
+    KIND_F32_ADD_DF,  // float add with the double-float carry
+    KIND_BF16_ADD_DF_F32,
+    KIND_BF16_ADD_DF_BF16,
     KIND_SEL16,  // stream compaction of 2-, 4- and 8-byte values
     KIND_SEL32,
     KIND_SEL64,

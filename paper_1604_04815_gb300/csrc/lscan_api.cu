@@ -43,6 +43,9 @@ void register_i64_add();
 void register_i64_max();
 void register_f64_max();
 void register_f64_add();
+void register_f32_add_df();
+void register_bf16_add_df_f32();
+void register_bf16_add_df_bf16();
 void register_select();
 
 void register_all_kernels() {
@@ -63,6 +66,9 @@ void register_all_kernels() {
     register_i64_max();
     register_f64_max();
     register_f64_add();
+    register_f32_add_df();
+    register_bf16_add_df_f32();
+    register_bf16_add_df_bf16();
     register_select();
 }
 
@@ -88,6 +94,11 @@ struct FnState {
     bool attr_set = false;
     int blocks_per_sm = 0;
 };
+// Per-kernel and per-device launch facts, filled on first use by whichever
+// host thread launches first (the API under g_mu, the no-allocation entry
+// point, the server thread and graph capture all launch), so they have a
+// lock of their own.
+std::mutex g_prep_mu;
 std::map<std::pair<int, const void *>, FnState> g_fn_state;
 std::map<int, int> g_sm_count;
 
@@ -96,6 +107,7 @@ constexpr uint64_t kEpochPeriod = (1ull << 30) - 1;
 }  // namespace
 
 int sm_count(int dev) {
+    std::lock_guard<std::mutex> lk(g_prep_mu);
     auto it = g_sm_count.find(dev);
     if (it != g_sm_count.end()) return it->second;
     int n = 0;
@@ -124,16 +136,21 @@ int select_kind(int op, int dtype, int out_dtype, int precision) {
         const bool ok = precision == LSCAN_PREC_DEFAULT || precision == LSCAN_PREC_F64_CARRY;
         return (out_dtype == LSCAN_F64 && ok) ? KIND_F64_ADD : -1;
     }
-    int prec = precision == LSCAN_PREC_DEFAULT ? LSCAN_PREC_F64_CARRY : precision;
-    if (prec < LSCAN_PREC_F32_CARRY || prec > LSCAN_PREC_COMPENSATED) return -1;
-    const int pi = prec - LSCAN_PREC_F32_CARRY;  // 0 plain, 1 f64, 2 comp
-    if (dtype == LSCAN_F32) {
-        if (out_dtype != LSCAN_F32) return -1;
-        return KIND_F32_ADD_PLAIN + pi;
-    }
+    const int prec = precision == LSCAN_PREC_DEFAULT ? LSCAN_PREC_DF_CARRY : precision;
+    // kinds by precision path: fp32 carry, FP64 carry, compensated,
+    // double-float carry
+    static const int kF32[] = {KIND_F32_ADD_PLAIN, KIND_F32_ADD_F64, KIND_F32_ADD_COMP,
+                               KIND_F32_ADD_DF};
+    static const int kBf16F32[] = {KIND_BF16_ADD_PLAIN_F32, KIND_BF16_ADD_F64_F32,
+                                   KIND_BF16_ADD_COMP_F32, KIND_BF16_ADD_DF_F32};
+    static const int kBf16Bf16[] = {KIND_BF16_ADD_PLAIN_BF16, KIND_BF16_ADD_F64_BF16,
+                                    KIND_BF16_ADD_COMP_BF16, KIND_BF16_ADD_DF_BF16};
+    if (prec < LSCAN_PREC_F32_CARRY || prec > LSCAN_PREC_DF_CARRY) return -1;
+    const int pi = prec - LSCAN_PREC_F32_CARRY;
+    if (dtype == LSCAN_F32) return out_dtype == LSCAN_F32 ? kF32[pi] : -1;
     if (dtype == LSCAN_BF16) {
-        if (out_dtype == LSCAN_F32) return KIND_BF16_ADD_PLAIN_F32 + pi;
-        if (out_dtype == LSCAN_BF16) return KIND_BF16_ADD_PLAIN_BF16 + pi;
+        if (out_dtype == LSCAN_F32) return kBf16F32[pi];
+        if (out_dtype == LSCAN_BF16) return kBf16Bf16[pi];
     }
     return -1;
 }
@@ -147,6 +164,7 @@ int dtype_size(int dt) {
 
 // Occupancy-derived persistent grid size for a kernel on device dev.
 static lscan_status kernel_prepare(int dev, const KernelEntry &e, int *blocks_per_sm) {
+    std::lock_guard<std::mutex> lk(g_prep_mu);
     FnState &st = g_fn_state[{dev, e.fn}];
     if (!st.attr_set) {
         if (cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -316,7 +334,8 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     }
     int cfg = opts ? opts->config : 0;
     if (cfg < 0 || cfg > kNumTmaCfg) return LSCAN_ERR_INVALID;
-    int variant = cfg > 0 ? cfg : tuned_variant(kind, mode, n);
+    int tuned_carry = LSCAN_CARRY_AUTO;
+    int variant = cfg > 0 ? cfg : tuned_variant(kind, mode, n, &tuned_carry);
     const bool aligned = (reinterpret_cast<uintptr_t>(x) % 16 == 0) &&
                          (reinterpret_cast<uintptr_t>(y) % 16 == 0);
     if (!aligned) variant = 0;
@@ -324,8 +343,11 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
     const int64_t n_tiles = (n + e.tile - 1) / e.tile;
     if (n_tiles > (int64_t{1} << 31) - 1) return LSCAN_ERR_INVALID;
-    const int carry = opts ? opts->carry : LSCAN_CARRY_AUTO;
+    int carry = opts ? opts->carry : LSCAN_CARRY_AUTO;
     if (carry < LSCAN_CARRY_AUTO || carry > LSCAN_CARRY_CHAINED) return LSCAN_ERR_INVALID;
+    // AUTO takes what the autotuner measured for this size (look-back unless
+    // the chained hand-off won)
+    if (carry == LSCAN_CARRY_AUTO && cfg == 0) carry = tuned_carry;
     const void *carry_in = opts ? opts->carry_in : nullptr;
     if (carry_in && (mode != MODE_SINGLE || reinterpret_cast<uintptr_t>(carry_in) % osz != 0))
         return LSCAN_ERR_INVALID;
@@ -371,7 +393,15 @@ int planned_tile(const LaunchSpec &ls) {
     return g_kernels[ls.kind][ls.mode][ls.variant].tile;
 }
 
-int carry_words(int kind) { return g_kernels[kind][MODE_SINGLE][1].car_words; }
+int64_t planned_tiles(const LaunchSpec &ls) {
+    if (ls.mode == MODE_LIST) return ls.list_tiles;
+    const int64_t tile = planned_tile(ls);
+    return (ls.n + tile - 1) / tile;
+}
+
+void ensure_kernels_registered() { std::call_once(g_reg_once, register_all_kernels); }
+
+int carry_words(int kind) { return g_kernels[kind][MODE_SINGLE][1].car_words; }  // config 1
 
 void note_launch() { g_launches.fetch_add(1); }
 
@@ -439,15 +469,17 @@ lscan_status lscan_stream_status(void *stream) {
 lscan_status lscan_reserve(void *stream, int64_t max_elems) {
     if (max_elems < 0) return LSCAN_ERR_INVALID;
     std::call_once(g_reg_once, register_all_kernels);
-    // smallest tile of any configuration (1024), 2 status words per such
-    // tile: 4-word slots come only with tiles of >= 4096 elements
-    int64_t min_tile = INT64_MAX;
+    // the most status words any built kernel needs for max_elems elements
+    size_t words = 0;
     for (int k = 0; k < kNumKinds; ++k)
         for (int m = 0; m < MODE_COUNT; ++m)
-            for (int v = 0; v < kNumVariants; ++v)
-                if (g_kernels[k][m][v].fn && g_kernels[k][m][v].tile < min_tile)
-                    min_tile = g_kernels[k][m][v].tile;
-    const size_t words = static_cast<size_t>((max_elems + min_tile - 1) / min_tile) * 2;
+            for (int v = 0; v < kNumVariants; ++v) {
+                const KernelEntry &e = g_kernels[k][m][v];
+                if (!e.fn) continue;
+                const size_t w = static_cast<size_t>((max_elems + e.tile - 1) / e.tile) *
+                                 static_cast<size_t>(e.car_words);
+                if (w > words) words = w;
+            }
     std::lock_guard<std::mutex> lk(g_mu);
     Scratch *sc = nullptr;
     return get_scratch(stream, words > 0 ? words : 1, &sc);

@@ -51,8 +51,13 @@ int planned_tile(const LaunchSpec &ls);
 // number of 64-bit status words per tile of a kind
 int carry_words(int kind);
 
-// tile configuration the tuning table picks for (kind, mode, n); 1..3
-int tuned_variant(int kind, int mode, int64_t n);
+// tile configuration the tuning table picks for (kind, mode, n), and the
+// carry protocol recorded with it (an lscan_carry; 0 = auto)
+int tuned_variant(int kind, int mode, int64_t n, int *carry);
+// tiles of a planned launch
+int64_t planned_tiles(const LaunchSpec &ls);
+// registers every compiled kernel (once)
+void ensure_kernels_registered();
 
 std::mutex &api_mutex();
 void shutdown_graphs_locked();
@@ -60,6 +65,7 @@ void shutdown_host_pipes();  // frees the staging of lscan_scan_host
 void shutdown_radix();       // frees the counters of lscan_radix_offsets
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
-void set_tuned_variant(int kind, int mode, int size_cls, int variant);
+// entry = configuration | carry << 8
+void set_tuned_variant(int kind, int mode, int size_cls, int entry);
 
 }  // namespace lscan

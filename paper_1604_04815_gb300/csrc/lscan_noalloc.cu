@@ -16,18 +16,24 @@
 // exits.
 //
 // Rules for callers (also stated in include/lscan.h):
-//  - The first call on each device looks up the array's device address and
-//    clears it with cudaMemsetAsync on the caller's stream; make that first
-//    call before any stream capture.
+//  - The first call on each device is a set-up call: it looks up the array's
+//    device address (under lazy module loading this loads the library's
+//    module, which is when the driver places the array) and clears it with
+//    cudaMemsetAsync on the caller's stream.  Make it at initialisation,
+//    outside any context that must not allocate, and before any stream
+//    capture.
 //  - All calls share the one array.  Each launch re-arms the ticket and
 //    advances the epoch itself at its end, so consecutive calls need no
 //    clearing, but calls that overlap on the GPU (different streams without
 //    synchronisation between them) race on the array and give wrong results.
-//  - Sizes whose status words do not fit return LSCAN_ERR_INVALID without
-//    launching anything.
-//  - Device-side wait timeouts of these launches are not reported (no status
-//    entry point reads this array); every wait is still bounded, so a call
-//    can never hang the GPU.
+//  - The tile configuration is fixed (configuration 2: 16 KiB input tiles,
+//    status slots of 2 words for 32-bit carries), so the size limit does not
+//    move with the autotuner's table.  Sizes whose status words do not fit
+//    return LSCAN_ERR_INVALID without launching anything.  Arrays of at most
+//    4096 elements take the single-CTA kernel, which uses no scratch.
+//  - A device-side wait that ran out of time (every wait is bounded, so a
+//    call cannot hang) latches the array's error word; lscan_noalloc_status
+//    reads and clears it.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -44,6 +50,9 @@ constexpr size_t kNoAllocStatusWords = size_t{1} << 18;
 constexpr size_t kNoAllocScratchWords = CTL_WORDS / 2 + kNoAllocStatusWords;
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocScratchWords];
+
+// tile configuration of every launch that needs scratch
+constexpr int kNoAllocConfig = 2;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mu;
@@ -77,8 +86,16 @@ extern "C" lscan_status lscan_scan_noalloc(lscan_op op, lscan_dtype dtype,
     lscan_status st = plan_scan(op, dtype, inclusive, x, y, n, nullptr, MODE_SINGLE,
                                 nullptr, 0, &ls);
     if (st != LSCAN_OK) return st;
-    if (ls.status_words > kNoAllocStatusWords) return LSCAN_ERR_INVALID;
     if (n == 0) return LSCAN_OK;
+    if (!ls.tiny) {
+        // a fixed configuration, so that the limit does not depend on tuning
+        lscan_options o{};
+        o.config = kNoAllocConfig;
+        o.carry = LSCAN_CARRY_LOOKBACK;
+        st = plan_scan(op, dtype, inclusive, x, y, n, &o, MODE_SINGLE, nullptr, 0, &ls);
+        if (st != LSCAN_OK) return st;
+    }
+    if (ls.status_words > kNoAllocStatusWords) return LSCAN_ERR_INVALID;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -96,4 +113,28 @@ extern "C" lscan_status lscan_scan_noalloc(lscan_op op, lscan_dtype dtype,
     }
     DevBuffers b{ctl, status};
     return launch_scan(ls, b, cs);
+}
+
+extern "C" lscan_status lscan_noalloc_status(void *stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return LSCAN_ERR_UNSUPPORTED;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (g_na_ptr[dev] == nullptr) return LSCAN_OK;  // no launch on this device yet
+    }
+    // the error word of this device's control block, read and cleared by
+    // symbol (plain copies through host memory; nothing is allocated)
+    const size_t off = CTL_ERROR * sizeof(uint32_t);
+    uint32_t err = 0;
+    if (cudaMemcpyFromSymbol(&err, g_noalloc_scratch, sizeof(err), off) != cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    if (err == 0) return LSCAN_OK;
+    const uint32_t zero = 0;
+    if (cudaMemcpyToSymbol(g_noalloc_scratch, &zero, sizeof(zero), off) != cudaSuccess)
+        return LSCAN_ERR_CUDA;
+    if (err & (DEV_ERR_CARRY_WAIT | DEV_ERR_BARRIER_WAIT)) return LSCAN_ERR_TIMEOUT;
+    return LSCAN_ERR_DEVICE;
 }

@@ -20,6 +20,15 @@
 //    keeps its own carry chain).  Different kinds run on different streams
 //    and overlap on the device; requests arriving while batches run are
 //    admitted and launched as slots free up.
+//  * Size-class lanes.  Requests of at most small_max elements (2^16 by
+//    default) form their own lane: their own admission queue and two launch
+//    slots on a stream created at the device's greatest priority, batched
+//    only with each other.  Bulk batches are capped at bulk_cap tiles (8192
+//    by default, ~128 MiB of 16 KiB tiles), so a small batch waits at most
+//    about one capped bulk launch for SM slots: when a bulk kernel's
+//    persistent CTAs retire, the block scheduler dispatches the
+//    higher-priority small batch before the bulk batch queued behind it.
+//    FIFO order holds within each lane.
 //  * Completion.  The scheduler polls each in-flight slot's last event
 //    (cudaEventQuery); nothing host-side sits in the stream, so the batch
 //    queued behind it starts the moment the kernel before it ends.  Launch
@@ -52,6 +61,9 @@ constexpr int64_t kMaxBatchTiles = 65536;   // ~1 GiB of 16 KiB tiles per launch
 constexpr int kSlotsPerStream = 2;          // a second batch queues behind the first
 constexpr int64_t kMinTileBytes = 8192;     // smallest input tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
+constexpr int64_t kDefaultSmallMax = int64_t{1} << 16;  // elements
+constexpr int64_t kDefaultBulkCap = 8192;               // tiles per bulk batch
+constexpr int kLanes = 2;                               // 0 bulk, 1 small
 
 double now_us(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0)
@@ -125,6 +137,7 @@ struct Request {
     lscan_req_stats st{};
     bool done = false;
     int64_t tag = -1;  // index in a replayed trace, -1 otherwise
+    int lane = 0;      // 0 bulk, 1 small
 };
 
 struct Batch {
@@ -144,6 +157,7 @@ struct Slot {
     Batch *inflight = nullptr;
     uint64_t launches = 0;
     bool owns_stream = false;
+    int lane = 0;  // which lane's requests this slot launches
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
     cudaEvent_t ev_fin = nullptr;  // after the batch's last operation (no timing)
 };
@@ -161,8 +175,11 @@ struct lscan_server {
     size_t pool_size = 0;
     PoolAllocator alloc;
     std::vector<Slot> slots;
-    std::deque<Request *> waiting;   // not admitted yet (output not allocated)
-    std::deque<Request *> admitted;  // ready to launch
+    std::deque<Request *> waiting[kLanes];   // not admitted (output not allocated)
+    std::deque<Request *> admitted[kLanes];  // ready to launch
+    int64_t small_max = kDefaultSmallMax;    // lane 1: n <= small_max (mu)
+    int64_t bulk_cap = kDefaultBulkCap;      // tiles per lane-0 batch (mu)
+    int64_t slot_words = 0;                  // status words per tile, reserved
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;     // requests, pool, slots
     std::mutex cb_mu;  // wake-up flag only
@@ -182,6 +199,18 @@ struct lscan_server {
 namespace lscan {
 namespace {
 
+// Widest status slot (64-bit words per tile) of any batched-list kernel: the
+// status words a launch slot reserves per tile.
+int64_t list_slot_words() {
+    ensure_kernels_registered();
+    int64_t w = 1;
+    for (int k = 0; k < kNumKinds; ++k)
+        for (int v = 0; v < kNumVariants; ++v)
+            if (g_kernels[k][MODE_LIST][v].fn && g_kernels[k][MODE_LIST][v].car_words > w)
+                w = g_kernels[k][MODE_LIST][v].car_words;
+    return w;
+}
+
 // Mark a request done.  Caller holds mu.
 void finish_locked(lscan_server *srv, Request *r) {
     r->done = true;
@@ -196,19 +225,24 @@ bool same_kind(const Request *a, const Request *b) {
     return a->op == b->op && a->dtype == b->dtype && a->inclusive == b->inclusive;
 }
 
-// Try to admit waiting requests (FIFO) into the pool.  Caller holds mu.
+// Try to admit waiting requests (FIFO within a lane; the small lane first)
+// into the pool.  Caller holds mu.
 void admit_locked(lscan_server *srv) {
-    while (!srv->waiting.empty()) {
-        Request *r = srv->waiting.front();
-        size_t off = 0;
-        const size_t bytes = static_cast<size_t>(r->n) * dtype_size(out_dtype_of(r->op, r->dtype));
-        if (!srv->alloc.alloc(bytes, &off)) break;  // head-of-line waits
-        r->y = srv->pool + off;
-        r->y_owned = true;
-        r->st.y = r->y;
-        srv->waiting.pop_front();
-        r->st.admit_us = now_us(srv->t0);
-        srv->admitted.push_back(r);
+    for (int lane = kLanes - 1; lane >= 0; --lane) {
+        auto &q = srv->waiting[lane];
+        while (!q.empty()) {
+            Request *r = q.front();
+            size_t off = 0;
+            const size_t bytes =
+                static_cast<size_t>(r->n) * dtype_size(out_dtype_of(r->op, r->dtype));
+            if (!srv->alloc.alloc(bytes, &off)) break;  // head-of-line waits
+            r->y = srv->pool + off;
+            r->y_owned = true;
+            r->st.y = r->y;
+            q.pop_front();
+            r->st.admit_us = now_us(srv->t0);
+            srv->admitted[lane].push_back(r);
+        }
     }
 }
 
@@ -241,16 +275,18 @@ void retire_locked(lscan_server *srv, int si, bool cuda_ok) {
 
 // Launch one batch on an idle slot.  Caller holds mu.
 bool launch_batch_locked(lscan_server *srv, int si) {
-    if (srv->admitted.empty()) return false;
     Slot &sl = srv->slots[si];
-    Request *head = srv->admitted.front();
+    auto &admitted = srv->admitted[sl.lane];
+    if (admitted.empty()) return false;
+    Request *head = admitted.front();
+    const int64_t cap = sl.lane == 0 ? srv->bulk_cap : kMaxBatchTiles;
     // plan with the head's kind (dummy disjoint aligned pointers, n = 1)
     LaunchSpec ls;
     if (plan_scan(head->op, head->dtype, head->inclusive, reinterpret_cast<void *>(256),
                   reinterpret_cast<void *>(4096), 1, nullptr, MODE_LIST, nullptr, 0,
                   &ls) != LSCAN_OK) {
         head->st.status = LSCAN_ERR_UNSUPPORTED;
-        srv->admitted.pop_front();
+        admitted.pop_front();
         finish_locked(srv, head);
         srv->cv_done.notify_all();
         return true;
@@ -259,14 +295,14 @@ bool launch_batch_locked(lscan_server *srv, int si) {
     Batch *b = new Batch();
     int64_t tiles = 0;
     bool aligned = true;
-    for (auto it = srv->admitted.begin(); it != srv->admitted.end();) {
+    for (auto it = admitted.begin(); it != admitted.end();) {
         Request *r = *it;
         if (!same_kind(r, head)) {
             ++it;
             continue;
         }
         const int64_t rt = (r->n + tile - 1) / tile;
-        if (!b->reqs.empty() && (tiles + rt > kMaxBatchTiles ||
+        if (!b->reqs.empty() && (tiles + rt > cap ||
                                  static_cast<int64_t>(b->reqs.size()) >= kMaxBatchRequests))
             break;
         sl.h_desc[b->reqs.size()] = SegDesc{r->x, r->y, r->n};
@@ -275,7 +311,7 @@ bool launch_batch_locked(lscan_server *srv, int si) {
         aligned = aligned && (reinterpret_cast<uintptr_t>(r->x) % 16 == 0) &&
                   (reinterpret_cast<uintptr_t>(r->y) % 16 == 0);
         b->reqs.push_back(r);
-        it = srv->admitted.erase(it);
+        it = admitted.erase(it);
     }
     const int64_t nseg = static_cast<int64_t>(b->reqs.size());
     sl.h_first[nseg] = tiles;
@@ -301,7 +337,7 @@ bool launch_batch_locked(lscan_server *srv, int si) {
                         cudaMemcpyHostToDevice, sl.stream);
         if (++sl.launches >= (1ull << 30) - 1) {  // keep the epoch tag from wrapping
             cudaMemsetAsync(sl.ctl, 0, CTL_WORDS * sizeof(uint32_t), sl.stream);
-            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * kMaxSlotWords * sizeof(uint64_t),
+            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * srv->slot_words * sizeof(uint64_t),
                             sl.stream);
             sl.launches = 0;
         }
@@ -357,7 +393,7 @@ void scheduler_main(lscan_server *srv) {
                 if (!srv->slots[si].inflight) launch_batch_locked(srv, static_cast<int>(si));
         busy = false;
         for (auto &sl : srv->slots) busy = busy || sl.inflight;
-        if (srv->stop && !busy && srv->admitted.empty()) break;
+        if (srv->stop && !busy && srv->admitted[0].empty() && srv->admitted[1].empty()) break;
     }
 }
 
@@ -391,11 +427,13 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     }
     auto up = [](size_t b) { return (b + kPoolAlign - 1) / kPoolAlign * kPoolAlign; };
     const size_t ctl_b = up(CTL_WORDS * sizeof(uint32_t));
-    const size_t st_b = up(kMaxBatchTiles * kMaxSlotWords * sizeof(uint64_t));
+    srv->slot_words = list_slot_words();
+    const size_t st_b = up(kMaxBatchTiles * srv->slot_words * sizeof(uint64_t));
     const size_t desc_b = up(kMaxBatchRequests * sizeof(SegDesc));
     const size_t first_b = up((kMaxBatchRequests + 1) * sizeof(int64_t));
     const size_t slot_b = ctl_b + st_b + desc_b + first_b;
-    const size_t reserve = slot_b * n_streams * kSlotsPerStream;
+    // n_streams bulk streams and one small-lane stream, two slots each
+    const size_t reserve = slot_b * (n_streams + 1) * kSlotsPerStream;
     if (hbm_budget_bytes < reserve + (size_t{1} << 20)) {
         delete srv;
         return nullptr;
@@ -409,7 +447,12 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     srv->pool = srv->mem + reserve;
     srv->pool_size = hbm_budget_bytes - reserve;
     srv->alloc.init(srv->pool_size);
-    const int n_slots = n_streams * kSlotsPerStream;
+    // slots: [0, n) bulk streams, n the small-lane stream; then a second
+    // slot for each of them on the same stream
+    const int n_str = n_streams + 1;
+    const int n_slots = n_str * kSlotsPerStream;
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     srv->slots.resize(n_slots);
     for (int i = 0; i < n_slots; ++i) {
         Slot &sl = srv->slots[i];
@@ -418,11 +461,13 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         sl.status = reinterpret_cast<uint64_t *>(base + ctl_b);
         sl.d_desc = reinterpret_cast<SegDesc *>(base + ctl_b + st_b);
         sl.d_first = reinterpret_cast<int64_t *>(base + ctl_b + st_b + desc_b);
-        if (i < n_streams)
-            cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        sl.lane = (i % n_str) == n_streams ? 1 : 0;
+        if (i < n_str)
+            cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking,
+                                         sl.lane == 1 ? prio_greatest : prio_least);
         else
-            sl.stream = srv->slots[i - n_streams].stream;  // shares the stream
-        sl.owns_stream = i < n_streams;
+            sl.stream = srv->slots[i - n_str].stream;  // shares the stream
+        sl.owns_stream = i < n_str;
         cudaMallocHost(&sl.h_desc, kMaxBatchRequests * sizeof(SegDesc));
         cudaMallocHost(&sl.h_first, (kMaxBatchRequests + 1) * sizeof(int64_t));
         cudaMallocHost(&sl.h_err, sizeof(uint32_t));
@@ -449,11 +494,13 @@ void lscan_server_destroy(lscan_server *srv) {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->stop = true;
         // requests that were never admitted cannot run any more
-        for (Request *r : srv->waiting) {
-            r->st.status = LSCAN_ERR_NOMEM;
-            finish_locked(srv, r);
+        for (auto &q : srv->waiting) {
+            for (Request *r : q) {
+                r->st.status = LSCAN_ERR_NOMEM;
+                finish_locked(srv, r);
+            }
+            q.clear();
         }
-        srv->waiting.clear();
     }
     kick(srv);
     if (srv->sched.joinable()) srv->sched.join();
@@ -481,6 +528,20 @@ lscan_status lscan_server_hold(lscan_server *srv, int hold) {
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->hold = hold != 0;
+    }
+    kick(srv);
+    return LSCAN_OK;
+}
+
+lscan_status lscan_server_set_lanes(lscan_server *srv, int64_t small_max_elems,
+                                   int64_t bulk_batch_tiles) {
+    if (!srv || small_max_elems < 0 || bulk_batch_tiles < 1 ||
+        bulk_batch_tiles > kMaxBatchTiles)
+        return LSCAN_ERR_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->small_max = small_max_elems;
+        srv->bulk_cap = bulk_batch_tiles;
     }
     kick(srv);
     return LSCAN_OK;
@@ -558,13 +619,14 @@ static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtyp
         }
         r->id = srv->next_id++;
         r->tag = tag;
+        r->lane = n <= srv->small_max ? 1 : 0;
         r->st.submit_us = tag >= 0 ? arrival_us : now_us(srv->t0);
         srv->reqs[r->id] = r;
         if (y) {
             r->st.admit_us = r->st.submit_us;
-            srv->admitted.push_back(r);
+            srv->admitted[r->lane].push_back(r);
         } else {
-            srv->waiting.push_back(r);
+            srv->waiting[r->lane].push_back(r);
         }
         *ticket = r->id;
     }

@@ -52,7 +52,7 @@
 namespace lscan {
 
 template <int ITEMS_, int CWARPS_, int STAGES_, int OSTAGES_ = 1, int MINB_ = 1,
-          int NCARRY_ = 1>
+          int NCARRY_ = 1, int RUN_ = 1, int SLOTW_ = 0>
 struct TileCfg {
     static constexpr int ITEMS = ITEMS_;
     static constexpr int CWARPS = CWARPS_;
@@ -60,6 +60,12 @@ struct TileCfg {
     static constexpr int OSTAGES = OSTAGES_;  // output staging buffers (0: direct)
     static constexpr int MINB = MINB_;        // CTAs per SM the registers must fit
     static constexpr int NCARRY = NCARRY_;    // carry warps (ring slots round-robin)
+    // consecutive tiles per ticket: only the first tile of a run looks back
+    // across CTAs; the others take the inclusive prefix of the CTA's own
+    // previous tile
+    static constexpr int RUN = RUN_;
+    // 64-bit status words per tile slot (0: the rule of status_slot_words)
+    static constexpr int SLOTW = SLOTW_;
     static constexpr int CTHREADS = CWARPS * 32;
     // + producer, reducer and NCARRY carry warps
     static constexpr int THREADS = CTHREADS + 64 + 32 * NCARRY;
@@ -300,10 +306,14 @@ __device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
 // 5256/5667/5668/5545 GB/s; a two-word FP64 carry with 32 KiB tiles (fp32
 // add, config 3) 2 words 5336, 4 words 5487, 8 words 5457 (means of 3),
 // but with 16 KiB tiles 4 words lost (bf16 add, config 2: 4892 -> 4684).
-template <class K, int TILE>
+template <class K, class Cfg>
 __host__ __device__ constexpr int status_slot_words() {
     constexpr int W = int(sizeof(typename K::Car) / 4);
-    constexpr int TILE_BYTES = TILE * int(sizeof(typename K::In));
+    constexpr int TILE_BYTES = Cfg::TILE * int(sizeof(typename K::In));
+    if constexpr (Cfg::SLOTW > 0) {
+        static_assert(Cfg::SLOTW >= W, "a slot holds the carry's words");
+        return Cfg::SLOTW;
+    }
     return W == 1 ? 2 : (TILE_BYTES >= 32768 ? 2 * W : W);
 }
 
@@ -594,7 +604,7 @@ struct TileReduce {
                 i = idx;
             }
         } else {
-            v = K::op(v, x);
+            v = op_step<K>(v, x);  // x is one element
         }
     }
     __device__ void warp_all() {
@@ -626,7 +636,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr bool SEG = MODE != MODE_SINGLE;  // segment heads exist
     constexpr int NC = Cfg::NCARRY;
     constexpr int CR = L::CR;
-    constexpr int SLOT = status_slot_words<K, TILE>();  // status words per tile
+    constexpr int SLOT = status_slot_words<K, Cfg>();  // status words per tile
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
@@ -700,6 +710,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
         // next segment head (segmented mode) of its next tile lies at or
         // after the one its previous tile needed: both searches resume here.
         int64_t cur = 0;
+        int64_t t = 0;     // tile of this ring use
+        int run_left = 0;  // tiles of the current run not yet issued
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             if (k >= ST) {
@@ -714,9 +726,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     break;
                 }
             }
-            int64_t t = 0;
-            if (lane == 0) t = static_cast<int64_t>(atomicAdd(p.ctl + CTL_TICKET, 1u));
-            t = __shfl_sync(0xffffffffu, t, 0);
+            if (run_left == 0 || t + 1 >= p.n_tiles) {
+                // a ticket hands out a run of RUN consecutive tiles
+                int64_t u = 0;
+                if (lane == 0) u = static_cast<int64_t>(atomicAdd(p.ctl + CTL_TICKET, 1u));
+                t = __shfl_sync(0xffffffffu, u, 0) * Cfg::RUN;
+                run_left = Cfg::RUN - 1;
+            } else {
+                ++t;
+                --run_left;
+            }
             if (lane == 0) tile_of[s] = t;
             if (t >= p.n_tiles) {
                 __syncwarp();
@@ -985,6 +1004,8 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
         // takes ring uses k = c, c + NC, ...: the tiles of one CTA are not
         // neighbours (tickets interleave across CTAs), so their look-backs
         // are independent and may overlap.
+        static_assert(Cfg::RUN == 1 || NC == 1, "a run's tiles share one carry warp");
+        Car run_incl = K::cident();  // inclusive prefix of the last tile carried
         for (int64_t k = warp - W_CARRY;; k += NC) {
             const int c = static_cast<int>(k % CR);
             const uint32_t par = static_cast<uint32_t>((k / CR) & 1);
@@ -1003,22 +1024,29 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             const bool okr = wait_phase(&reduced[c], par, wc);
             if (!__all_sync(0xffffffffu, okr) && lane == 0) *abort_s = 1;
             Car excl = K::cident();
-            if (t > 0 && !head0)
-                excl = p.carry_mode == CARRY_CHAINED
-                           ? chained_wait<K, SLOT>(p, wc, t, ebase, lane)
-                           : lookback<K, SLOT>(p, wc, t, ebase, lane);
-            else if (!SEG && t == 0)
+            if (t > 0 && !head0) {
+                if (Cfg::RUN > 1 && t % Cfg::RUN != 0)
+                    excl = run_incl;  // the previous tile of the run is ours
+                else
+                    excl = p.carry_mode == CARRY_CHAINED
+                               ? chained_wait<K, SLOT>(p, wc, t, ebase, lane)
+                               : lookback<K, SLOT>(p, wc, t, ebase, lane);
+            } else if (!SEG && t == 0) {
                 excl = carry_in_of<K>(p);
+            }
+            const bool has_head = SEG && head_r[c] != 0u;
+            // inclusive prefix of this tile (a tile holding a head restarts
+            // at its last head: the reducer's aggregate)
+            const Car incl = has_head ? agg_r[c] : K::cop(excl, agg_r[c]);
+            if constexpr (Cfg::RUN > 1) run_incl = incl;
             if (lane == 0) {
-                const bool has_head = SEG && head_r[c] != 0u;
                 // tile 0 and tiles holding a head got theirs from the reducer
                 if (t > 0 && !has_head && t != p.skip_tile)
-                    StatusIO<K, SLOT>::publish(p.status, t, ebase | ST_INCLUSIVE,
-                                         K::cop(excl, agg_r[c]));
+                    StatusIO<K, SLOT>::publish(p.status, t, ebase | ST_INCLUSIVE, incl);
                 // the last tile's inclusive prefix is the array's total (the
                 // carry-in of the next chunk when an array is scanned in chunks)
                 if (!SEG && t == p.n_tiles - 1 && p.total_out != nullptr)
-                    *static_cast<Car *>(p.total_out) = K::cop(excl, agg_r[c]);
+                    *static_cast<Car *>(p.total_out) = incl;
                 carry_s[c] = K::to_apply(excl);
                 stop_s[c] = *abort_s;  // one snapshot for every consumer warp
                 mbar_arrive(&carried[c]);
@@ -1100,7 +1128,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
 #pragma unroll
             for (int i = 1; i < ITEMS; ++i) {
                 if (SG && ((hb >> i) & 1u)) continue;
-                v[i] = K::op(v[i - 1], v[i]);
+                v[i] = op_step<K>(v[i - 1], v[i]);
             }
             // ---- warp scan of thread totals (Hillis-Steele, 5 rounds) ----
             Acc wv = v[ITEMS - 1];

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kTinyThreads) lscan_tiny_kernel(const TinyPara
 
     // thread-serial scan, then the thread totals across the warp
 #pragma unroll
-    for (int i = 1; i < kTinyItems; ++i) v[i] = K::op(v[i - 1], v[i]);
+    for (int i = 1; i < kTinyItems; ++i) v[i] = op_step<K>(v[i - 1], v[i]);
     Acc wv = v[kTinyItems - 1];
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {

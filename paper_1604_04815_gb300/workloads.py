@@ -147,6 +147,41 @@ def random_array(dtype, n, rng, kind="uniform"):
     raise ValueError(dtype)
 
 
+def ties_array(dtype, n, rng, pattern="zeros", first_zero=0, p_zero=0.02):
+    """Tie-heavy input for the float max scans (fp32, bf16 bits, double),
+    drawn from small pools.  Under max, equal values differ in their bits only
+    for +0 and -0, so these arrays make the first-occurrence rule observable:
+      "zeros"      : -1, -2.5 and -inf (the identity's value), with +0 or -0
+                     (random sign) at rate p_zero from index first_zero on;
+                     before it only negatives, so the running maximum is a
+                     zero whose sign is that of the first zero
+      "all_zeros"  : +0 or -0 only (random signs)
+      "repeated"   : 0.5, 0.25, -1 and +-0 at similar rates (repeated maxima)
+    """
+    if pattern == "all_zeros":
+        f = np.where(rng.random(size=n) < 0.5, -0.0, 0.0)
+    elif pattern == "repeated":
+        f = rng.choice(np.array([0.5, 0.25, -1.0, 0.0, -0.0]), size=n)
+    elif pattern == "zeros":
+        f = rng.choice(np.array([-1.0, -2.5, -np.inf]), size=n)
+        z = np.where(rng.random(size=n) < 0.5, -0.0, 0.0)
+        put = rng.random(size=n) < p_zero
+        put[:first_zero] = False
+        if 0 <= first_zero < n:
+            put[first_zero] = True
+        f = np.where(put, z, f)
+    else:
+        raise ValueError(pattern)
+    if dtype == "f64":
+        return f.astype(np.float64)
+    f32 = f.astype(np.float32)
+    if dtype == "f32":
+        return f32
+    if dtype == "bf16":
+        return f32_to_bf16_bits(f32)
+    raise ValueError(dtype)
+
+
 def serving_requests(n_req, seed=SEEDS["serving"], min_log2=10, max_log2=24):
     """Request mix: list of dicts (size, dtype, op); arrival gaps drawn later."""
     rng = np.random.default_rng(seed)

@@ -17,13 +17,13 @@ LOP = {"add": _lib.LSCAN_ADD, "max": _lib.LSCAN_MAX}
 TEST_WAIT_NS = 200_000_000
 
 # |y_j - ref_j| <= c * S_j for float add, per precision path
-BOUND = {"plain": 1e-5, "f64": 1e-5, "comp": 2.5e-7}
+BOUND = {"plain": 1e-5, "f64": 1e-5, "df": 1e-5, "comp": 2.5e-7}
 # double add (double in tile and carry): |y_j - ref_j| <= 1e-12 * S_j
 # (~9000 units of double roundoff: the worst case (K + 11 + carry hops) u S_j
 # of a double-in-tile, double-carry scan stays below it up to ~9000 hops)
 BOUND_F64_ADD = 1e-12
 PREC_CODE = {"plain": _lib.LSCAN_PREC_F32_CARRY, "f64": _lib.LSCAN_PREC_F64_CARRY,
-             "comp": _lib.LSCAN_PREC_COMPENSATED}
+             "comp": _lib.LSCAN_PREC_COMPENSATED, "df": _lib.LSCAN_PREC_DF_CARRY}
 
 
 def to_device(x_np, dtype, pad_front=0):

@@ -34,19 +34,27 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(so, name), name
 
 
+# input tile bytes of configurations 1..16 (the autotuner's search space)
+TILE_KIB = [8, 16, 32, 16, 32, 32, 16, 32, 8, 16, 32, 64, 16, 32, 32, 16]
+
+
 def test_version_and_configs(lib):
     assert "sm_103a" in lib.lscan_version()
-    assert lib.lscan_num_configs() == 3
-    for c in range(1, 4):
-        for dt in (lib.LSCAN_I32, lib.LSCAN_F32, lib.LSCAN_BF16):
+    assert lib.lscan_num_configs() == len(TILE_KIB)
+    for c in range(1, lib.lscan_num_configs() + 1):
+        for dt in (lib.LSCAN_I32, lib.LSCAN_F32, lib.LSCAN_BF16,
+                   lib.LSCAN_I64, lib.LSCAN_F64):
             info = lib.lscan_config_info(c, dt)
             assert info["tile"] == info["items"] * info["threads"]
             assert info["stages"] >= 2
-    # bulk-copy tiles are 8, 16 and 32 KiB of input
-    assert [lib.lscan_config_info(c, lib.LSCAN_I32)["tile"] * 4
-            for c in (1, 2, 3)] == [8192, 16384, 32768]
-    assert [lib.lscan_config_info(c, lib.LSCAN_BF16)["tile"] * 2
-            for c in (1, 2, 3)] == [8192, 16384, 32768]
+    # a configuration number means the same input bytes per tile for every
+    # element size (bf16 entry 12: 32 KiB, items per thread are capped at 32)
+    assert [lib.lscan_config_info(c, lib.LSCAN_I32)["tile"] * 4 // 1024
+            for c in range(1, 17)] == TILE_KIB
+    assert [lib.lscan_config_info(c, lib.LSCAN_I64)["tile"] * 8 // 1024
+            for c in range(1, 17)] == TILE_KIB
+    assert [lib.lscan_config_info(c, lib.LSCAN_BF16)["tile"] * 2 // 1024
+            for c in range(1, 17)] == TILE_KIB[:11] + [32] + TILE_KIB[12:]
 
 
 def test_host_argument_checks(lib):
@@ -74,9 +82,13 @@ def test_host_argument_checks(lib):
     o = L.make_options(precision=9)
     assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
         L.LSCAN_ERR_UNSUPPORTED
-    o = L.make_options(config=7)
+    o = L.make_options(config=L.lscan_num_configs() + 1)
     assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
         L.LSCAN_ERR_INVALID
+    # batched scans have the first six configurations only
+    o = L.make_options(config=7)
+    assert L.lscan_batched(L.LSCAN_ADD, L.LSCAN_I32, 1, base, base * 2,
+                           base * 4, 3, 10, o) == L.LSCAN_ERR_UNSUPPORTED
     o = L.make_options(carry=5)
     assert L.lscan_scan(L.LSCAN_ADD, L.LSCAN_F32, 1, base, base * 2, 10, o) == \
         L.LSCAN_ERR_INVALID
@@ -127,7 +139,7 @@ def test_host_scan_argument_checks(lib):
     assert f(add, 7, 1, base, base * 2, 10) == L.LSCAN_ERR_INVALID
     o = L.make_options(out_dtype=L.LSCAN_BF16)
     assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_UNSUPPORTED
-    o = L.make_options(config=7)
+    o = L.make_options(config=L.lscan_num_configs() + 1)
     assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_INVALID
     o = L.make_options(carry_in=base + 2)
     assert f(add, i32, 1, base, base * 2, 10, o) == L.LSCAN_ERR_INVALID
@@ -166,31 +178,63 @@ def test_server_entry_points_reject_null_handles(lib):
     L.lscan_server_destroy(None)                   # no-op
 
 
+def test_noalloc_size_limits(lib):
+    """lscan_scan_noalloc's fixed array holds 262144 status words; launches
+    use tile configuration 2 (2 words per tile for every kind), or the
+    plain-load configuration (tiles half as long) for unaligned pointers.
+    One element past each limit is refused on the host; no GPU is touched
+    (without one, an accepted size would fail with a CUDA error instead)."""
+    L = lib
+    f = L.lscan_scan_noalloc
+    base = 1 << 44   # never dereferenced
+    cases = [(L.LSCAN_ADD, L.LSCAN_I32, 0, 1 << 29),   # 4096-element tiles
+             (L.LSCAN_ADD, L.LSCAN_F32, 0, 1 << 29),
+             (L.LSCAN_MAX, L.LSCAN_BF16, 0, 1 << 30),  # 8192
+             (L.LSCAN_ADD, L.LSCAN_I64, 0, 1 << 28),   # 2048
+             (L.LSCAN_MAX, L.LSCAN_F64, 0, 1 << 28),
+             (L.LSCAN_ADD, L.LSCAN_I32, 4, 1 << 28)]   # unaligned x: 2048
+    for op, dt, off, limit in cases:
+        assert f(op, dt, 1, base + off, base * 2, limit + 1) == \
+            L.LSCAN_ERR_INVALID, (op, dt, off)
+        # at the limit the host checks pass; with no GPU the call then fails
+        # on its first CUDA call
+        assert f(op, dt, 1, base + off, base * 2, limit) == L.LSCAN_ERR_CUDA
+
+
 def test_tune_table_json_roundtrip(lib, tmp_path):
     """The tuning table loads/saves without a GPU; malformed files are
     refused and leave the table unchanged."""
+    import json
     p = tmp_path / "t.json"
-    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 3], [4, 1, 20, 1]]}')
+    # [kind, mode, log2 size class, configuration(, carry)]: four-field
+    # entries mean carry 0 (auto)
+    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 3], [4, 1, 20, 1],'
+                 ' [1, 0, 12, 2, 2]]}')
     assert lib.lscan_tune_load(p) == lib.LSCAN_OK
     out = tmp_path / "o.json"
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
-    import json
     d = json.loads(out.read_text())
     assert d["lscan_tune"] == 1
-    assert sorted(map(tuple, d["entries"])) == [(0, 0, 28, 3), (4, 1, 20, 1)]
+    assert sorted(map(tuple, d["entries"])) == [(0, 0, 28, 3, 0),
+                                                (1, 0, 12, 2, 2),
+                                                (4, 1, 20, 1, 0)]
     bad = tmp_path / "bad.json"
-    bad.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 9]]}')
-    assert lib.lscan_tune_load(bad) == lib.LSCAN_ERR_INVALID
+    for entries in ("[[0, 0, 28, 99]]",        # no such configuration
+                    "[[0, 1, 28, 9]]",         # not built for batched scans
+                    "[[0, 0, 28, 2, 7]]",      # no such carry protocol
+                    "[[99, 0, 28, 2]]"):       # no such kind
+        bad.write_text('{"lscan_tune": 1, "entries": %s}' % entries)
+        assert lib.lscan_tune_load(bad) == lib.LSCAN_ERR_INVALID, entries
     assert lib.lscan_tune_load(tmp_path / "missing.json") == lib.LSCAN_ERR_INVALID
     assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
     assert json.loads(out.read_text())["entries"] == []
-    # defaults are per kind (kind 5, fp32 add with an FP64 carry, defaults to
-    # configuration 3): only entries that differ from them are saved
-    p.write_text('{"lscan_tune": 1, "entries": [[5, 0, 28, 3], [5, 0, 27, 2]]}')
+    # defaults are per kind and mode (kind 0, int32 add, defaults to
+    # configuration 6): only entries that differ from them are saved
+    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 6], [0, 0, 27, 2]]}')
     assert lib.lscan_tune_load(p) == lib.LSCAN_OK
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
-    assert json.loads(out.read_text())["entries"] == [[5, 0, 27, 2]]
+    assert json.loads(out.read_text())["entries"] == [[0, 0, 27, 2, 0]]
     assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_autotune(0, 0, 1, 16, 32, 0)[0] == lib.LSCAN_ERR_INVALID
 

@@ -31,6 +31,10 @@ KINDS = [
     ("add", "bf16", "plain", True),
     ("add", "bf16", "f64", True),
     ("add", "bf16", "comp", True),
+    # the double-float carry (the default precision of float add)
+    ("add", "f32", "df", False),
+    ("add", "bf16", "df", False),
+    ("add", "bf16", "df", True),
     # the paper's 64-bit types (Table 2)
     ("add", "i64", None, False),
     ("max", "i64", None, False),
@@ -39,6 +43,22 @@ KINDS = [
 ]
 KIND_IDS = [f"{o}-{d}-{p or 'exact'}{'-bf16out' if b else ''}"
             for o, d, p, b in KINDS]
+
+
+def _pick(*ids):
+    """(kinds, ids) of the named kinds, for parametrize."""
+    idx = [KIND_IDS.index(i) for i in ids]
+    return [KINDS[i] for i in idx], [KIND_IDS[i] for i in idx]
+
+
+CHAINED_KINDS = _pick("add-i32-exact", "max-i32-exact", "add-f32-f64",
+                      "add-f32-df", "add-bf16-comp", "add-i64-exact",
+                      "add-f64-exact")
+BATCHED_KINDS = _pick("add-i32-exact", "max-i32-exact", "max-f32-exact",
+                      "max-bf16-exact", "add-f32-f64", "add-f32-comp",
+                      "add-f32-df", "add-bf16-f64", "add-bf16-df",
+                      "add-i64-exact", "max-i64-exact", "max-f64-exact",
+                      "add-f64-exact")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -67,7 +87,11 @@ def _sizes(tile):
     return [1, 2, 31, 33, 1000, tile - 1, tile, tile + 1, 7 * tile + 123]
 
 
-@pytest.mark.parametrize("config", [1, 2, 3])
+# every tile configuration the autotuner may choose for a single array
+ALL_CONFIGS = list(range(1, 17))
+
+
+@pytest.mark.parametrize("config", ALL_CONFIGS)
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
 @pytest.mark.parametrize("kind", KINDS, ids=KIND_IDS)
 def test_sizes_configs(kind, inclusive, config):
@@ -125,8 +149,7 @@ def test_in_place(kind, config):
 
 
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
-@pytest.mark.parametrize("kind", [KINDS[i] for i in (0, 1, 5, 9, 13, 16)],
-                         ids=[KIND_IDS[i] for i in (0, 1, 5, 9, 13, 16)])
+@pytest.mark.parametrize("kind", CHAINED_KINDS[0], ids=CHAINED_KINDS[1])
 def test_chained_carry(kind, inclusive):
     """The paper's neighbour-to-neighbour hand-off (Algorithm 4)."""
     op, dtype, prec, ob = kind
@@ -195,17 +218,14 @@ def _offsets(kind, rng):
                                      "empty_tail", "loguniform",
                                      "tile_aligned"])
 @pytest.mark.parametrize("inclusive", [True, False], ids=["incl", "excl"])
-@pytest.mark.parametrize("kind", [KINDS[i] for i in
-                                  (0, 1, 2, 3, 5, 6, 8, 13, 14, 15, 16)],
-                         ids=[KIND_IDS[i] for i in
-                              (0, 1, 2, 3, 5, 6, 8, 13, 14, 15, 16)])
+@pytest.mark.parametrize("kind", BATCHED_KINDS[0], ids=BATCHED_KINDS[1])
 def test_batched(kind, inclusive, pattern):
     op, dtype, prec, ob = kind
     rng = np.random.default_rng(sum(map(ord, pattern)))
     off = _offsets(pattern, rng)
     n = int(off[-1])
     x = _input(op, dtype, n, seed=9)
-    for config in (1, 2, 3):
+    for config in range(1, 7):  # the configurations built for batched scans
         xd = to_device(x, dtype)
         od = torch.from_numpy(off).cuda()
         y = torch.empty(n, dtype=torch.float32 if (op == "add" and
@@ -355,10 +375,17 @@ def test_autotune_picks_a_config_and_stays_correct(tmp_path):
         xd = to_device(x, dtype)
         y = torch.empty_like(xd)
         s = torch.cuda.current_stream().cuda_stream
-        st, best, ms = _lib.lscan_autotune(LOP[op], LDT[dtype], 1,
-                                           xd.data_ptr(), y.data_ptr(),
-                                           xd.shape[0], reps=2, stream=s)
-        assert st == _lib.LSCAN_OK and 1 <= best <= 3 and ms > 0
+        st, res = _lib.lscan_autotune(LOP[op], LDT[dtype], 1, xd.data_ptr(),
+                                      y.data_ptr(), xd.shape[0], reps=5,
+                                      stream=s)
+        assert st == _lib.LSCAN_OK
+        assert 1 <= res["config"] <= _lib.lscan_num_configs()
+        assert res["n_timed"] == _lib.lscan_num_configs()
+        assert res["ms"] > 0 and res["ms"] == min(
+            [res["ms"]] + list(res["ms_by_config"].values()))
+        assert res["default_ms"] >= res["ms"]
+        # 1025 tiles at most: the chained carry is timed too
+        assert res["chained_ms"] > 0
         assert_matches(op, dtype, x, to_host(y))       # y holds a real scan
         y2 = run_c_abi(op, dtype, xd, True)             # tuned configuration
         assert_matches(op, dtype, x, to_host(y2))

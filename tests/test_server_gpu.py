@@ -99,7 +99,10 @@ def test_server_outputs_and_admission_under_a_small_budget():
     n = 1 << 20                      # 4 MiB output each
     reqs = [random_array("i32", n, rng, kind="full") for _ in range(24)]
     xs = [to_device(x, "i32") for x in reqs]
-    srv = lscan.Server(budget_bytes=24 << 20, n_streams=2)  # pool < 24 MiB
+    # the launch slots reserve their scratch first (6 slots x ~8 MiB of
+    # status words); the pool that remains (< 40 MiB) holds only a few of
+    # the 24 outputs of 4 MiB at a time
+    srv = lscan.Server(budget_bytes=88 << 20, n_streams=2)
     try:
         tks = [srv.submit(xd, "add", True) for xd in xs]     # out=None
         for x, tk in zip(reqs, tks):
@@ -111,7 +114,7 @@ def test_server_outputs_and_admission_under_a_small_budget():
             assert_matches("add", "i32", x, to_host(y))
             srv.release(tk)
         # a request whose output can never fit is refused at once
-        big = torch.empty(8 << 20, dtype=torch.int32, device="cuda")
+        big = torch.empty(16 << 20, dtype=torch.int32, device="cuda")
         with pytest.raises(lscan.LscanError):
             srv.submit(big, "add", True)
     finally:
