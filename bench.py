@@ -290,6 +290,12 @@ def run_gpu(args, ws, rank, local):
     step_bytes = sum(2 * N * ELEM_BYTES[dt] for _, _, dt in CASES)
 
     def launch(case, op, dt):
+        if args.sharded and ws > 1:
+            # this rank's 2^k elements are shard `rank` of one array of
+            # ws * 2^k: reduce, all-gather of the totals, carry-in scan
+            lscan.shard.sharded_scan(xs[case], op, True, out=ys[case],
+                                     stream=stream)
+            return
         st = _lib.lscan_scan(_lib.LSCAN_ADD if op == "add" else _lib.LSCAN_MAX,
                              _lib.LSCAN_I32 if dt == "i32" else _lib.LSCAN_F32,
                              1, xs[case].data_ptr(), ys[case].data_ptr(), N,
@@ -471,7 +477,10 @@ def run_gpu(args, ws, rank, local):
         "config": {"workload": _workload(N), "n": N, "tile_config": args.config or tuned,
                    "carry": ["auto", "lookback", "chained"][args.carry],
                    "l2": "inputs 1 GiB per array > 129 MB L2; no flush",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": (f"one array sharded over {ws} ranks "
+                                   "(reduce, all-gather of totals, carry-in "
+                                   "scan)" if args.sharded and ws > 1
+                                   else f"replicas x{ws}")},
         "hbm_frac_measured": round(value / ws / peak, 4),
         "geps": round(N * len(CASES) * args.steps * ws / elapsed_max / 1e9, 2),
         "kernels": {c: {k: round(v, 2) for k, v in d.items()}
@@ -991,6 +1000,10 @@ def main():
                     help="timed launches per configuration in the autotuner "
                          "(median kept)")
     ap.add_argument("--carry", type=int, default=0)
+    ap.add_argument("--sharded", action="store_true",
+                    help="with N > 1 ranks: each rank's arrays are shards of "
+                         "one N-times-longer array (a collective per scan) "
+                         "instead of independent replicas")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-radix", action="store_true")
     ap.add_argument("--e2e-chunk", type=int, default=0,

@@ -112,14 +112,18 @@ typedef struct lscan_options {
     int32_t config;      /* 0 = tuned; 1..lscan_num_configs() pick a
                             bulk-copy tile configuration */
     int32_t max_ctas;    /* cap on persistent CTAs, 0 = occupancy x SMs */
-    int32_t reserved;
+    int32_t carry_in_type; /* 0: carry_in is one output element; 1: it holds
+                              a value of the kind's carry type
+                              (lscan_carry_bytes bytes, aligned to that size),
+                              as lscan_reduce and lscan_carry_combine make */
     /* Single-array scans only (not in the paper: the carry-in of a scan
      * sharded over devices, where shard g starts from the total of the shards
      * before it).  NULL = the operator's identity.  Otherwise a device
-     * pointer to ONE element of the output type, read by the kernel in
+     * pointer to ONE element of the output type (carry_in_type 0) or to one
+     * value of the kind's carry type (carry_in_type 1), read by the kernel in
      * stream order: inclusive y_j = c (+) x_0 (+) ... (+) x_j, exclusive
      * y_0 = c and y_j = c (+) x_0 (+) ... (+) x_{j-1}.  It must be aligned
-     * to the output element size; batched calls with a carry-in return
+     * to its size; batched calls with a carry-in return
      * LSCAN_ERR_INVALID. */
     const void *carry_in;
 } lscan_options;
@@ -212,6 +216,47 @@ lscan_status lscan_scan_noalloc(lscan_op op, lscan_dtype dtype, int inclusive,
  * its output is wrong) or LSCAN_ERR_CUDA.  Reads by symbol, allocating
  * nothing.  (The paper has no counterpart.) */
 lscan_status lscan_noalloc_status(void *stream);
+
+/* ------------------------------------------------------- sharded scans
+ * A scan of one array split into contiguous shards over several devices
+ * (not in the paper, whose arrays live on one GPU: its inter-block carry of
+ * Section 4.3 lifted one level up).  Reduce-then-scan, 3N bytes:
+ *   1. each device: lscan_reduce(shard) -> its total, in the carry type;
+ *   2. the caller's collective all-gathers the P totals (lscan_carry_bytes
+ *      bytes each);
+ *   3. each device: lscan_carry_combine(totals of the shards before it) ->
+ *      its offset (on the host), copied to the device and passed to
+ *      lscan_scan as carry_in with carry_in_type = 1.
+ * The carry type keeps the precision path's accuracy across the boundary:
+ * uint32/uint64 wrapping sums, int32/int64/float maxima (double max as an
+ * order-preserving int64 key), fp32 for the fp32 carry, FP64 for the FP64
+ * carry and double add, a normalised fp32 (hi, lo) pair for the
+ * double-float and compensated paths. */
+
+/* Size in bytes (4 or 8) of the carry type of the scan lscan_scan would run
+ * for (op, dtype, opts: out_dtype and precision); 0 if unsupported. */
+int32_t lscan_carry_bytes(lscan_op op, lscan_dtype dtype,
+                          const lscan_options *opts);
+/* d_total (DEVICE, lscan_carry_bytes bytes, aligned to that size, not
+ * overlapping x) = x_0 (+) ... (+) x_{n-1} in the kind's carry type (the
+ * identity for n = 0).  One pass over x (16-byte loads when x is 16-byte
+ * aligned; any element-aligned x is accepted).  Per 16-byte chunk the
+ * elements are folded in the scan's in-tile arithmetic and the chunks in the
+ * carry arithmetic; float max keeps the first occurrence (+0 / -0).
+ * Scratch (1024 partials and a done word per (device, stream)) is owned by
+ * the library, allocated on first use (LSCAN_ERR_BUSY during capture) and
+ * freed by lscan_shutdown.  Asynchronous on stream. */
+lscan_status lscan_reduce(lscan_op op, lscan_dtype dtype, const void *x,
+                          int64_t n, const lscan_options *opts, void *d_total,
+                          void *stream);
+/* HOST: h_out = totals[0] (+) ... (+) totals[count - 1] in the kind's carry
+ * arithmetic, earlier operands first (the identity for count = 0).
+ * h_totals: count values of lscan_carry_bytes bytes each, in host memory.
+ * Needs no GPU. */
+lscan_status lscan_carry_combine(lscan_op op, lscan_dtype dtype,
+                                 const lscan_options *opts,
+                                 const void *h_totals, int32_t count,
+                                 void *h_out);
 
 /* Batched scan of n_seg independent arrays stored back to back in x (and y):
  * segment s is elements [offsets[s], offsets[s+1]).  d_offsets is a DEVICE

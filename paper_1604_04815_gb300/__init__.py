@@ -9,6 +9,7 @@ torch is used for device memory and streams only.
     y = lscan.exclusive(x, op="max")
     y = lscan.batched(x, offsets)          # offsets: int64 cuda tensor [S+1]
     y = lscan.scan_host(x_cpu)             # x_cpu in (pinned) host memory
+    y = lscan.shard.sharded_scan(x_shard)  # one rank's shard of a global scan
 """
 import torch
 
@@ -21,7 +22,7 @@ _DT = {torch.int32: _lib.LSCAN_I32, torch.float32: _lib.LSCAN_F32,
 _TORCH_DT = {v: k for k, v in _DT.items()}
 _OPS = {"add": _lib.LSCAN_ADD, "max": _lib.LSCAN_MAX}
 _PREC = {None: 0, "default": 0, "f32": 1, "plain": 1, "f64": 2,
-         "compensated": 3, "comp": 3}
+         "compensated": 3, "comp": 3, "df": 4, "double-float": 4}
 _CARRY = {None: 0, "auto": 0, "lookback": 1, "chained": 2}
 
 
@@ -348,3 +349,6 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+from . import shard  # noqa: E402,F401  (sharded scans over ranks)

@@ -41,13 +41,14 @@ EXPORTED = [
     "lscan_server_hold", "lscan_server_set_lanes",
     "lscan_autotune", "lscan_tune_save", "lscan_tune_load",
     "lscan_tune_reset", "lscan_select_flagged", "lscan_radix_offsets",
+    "lscan_carry_bytes", "lscan_reduce", "lscan_carry_combine",
 ]
 
 
 class lscan_options(ctypes.Structure):
     _fields_ = [("out_dtype", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("carry", ctypes.c_int32), ("config", ctypes.c_int32),
-                ("max_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_ctas", ctypes.c_int32), ("carry_in_type", ctypes.c_int32),
                 ("carry_in", ctypes.c_void_p)]
 
 
@@ -123,6 +124,8 @@ def load():
         "lscan_autotune": [i32, i32, i32, vp, vp, i64, vp, i64, optp, i32, vp,
                            ctypes.POINTER(lscan_tune_result)],
         "lscan_noalloc_status": [vp],
+        "lscan_reduce": [i32, i32, vp, i64, optp, vp, vp],
+        "lscan_carry_combine": [i32, i32, optp, vp, ctypes.c_int32, vp],
         "lscan_tune_save": [ctypes.c_char_p],
         "lscan_tune_load": [ctypes.c_char_p],
         "lscan_tune_reset": [],
@@ -161,6 +164,8 @@ def load():
     lib.lscan_launch_count.restype = ctypes.c_uint64
     lib.lscan_num_configs.argtypes = []
     lib.lscan_num_configs.restype = ctypes.c_int32
+    lib.lscan_carry_bytes.argtypes = [i32, i32, optp]
+    lib.lscan_carry_bytes.restype = ctypes.c_int32
     _lib = lib
     return lib
 
@@ -175,7 +180,7 @@ def check(status, where):
 
 
 def make_options(out_dtype=0, precision=0, carry=0, config=0, max_ctas=0,
-                 carry_in=None):
+                 carry_in=None, carry_in_type=0):
     o = lscan_options()
     o.out_dtype = out_dtype
     o.precision = precision
@@ -183,6 +188,7 @@ def make_options(out_dtype=0, precision=0, carry=0, config=0, max_ctas=0,
     o.config = config
     o.max_ctas = max_ctas
     o.carry_in = carry_in
+    o.carry_in_type = carry_in_type
     return o
 
 
@@ -287,6 +293,28 @@ def lscan_autotune(op, dtype, inclusive, x, y, n, d_offsets=None, n_seg=0,
 
 def lscan_noalloc_status(stream=None):
     return load().lscan_noalloc_status(stream)
+
+
+def _optref(opts):
+    return ctypes.byref(opts) if opts is not None else None
+
+
+def lscan_carry_bytes(op, dtype, opts=None):
+    return int(load().lscan_carry_bytes(op, dtype, _optref(opts)))
+
+
+def lscan_reduce(op, dtype, x, n, opts=None, d_total=None, stream=None):
+    return load().lscan_reduce(op, dtype, x, n, _optref(opts), d_total, stream)
+
+
+def lscan_carry_combine(op, dtype, totals, count, opts=None):
+    """Host fold of `count` carry-type totals (bytes, concatenated); returns
+    (status, bytes of the result)."""
+    nb = lscan_carry_bytes(op, dtype, opts)
+    out = ctypes.create_string_buffer(max(nb, 1))
+    buf = ctypes.create_string_buffer(bytes(totals), max(len(totals), 1))
+    st = load().lscan_carry_combine(op, dtype, _optref(opts), buf, count, out)
+    return st, out.raw[:nb]
 
 
 def lscan_tune_save(path):

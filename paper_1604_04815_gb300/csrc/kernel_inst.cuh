@@ -3,6 +3,7 @@
 #include <utility>
 
 #include "kernel_table.h"
+#include "reduce_kernel.cuh"
 #include "scan_kernel.cuh"
 #include "tiny_kernel.cuh"
 
@@ -159,6 +160,8 @@ void fill_select(int kind) {
 template <class K>
 void fill_kind(int kind) {
     g_tiny_kernels[kind] = reinterpret_cast<const void *>(&lscan_tiny_kernel<K>);
+    g_reduce_kernels[kind] = reinterpret_cast<const void *>(&lscan_reduce_kernel<K>);
+    g_carry_bytes[kind] = int(sizeof(typename K::Car));
     fill_mode<K, MODE_SINGLE>(kind);
     fill_mode<K, MODE_SEGMENTED>(kind);
     fill_mode<K, MODE_LIST>(kind);

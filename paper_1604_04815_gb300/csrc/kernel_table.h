@@ -35,6 +35,10 @@ struct KernelEntry {
 extern KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
 // [kind]: the single-CTA kernel for n <= kTinyMax
 extern const void *g_tiny_kernels[kNumKinds];
+// [kind]: the reduction to the kind's carry type (sharded scans), and the
+// carry type's size in bytes
+extern const void *g_reduce_kernels[kNumKinds];
+extern int g_carry_bytes[kNumKinds];
 
 void register_all_kernels();
 

@@ -151,6 +151,8 @@ struct FloatOut<uint16_t> {
 template <class InT>
 struct KFMax {
     static constexpr bool kTieOrdered = true;  // +0 / -0 compare equal
+    // a tile's maximum may be found on the raw bits (raw_float_max_tile)
+    static constexpr bool kRawMax = true;
     // strict "greater" of the operator (tie-ordered folds; +0 == -0)
     __device__ static bool gt(float a, float b) { return a > b; }
     using In = InT;
@@ -430,6 +432,11 @@ struct KSelect {
     __device__ static Out fin(CarA, Acc) { return Out{}; }  // not used
     __device__ static Car car_of_out(Out) { return 0ull; }  // no carry-in
 };
+
+template <class K, class = void>
+struct has_raw_max : std::false_type {};
+template <class K>
+struct has_raw_max<K, std::void_t<decltype(K::kRawMax)>> : std::bool_constant<K::kRawMax> {};
 
 template <class K, class = void>
 struct is_select : std::false_type {};

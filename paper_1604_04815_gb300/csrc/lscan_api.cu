@@ -25,6 +25,8 @@ namespace lscan {
 
 KernelEntry g_kernels[kNumKinds][MODE_COUNT][kNumVariants];
 const void *g_tiny_kernels[kNumKinds] = {};
+const void *g_reduce_kernels[kNumKinds] = {};
+int g_carry_bytes[kNumKinds] = {};
 
 void register_i32_add();
 void register_i32_max();
@@ -308,6 +310,21 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     return LSCAN_OK;
 }
 
+lscan_status resolve_kind(int op, int dtype, const lscan_options *opts, int *kind,
+                          int *out_dtype) {
+    std::call_once(g_reg_once, register_all_kernels);
+    if (dtype_size(dtype) == 0 || (op != LSCAN_ADD && op != LSCAN_MAX)) return LSCAN_ERR_INVALID;
+    int od = dtype;
+    if (op == LSCAN_ADD && dtype == LSCAN_BF16) od = LSCAN_F32;
+    if (opts && opts->out_dtype > 0 && opts->out_dtype <= LSCAN_F64) od = opts->out_dtype;
+    const int prec = opts ? opts->precision : LSCAN_PREC_DEFAULT;
+    const int k = select_kind(op, dtype, od, prec);
+    if (k < 0) return LSCAN_ERR_UNSUPPORTED;
+    *kind = k;
+    if (out_dtype) *out_dtype = od;
+    return LSCAN_OK;
+}
+
 lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
                        int64_t n, const lscan_options *opts, int mode,
                        const int64_t *offsets, int64_t n_seg, LaunchSpec *ls) {
@@ -315,13 +332,9 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     if (n < 0) return LSCAN_ERR_INVALID;
     const int isz = dtype_size(dtype);
     if (isz == 0 || (op != LSCAN_ADD && op != LSCAN_MAX)) return LSCAN_ERR_INVALID;
-    int out_dtype = dtype;
-    if (op == LSCAN_ADD && dtype == LSCAN_BF16) out_dtype = LSCAN_F32;
-    if (opts && opts->out_dtype > 0 && opts->out_dtype <= LSCAN_F64)
-        out_dtype = opts->out_dtype;
-    const int prec = opts ? opts->precision : LSCAN_PREC_DEFAULT;
-    const int kind = select_kind(op, dtype, out_dtype, prec);
-    if (kind < 0) return LSCAN_ERR_UNSUPPORTED;
+    int kind = -1, out_dtype = dtype;
+    lscan_status rs = resolve_kind(op, dtype, opts, &kind, &out_dtype);
+    if (rs != LSCAN_OK) return rs;
     const int osz = dtype_size(out_dtype);
     if (n > 0) {
         if (x == nullptr || y == nullptr) return LSCAN_ERR_INVALID;
@@ -349,7 +362,12 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     // the chained hand-off won)
     if (carry == LSCAN_CARRY_AUTO && cfg == 0) carry = tuned_carry;
     const void *carry_in = opts ? opts->carry_in : nullptr;
-    if (carry_in && (mode != MODE_SINGLE || reinterpret_cast<uintptr_t>(carry_in) % osz != 0))
+    const int cit = opts ? opts->carry_in_type : 0;
+    if (cit < 0 || cit > 1) return LSCAN_ERR_INVALID;
+    // a carry-in is one output element, or (type 1) a value of the kind's
+    // carry type, aligned to its size
+    const int cin_align = cit == 1 ? g_carry_bytes[kind] : osz;
+    if (carry_in && (mode != MODE_SINGLE || reinterpret_cast<uintptr_t>(carry_in) % cin_align != 0))
         return LSCAN_ERR_INVALID;
 
     ls->kind = kind;
@@ -365,6 +383,7 @@ lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
     ls->max_ctas = opts ? opts->max_ctas : 0;
     ls->status_words = static_cast<size_t>(n_tiles) * e.car_words;
     ls->carry_in = carry_in;
+    ls->carry_in_car = carry_in != nullptr && cit == 1;
     // arrays of at most one tile take the single-CTA kernel when the tile
     // configuration is left to the library
     ls->tiny = mode == MODE_SINGLE && cfg == 0 && n > 0 && n <= kTinyMax &&
@@ -488,6 +507,7 @@ lscan_status lscan_reserve(void *stream, int64_t max_elems) {
 void lscan_shutdown(void) {
     shutdown_host_pipes();
     shutdown_radix();
+    shutdown_reduce();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

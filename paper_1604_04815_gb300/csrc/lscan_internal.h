@@ -40,6 +40,9 @@ struct DevBuffers {
     uint64_t *status;
 };
 
+// kind id (and output dtype) of (op, dtype, opts: out_dtype, precision)
+lscan_status resolve_kind(int op, int dtype, const lscan_options *opts, int *kind,
+                          int *out_dtype);
 lscan_status plan_scan(int op, int dtype, int inclusive, const void *x, void *y,
                        int64_t n, const lscan_options *opts, int mode,
                        const int64_t *offsets, int64_t n_seg, LaunchSpec *ls);
@@ -63,6 +66,7 @@ std::mutex &api_mutex();
 void shutdown_graphs_locked();
 void shutdown_host_pipes();  // frees the staging of lscan_scan_host
 void shutdown_radix();       // frees the counters of lscan_radix_offsets
+void shutdown_reduce();      // frees the partials of lscan_reduce
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
 // entry = configuration | carry << 8

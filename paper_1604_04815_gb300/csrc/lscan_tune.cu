@@ -41,8 +41,8 @@ int default_variant(int kind, int mode) {
     switch (kind) {
         case KIND_I32_ADD: return 6;              // 6155
         case KIND_I32_MAX: return single ? 8 : 6; // 6140
-        case KIND_F32_MAX: return single ? 8 : 5; // 5625
-        case KIND_BF16_MAX: return single ? 13 : 4;
+        case KIND_F32_MAX: return single ? 8 : 5; // 6084
+        case KIND_BF16_MAX: return single ? 11 : 5;  // 4415
         case KIND_F32_ADD_PLAIN: return 6;        // 6180
         case KIND_F32_ADD_F64: return single ? 12 : 5;
         case KIND_F32_ADD_DF: return single ? 8 : 5;   // 5880

@@ -617,6 +617,78 @@ struct TileReduce {
     }
 };
 
+// Maximum of a full tile of fp32 or bf16 values under the scan's rule
+// (first occurrence on ties, so +0 and -0 compare equal), found on the raw
+// bits by one warp.  As signed integers the bits of non-negative floats
+// order like their values, and those of negative floats in reverse with -0
+// the smallest: so the signed maximum m1 of the raw bits is the largest
+// non-negative value when there is one (m1 >= 0), and otherwise the signed
+// minimum m2 is the negative value closest to zero (-0 if present; then no
+// +0 exists and every zero of the tile is -0).  Equal values other than
+// zeros have equal bits, so the result is exact except when the maximum is
+// +0 and a -0 may precede it: only then (m1 == 0) the tile is searched for
+// its first zero.  Two integer min/max per element (bf16: per two elements,
+// 16-bit SIMD) instead of a compare-select chain with index tracking.
+template <class In, int TILE>
+__device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane) {
+    constexpr int WORDS = TILE * int(sizeof(In)) / 4;
+    const uint4 *q4 = reinterpret_cast<const uint4 *>(tsm);
+    int32_t m1, m2;
+    if constexpr (sizeof(In) == 4) {
+        m1 = INT32_MIN;
+        m2 = INT32_MAX;
+        for (int c = lane; c < WORDS / 4; c += 32) {
+            const uint4 q = q4[c];
+            const int32_t w[4] = {int32_t(q.x), int32_t(q.y), int32_t(q.z), int32_t(q.w)};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                m1 = max(m1, w[j]);
+                m2 = min(m2, w[j]);
+            }
+        }
+    } else {
+        static_assert(sizeof(In) == 2, "fp32 or bf16");
+        uint32_t p1 = 0x80008000u, p2 = 0x7fff7fffu;  // per 16-bit half
+        for (int c = lane; c < WORDS / 4; c += 32) {
+            const uint4 q = q4[c];
+            const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                p1 = __vmaxs2(p1, w[j]);
+                p2 = __vmins2(p2, w[j]);
+            }
+        }
+        m1 = max(int32_t(int16_t(p1 & 0xffffu)), int32_t(int16_t(p1 >> 16)));
+        m2 = min(int32_t(int16_t(p2 & 0xffffu)), int32_t(int16_t(p2 >> 16)));
+    }
+    m1 = __reduce_max_sync(0xffffffffu, m1);
+    m2 = __reduce_min_sync(0xffffffffu, m2);
+    uint32_t bits;
+    if (m1 > 0) {
+        bits = static_cast<uint32_t>(m1);
+    } else if (m1 < 0) {
+        bits = static_cast<uint32_t>(m2);
+    } else {
+        // the maximum is a zero: the first zero of the tile decides its sign
+        constexpr uint32_t MAG = sizeof(In) == 4 ? 0x7fffffffu : 0x7fffu;
+        const In *e = reinterpret_cast<const In *>(tsm);
+        bits = 0u;
+        for (int base = 0; base < TILE; base += 32) {
+            const uint32_t b = static_cast<uint32_t>(e[base + lane]);
+            const uint32_t z = __ballot_sync(0xffffffffu, (b & MAG) == 0u);
+            if (z) {
+                bits = __shfl_sync(0xffffffffu, b, __ffs(z) - 1);
+                break;
+            }
+        }
+    }
+    if constexpr (sizeof(In) == 4) {
+        return __uint_as_float(bits);
+    } else {
+        return __uint_as_float((bits & 0xffffu) << 16);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 template <class K, class Cfg, int MODE, bool TMA>
 __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
@@ -934,6 +1006,15 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             // with and without a head inside the tile
             auto reduce_tile = [&](auto seg_tag) {
                 constexpr bool SG = decltype(seg_tag)::value;
+                if constexpr (has_raw_max<K>::value && !SG && TMA) {
+                    if (nt == TILE) {
+                        // whole tile, one value: every lane holds it
+                        r.v = raw_float_max_tile<In, TILE>(
+                            smem + L::off_in + s * TILE * sizeof(In), lane);
+                        r.i = 0;
+                        return;
+                    }
+                }
                 if (TMA && nt == TILE) {
                     // one accumulator per element position in a 16-byte chunk:
                     // EPC independent left folds (instruction-level

@@ -148,11 +148,12 @@ def test_host_scan_argument_checks(lib):
 
 
 def test_options_struct_layout(lib):
-    """lscan_options: five int32 settings, one reserved int32, then the
-    carry-in pointer at byte 24 (32 bytes in all)."""
+    """lscan_options: six int32 settings (the sixth the carry-in's type),
+    then the carry-in pointer at byte 24 (32 bytes in all)."""
     import ctypes
     from paper_1604_04815_gb300 import _lib
     assert ctypes.sizeof(_lib.lscan_options) == 32
+    assert _lib.lscan_options.carry_in_type.offset == 20
     assert _lib.lscan_options.carry_in.offset == 24
 
 
