@@ -670,8 +670,10 @@ __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane
         bits = static_cast<uint32_t>(m2);
     } else {
         // the maximum is a zero: the first zero of the tile decides its sign
+        // the elements' bit patterns (an unsigned word of the element's size)
+        using Bits = std::conditional_t<sizeof(In) == 4, uint32_t, uint16_t>;
         constexpr uint32_t MAG = sizeof(In) == 4 ? 0x7fffffffu : 0x7fffu;
-        const In *e = reinterpret_cast<const In *>(tsm);
+        const Bits *e = reinterpret_cast<const Bits *>(tsm);
         bits = 0u;
         for (int base = 0; base < TILE; base += 32) {
             const uint32_t b = static_cast<uint32_t>(e[base + lane]);
@@ -1404,6 +1406,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             c[CTL_TICKET] = 0u;
             c[CTL_DONE] = 0u;
             c[CTL_EPOCH] = epoch + 1u;
+            if (p.err_host != nullptr) {
+                *reinterpret_cast<volatile uint32_t *>(p.err_host) = c[CTL_ERROR];
+                c[CTL_ERROR] = 0u;
+                __threadfence_system();
+            }
             __threadfence();
         }
     }
