@@ -302,6 +302,7 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.total_out = ls.mode == MODE_SINGLE ? ls.total_out : nullptr;
     p.values = ls.values;
     p.count_out = ls.count_out;
+    p.err_host = ls.err_host;
     void *args[] = {&p};
     cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
                                       dim3(e.threads), args, e.smem, cs);

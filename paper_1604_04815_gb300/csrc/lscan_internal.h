@@ -32,6 +32,7 @@ struct LaunchSpec {
     bool tiny = false;               // single-CTA kernel, no scratch
     const void *values = nullptr;    // stream compaction: values, count
     unsigned long long *count_out = nullptr;
+    uint32_t *err_host = nullptr;    // mapped host word for the error word
 };
 
 // Device scratch a launch uses (control block + status words).

@@ -142,24 +142,33 @@ struct Request {
 
 struct Batch {
     std::vector<Request *> reqs;
-    cudaEvent_t ev_start = nullptr, ev_done = nullptr;
+};
+
+// A batch chosen under the lock, launched after it is released.
+struct Pending {
+    int slot = -1;
+    LaunchSpec ls;
+    size_t list_bytes = 0;  // first-tile indices + descriptors to copy
+    bool empty = false;     // only empty requests: no kernel
 };
 
 struct Slot {
     cudaStream_t stream = nullptr;
     uint32_t *ctl = nullptr;
     uint64_t *status = nullptr;
-    SegDesc *d_desc = nullptr;
-    int64_t *d_first = nullptr;
-    SegDesc *h_desc = nullptr;   // pinned
-    int64_t *h_first = nullptr;  // pinned
-    uint32_t *h_err = nullptr;   // pinned copy of the batch's device error word
+    // one batch's array list: first-tile indices (n_seg + 1 int64) followed
+    // by the descriptors, filled in pinned host memory and moved to the
+    // device by ONE copy
+    uint8_t *d_list = nullptr;
+    uint8_t *h_list = nullptr;   // pinned
+    uint32_t *h_err = nullptr;   // pinned, mapped: the kernel's last CTA
+                                 // moves the batch's error word here
+    uint32_t *d_err = nullptr;   // its device address
     Batch *inflight = nullptr;
     uint64_t launches = 0;
     bool owns_stream = false;
     int lane = 0;  // which lane's requests this slot launches
     cudaEvent_t ev_start = nullptr, ev_done = nullptr;
-    cudaEvent_t ev_fin = nullptr;  // after the batch's last operation (no timing)
 };
 
 }  // namespace
@@ -273,28 +282,39 @@ void retire_locked(lscan_server *srv, int si, bool cuda_ok) {
     srv->cv_done.notify_all();
 }
 
-// Launch one batch on an idle slot.  Caller holds mu.
-bool launch_batch_locked(lscan_server *srv, int si) {
+// Choose one batch for an idle slot and fill the slot's pinned array list.
+// Caller holds mu; the CUDA calls happen later in issue_batch, outside it.
+bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd) {
     Slot &sl = srv->slots[si];
     auto &admitted = srv->admitted[sl.lane];
-    if (admitted.empty()) return false;
-    Request *head = admitted.front();
     const int64_t cap = sl.lane == 0 ? srv->bulk_cap : kMaxBatchTiles;
-    // plan with the head's kind (dummy disjoint aligned pointers, n = 1)
+    // plan with the head's kind (dummy disjoint aligned pointers, n = 1); a
+    // head whose kind is not built fails and the next one is tried
     LaunchSpec ls;
-    if (plan_scan(head->op, head->dtype, head->inclusive, reinterpret_cast<void *>(256),
-                  reinterpret_cast<void *>(4096), 1, nullptr, MODE_LIST, nullptr, 0,
-                  &ls) != LSCAN_OK) {
+    Request *head = nullptr;
+    while (!admitted.empty()) {
+        head = admitted.front();
+        if (plan_scan(head->op, head->dtype, head->inclusive, reinterpret_cast<void *>(256),
+                      reinterpret_cast<void *>(4096), 1, nullptr, MODE_LIST, nullptr, 0,
+                      &ls) == LSCAN_OK)
+            break;
         head->st.status = LSCAN_ERR_UNSUPPORTED;
         admitted.pop_front();
         finish_locked(srv, head);
         srv->cv_done.notify_all();
-        return true;
+        head = nullptr;
     }
+    if (head == nullptr) return false;
     const int tile = planned_tile(ls);
     Batch *b = new Batch();
     int64_t tiles = 0;
     bool aligned = true;
+    // the list: first-tile indices [0, n_seg] then the descriptors; both
+    // regions are written once n_seg is known (indices first, so the
+    // descriptors go to a staging area at the end and move down)
+    SegDesc *desc_tmp = reinterpret_cast<SegDesc *>(
+        sl.h_list + (kMaxBatchRequests + 1) * sizeof(int64_t));
+    int64_t *first = reinterpret_cast<int64_t *>(sl.h_list);
     for (auto it = admitted.begin(); it != admitted.end();) {
         Request *r = *it;
         if (!same_kind(r, head)) {
@@ -305,8 +325,8 @@ bool launch_batch_locked(lscan_server *srv, int si) {
         if (!b->reqs.empty() && (tiles + rt > cap ||
                                  static_cast<int64_t>(b->reqs.size()) >= kMaxBatchRequests))
             break;
-        sl.h_desc[b->reqs.size()] = SegDesc{r->x, r->y, r->n};
-        sl.h_first[b->reqs.size()] = tiles;
+        desc_tmp[b->reqs.size()] = SegDesc{r->x, r->y, r->n};
+        first[b->reqs.size()] = tiles;
         tiles += rt;
         aligned = aligned && (reinterpret_cast<uintptr_t>(r->x) % 16 == 0) &&
                   (reinterpret_cast<uintptr_t>(r->y) % 16 == 0);
@@ -314,48 +334,55 @@ bool launch_batch_locked(lscan_server *srv, int si) {
         it = admitted.erase(it);
     }
     const int64_t nseg = static_cast<int64_t>(b->reqs.size());
-    sl.h_first[nseg] = tiles;
+    first[nseg] = tiles;
+    const size_t first_b = static_cast<size_t>(nseg + 1) * sizeof(int64_t);
+    memmove(sl.h_list + first_b, desc_tmp, static_cast<size_t>(nseg) * sizeof(SegDesc));
     if (!aligned) ls.variant = 0;
     ls.mode = MODE_LIST;
-    ls.segs = sl.d_desc;
-    ls.offsets = sl.d_first;
+    ls.offsets = reinterpret_cast<const int64_t *>(sl.d_list);
+    ls.segs = sl.d_list + first_b;
     ls.n_seg = nseg;
     ls.list_tiles = tiles;
     ls.n = 0;
+    ls.err_host = sl.d_err;
+    const double t = now_us(srv->t0);
     for (Request *r : b->reqs) {
-        r->st.launch_us = now_us(srv->t0);
+        r->st.launch_us = t;
         ls.n += r->n;
     }
     sl.inflight = b;
-    if (tiles == 0) {  // only empty requests
-        cudaEventRecord(sl.ev_start, sl.stream);
-        cudaEventRecord(sl.ev_done, sl.stream);
-    } else {
-        cudaMemcpyAsync(sl.d_desc, sl.h_desc, nseg * sizeof(SegDesc), cudaMemcpyHostToDevice,
-                        sl.stream);
-        cudaMemcpyAsync(sl.d_first, sl.h_first, (nseg + 1) * sizeof(int64_t),
-                        cudaMemcpyHostToDevice, sl.stream);
-        if (++sl.launches >= (1ull << 30) - 1) {  // keep the epoch tag from wrapping
-            cudaMemsetAsync(sl.ctl, 0, CTL_WORDS * sizeof(uint32_t), sl.stream);
-            cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * srv->slot_words * sizeof(uint64_t),
-                            sl.stream);
-            sl.launches = 0;
-        }
-        cudaEventRecord(sl.ev_start, sl.stream);
-        DevBuffers db{sl.ctl, sl.status};
-        const lscan_status st = launch_scan(ls, db, sl.stream);
-        cudaEventRecord(sl.ev_done, sl.stream);
-        if (st != LSCAN_OK)
-            for (Request *r : b->reqs) r->st.status = st;
-    }
-    // the batch's error word travels with it; ev_fin marks the end of all of
-    // it and is what the scheduler polls (no blocking CUDA call is ever made
-    // under the lock)
-    cudaMemcpyAsync(sl.h_err, sl.ctl + CTL_ERROR, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                    sl.stream);
-    cudaMemsetAsync(sl.ctl + CTL_ERROR, 0, sizeof(uint32_t), sl.stream);
-    cudaEventRecord(sl.ev_fin, sl.stream);
+    pd->slot = si;
+    pd->ls = ls;
+    pd->list_bytes = first_b + static_cast<size_t>(nseg) * sizeof(SegDesc);
+    pd->empty = tiles == 0;
     return true;
+}
+
+// Launch a prepared batch: one copy of its array list, the kernel between
+// two events (the second is the one the scheduler polls).  Only the
+// scheduler thread touches a slot, so no lock is held.
+void issue_batch(lscan_server *srv, const Pending &pd) {
+    Slot &sl = srv->slots[pd.slot];
+    Batch *b = sl.inflight;
+    *reinterpret_cast<volatile uint32_t *>(sl.h_err) = 0u;
+    if (pd.empty) {  // only empty requests
+        cudaEventRecord(sl.ev_start, sl.stream);
+        cudaEventRecord(sl.ev_done, sl.stream);
+        return;
+    }
+    cudaMemcpyAsync(sl.d_list, sl.h_list, pd.list_bytes, cudaMemcpyHostToDevice, sl.stream);
+    if (++sl.launches >= (1ull << 30) - 1) {  // keep the epoch tag from wrapping
+        cudaMemsetAsync(sl.ctl, 0, CTL_WORDS * sizeof(uint32_t), sl.stream);
+        cudaMemsetAsync(sl.status, 0, kMaxBatchTiles * srv->slot_words * sizeof(uint64_t),
+                        sl.stream);
+        sl.launches = 0;
+    }
+    cudaEventRecord(sl.ev_start, sl.stream);
+    DevBuffers db{sl.ctl, sl.status};
+    const lscan_status st = launch_scan(pd.ls, db, sl.stream);
+    cudaEventRecord(sl.ev_done, sl.stream);
+    if (st != LSCAN_OK)
+        for (Request *r : b->reqs) r->st.status = st;
 }
 
 // The scheduler sleeps while no batch is in flight; otherwise it polls the
@@ -365,6 +392,7 @@ bool launch_batch_locked(lscan_server *srv, int si) {
 void scheduler_main(lscan_server *srv) {
     cudaSetDevice(srv->device);
     std::vector<std::pair<int, bool>> done;  // (slot, CUDA ok)
+    std::vector<Pending> todo;               // batches to launch
     bool busy = false;
     while (true) {
         bool kicked;
@@ -378,22 +406,31 @@ void scheduler_main(lscan_server *srv) {
         for (size_t si = 0; si < srv->slots.size(); ++si) {
             const Slot &sl = srv->slots[si];
             if (!sl.inflight) continue;
-            const cudaError_t q = cudaEventQuery(sl.ev_fin);
+            const cudaError_t q = cudaEventQuery(sl.ev_done);
             if (q != cudaErrorNotReady) done.emplace_back(static_cast<int>(si), q == cudaSuccess);
         }
         if (!kicked && done.empty()) {
             std::this_thread::yield();
             continue;
         }
-        std::lock_guard<std::mutex> lk(srv->mu);
-        for (auto &d : done) retire_locked(srv, d.first, d.second);
-        admit_locked(srv);
-        if (!srv->hold || srv->stop)
-            for (size_t si = 0; si < srv->slots.size(); ++si)
-                if (!srv->slots[si].inflight) launch_batch_locked(srv, static_cast<int>(si));
-        busy = false;
-        for (auto &sl : srv->slots) busy = busy || sl.inflight;
-        if (srv->stop && !busy && srv->admitted[0].empty() && srv->admitted[1].empty()) break;
+        todo.clear();
+        bool leave = false;
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            for (auto &d : done) retire_locked(srv, d.first, d.second);
+            admit_locked(srv);
+            if (!srv->hold || srv->stop)
+                for (size_t si = 0; si < srv->slots.size(); ++si) {
+                    if (srv->slots[si].inflight) continue;
+                    Pending pd;
+                    if (prepare_batch_locked(srv, static_cast<int>(si), &pd)) todo.push_back(pd);
+                }
+            busy = false;
+            for (auto &sl : srv->slots) busy = busy || sl.inflight;
+            leave = srv->stop && !busy && srv->admitted[0].empty() && srv->admitted[1].empty();
+        }
+        for (const Pending &pd : todo) issue_batch(srv, pd);
+        if (leave) break;
     }
 }
 
@@ -429,9 +466,9 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     const size_t ctl_b = up(CTL_WORDS * sizeof(uint32_t));
     srv->slot_words = list_slot_words();
     const size_t st_b = up(kMaxBatchTiles * srv->slot_words * sizeof(uint64_t));
-    const size_t desc_b = up(kMaxBatchRequests * sizeof(SegDesc));
-    const size_t first_b = up((kMaxBatchRequests + 1) * sizeof(int64_t));
-    const size_t slot_b = ctl_b + st_b + desc_b + first_b;
+    const size_t list_b = up((kMaxBatchRequests + 1) * sizeof(int64_t) +
+                             kMaxBatchRequests * sizeof(SegDesc));
+    const size_t slot_b = ctl_b + st_b + list_b;
     // n_streams bulk streams and one small-lane stream, two slots each
     const size_t reserve = slot_b * (n_streams + 1) * kSlotsPerStream;
     if (hbm_budget_bytes < reserve + (size_t{1} << 20)) {
@@ -459,8 +496,7 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         uint8_t *base = srv->mem + i * slot_b;
         sl.ctl = reinterpret_cast<uint32_t *>(base);
         sl.status = reinterpret_cast<uint64_t *>(base + ctl_b);
-        sl.d_desc = reinterpret_cast<SegDesc *>(base + ctl_b + st_b);
-        sl.d_first = reinterpret_cast<int64_t *>(base + ctl_b + st_b + desc_b);
+        sl.d_list = base + ctl_b + st_b;
         sl.lane = (i % n_str) == n_streams ? 1 : 0;
         if (i < n_str)
             cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking,
@@ -468,13 +504,17 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         else
             sl.stream = srv->slots[i - n_str].stream;  // shares the stream
         sl.owns_stream = i < n_str;
-        cudaMallocHost(&sl.h_desc, kMaxBatchRequests * sizeof(SegDesc));
-        cudaMallocHost(&sl.h_first, (kMaxBatchRequests + 1) * sizeof(int64_t));
-        cudaMallocHost(&sl.h_err, sizeof(uint32_t));
-        *sl.h_err = 0;
+        // the list is built in place: indices, then a staging area for the
+        // descriptors at the end (one list's worth of each)
+        cudaMallocHost(&sl.h_list, (kMaxBatchRequests + 1) * sizeof(int64_t) +
+                                       2 * kMaxBatchRequests * sizeof(SegDesc));
+        cudaHostAlloc(&sl.h_err, sizeof(uint32_t), cudaHostAllocMapped);
+        if (sl.h_err) {
+            *sl.h_err = 0;
+            cudaHostGetDevicePointer(reinterpret_cast<void **>(&sl.d_err), sl.h_err, 0);
+        }
         cudaEventCreate(&sl.ev_start);
         cudaEventCreate(&sl.ev_done);
-        cudaEventCreateWithFlags(&sl.ev_fin, cudaEventDisableTiming);
     }
     cudaEventCreate(&srv->ref_ev);
     cudaEventRecord(srv->ref_ev, srv->slots[0].stream);
@@ -507,12 +547,10 @@ void lscan_server_destroy(lscan_server *srv) {
     cudaSetDevice(srv->device);
     for (Slot &sl : srv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-        if (sl.h_desc) cudaFreeHost(sl.h_desc);
-        if (sl.h_first) cudaFreeHost(sl.h_first);
+        if (sl.h_list) cudaFreeHost(sl.h_list);
         if (sl.h_err) cudaFreeHost(sl.h_err);
         if (sl.ev_start) cudaEventDestroy(sl.ev_start);
         if (sl.ev_done) cudaEventDestroy(sl.ev_done);
-        if (sl.ev_fin) cudaEventDestroy(sl.ev_fin);
         delete sl.inflight;
     }
     for (Slot &sl : srv->slots)

@@ -73,6 +73,10 @@ struct ScanParams {
     // stream compaction (x = flags): the values, and where the count goes
     const void *values;
     unsigned long long *count_out;
+    // if set: the last CTA moves the launch's device error word here (host
+    // memory mapped for the device) and clears it, so a caller polling for
+    // completion reads it without a device-to-host copy
+    uint32_t *err_host;
 };
 
 // Single-CTA kernel for arrays of at most one tile (no inter-tile carry).
