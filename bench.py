@@ -934,12 +934,13 @@ def bench_serving(args, dev, peak, n_req, fracs, seed=6):
         base.append([r["op"], t, True, lk.data_ptr() + off * es, r["n"]])
     n_streams = getattr(args, "serving_streams", 2)
     srv = lscan.Server(budget_bytes=16 << 30, n_streams=n_streams)
-    small_max = getattr(args, "serving_small_max", 1 << 16)
-    bulk_tiles = getattr(args, "serving_bulk_tiles", 8192)
-    srv.set_lanes(small_max, bulk_tiles)
+    small_max = getattr(args, "serving_small_max", 1 << 14)
+    bulk_tiles = getattr(args, "serving_bulk_tiles", 16384)
+    reserve = getattr(args, "serving_reserve_sms", 8)
+    srv.set_lanes(small_max, bulk_tiles, reserve)
     out = {"requests": n_req, "budget_gib": 16, "n_streams": n_streams,
            "lanes": {"small_max_elems": small_max,
-                     "bulk_batch_tiles": bulk_tiles},
+                     "bulk_batch_tiles": bulk_tiles, "reserve_sms": reserve},
            "mean_elems": float(np.mean([r["n"] for r in mix]))}
     try:
         # warm-up (kernels, scratch, pool) on a short closed-loop burst
@@ -1024,11 +1025,13 @@ def main():
     ap.add_argument("--serving-loads", default="0.5,0.8,0.95",
                     help="offered loads as fractions of the saturation rate")
     ap.add_argument("--serving-streams", type=int, default=2)
-    ap.add_argument("--serving-small-max", type=int, default=1 << 16,
-                    help="largest request (elements) of the small lane; 0 = "
-                         "one lane")
-    ap.add_argument("--serving-bulk-tiles", type=int, default=8192,
+    ap.add_argument("--serving-small-max", type=int, default=1 << 14,
+                    help="largest request (elements) of the resident lane; "
+                         "0 = every request in the bulk lane")
+    ap.add_argument("--serving-bulk-tiles", type=int, default=16384,
                     help="tiles per bulk-lane batch")
+    ap.add_argument("--serving-reserve-sms", type=int, default=8,
+                    help="SMs kept for the resident lane's kernel")
     ap.add_argument("--log2n", type=int, default=28,
                     help="array size 2^k (28 = the benchmarked workload; "
                          "smaller only for profiler captures)")

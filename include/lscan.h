@@ -300,12 +300,13 @@ void lscan_graph_destroy(lscan_graph *g);
  * outputs and client buffers, so nothing is allocated while serving.
  * Requests wait in a FIFO admission queue (one per size-class lane, see
  * lscan_server_set_lanes) until the pool can hold their output; a scheduler
- * thread keeps two launch slots per stream busy (the second queued behind
+ * thread per stream keeps its two launch slots busy (the second queued behind
  * the first, so the device does not wait for the host between launches),
  * each running one persistent launch over the admitted requests of one
  * (op, dtype, inclusive) kind and lane -- up to 8192 tiles for the bulk
  * lane by default -- so kinds overlap on the device and later arrivals join
- * the next launch.  n_streams bulk streams plus one small-lane stream.
+ * the next launch.  n_streams bulk streams plus one small-lane stream, each
+ * with its own scheduler thread.
  * While batches are in flight the scheduler thread polls their completion
  * events (it sleeps when the server is idle).  Times are microseconds on the
  * host's steady clock since server creation; launch and completion times
@@ -343,10 +344,12 @@ lscan_status lscan_server_hold(lscan_server *srv, int hold);
  * the device's greatest priority, and are batched only with each other;
  * bulk batches hold at most bulk_batch_tiles tiles (default 8192, 1 ..
  * 65536), so a small batch waits at most about one capped bulk launch for
- * SM slots.  small_max_elems = 0 puts every request in the bulk lane.
- * Applies to requests submitted afterwards.  (Not in the paper.) */
+ * SM slots, and launch CTAs for (SMs - reserve_sms) SMs only (default 0,
+ * at most 64), leaving that many SMs' worth of CTA slots to small batches.
+ * small_max_elems = 0 puts every request in the bulk lane.  Applies to
+ * requests submitted afterwards.  (Not in the paper.) */
 lscan_status lscan_server_set_lanes(lscan_server *srv, int64_t small_max_elems,
-                                   int64_t bulk_batch_tiles);
+                                   int64_t bulk_batch_tiles, int32_t reserve_sms);
 /* Client buffers from the pool (count against the budget); NOMEM if full. */
 lscan_status lscan_server_alloc(lscan_server *srv, size_t bytes, void **dptr);
 lscan_status lscan_server_free(lscan_server *srv, void *dptr);

@@ -139,7 +139,7 @@ def load():
                               ctypes.POINTER(lscan_req_stats)],
         "lscan_server_release": [vp, ctypes.c_uint64],
         "lscan_server_hold": [vp, ctypes.c_int],
-        "lscan_server_set_lanes": [vp, i64, i64],
+        "lscan_server_set_lanes": [vp, i64, i64, ctypes.c_int32],
         "lscan_server_replay": [vp, ctypes.POINTER(lscan_trace_req), i64,
                                 ctypes.POINTER(lscan_req_stats),
                                 ctypes.POINTER(ctypes.c_double)],

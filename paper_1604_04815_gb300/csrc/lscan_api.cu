@@ -277,7 +277,9 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     if (st != LSCAN_OK) return st;
     const int64_t n_tiles =
         ls.mode == MODE_LIST ? ls.list_tiles : (ls.n + e.tile - 1) / e.tile;
-    int64_t grid = static_cast<int64_t>(bps) * sm_count(dev);
+    int sms = sm_count(dev) - ls.reserve_sms;
+    if (sms < 1) sms = 1;
+    int64_t grid = static_cast<int64_t>(bps) * sms;
     if (ls.max_ctas > 0 && grid > ls.max_ctas) grid = ls.max_ctas;
     if (grid > n_tiles) grid = n_tiles;
     if (grid < 1) grid = 1;

@@ -33,6 +33,7 @@ struct LaunchSpec {
     const void *values = nullptr;    // stream compaction: values, count
     unsigned long long *count_out = nullptr;
     uint32_t *err_host = nullptr;    // mapped host word for the error word
+    int reserve_sms = 0;             // launch for (SMs - reserve_sms) x CTAs/SM
 };
 
 // Device scratch a launch uses (control block + status words).

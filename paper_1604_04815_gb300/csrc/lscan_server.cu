@@ -8,18 +8,22 @@
 //    lscan_server_alloc) are carved, plus a small reserve for per-stream
 //    scratch (status words, array descriptors).  No cudaMalloc happens while
 //    serving.
-//  * Admission.  A request whose output the server must allocate waits in a
-//    FIFO queue until the pool can hold it; requests are admitted in arrival
-//    order as earlier ones release their outputs.
-//  * Continuous batching.  A scheduler thread keeps two launch slots per
-//    stream (the second batch of a stream is queued behind the first, so the
-//    GPU never waits for the host between batches).  Whenever a slot is idle
-//    it takes the oldest admitted request, gathers
-//    every admitted request of the same (op, dtype, inclusive) up to a tile
-//    budget, and issues ONE persistent MODE_LIST launch over them (each array
-//    keeps its own carry chain).  Different kinds run on different streams
-//    and overlap on the device; requests arriving while batches run are
-//    admitted and launched as slots free up.
+//  * Admission.  A request whose output the server must allocate is
+//    admitted at submission when the pool can hold its output and nothing
+//    of its lane waits before it; otherwise it waits in its lane's FIFO queue
+//    and is admitted in arrival order as earlier outputs are released.
+//  * Continuous batching.  One scheduler thread per stream keeps that
+//    stream's two launch slots busy (the second batch of a stream is queued
+//    behind the first, so the GPU never waits for the host between
+//    batches).  Whenever a slot is idle it takes the oldest admitted request
+//    of its lane, gathers every admitted request of the same (op, dtype,
+//    inclusive) up to a tile budget, and issues ONE persistent MODE_LIST
+//    launch over them (each array keeps its own carry chain).  Batches are
+//    chosen under the server lock and launched after it is released (one
+//    copy of the array list, the kernel, two events), so the streams'
+//    schedulers issue in parallel.  Different kinds run on different streams
+//    and overlap on the device; requests arriving while batches run join the
+//    next launch.
 //  * Size-class lanes.  Requests of at most small_max elements (2^16 by
 //    default) form their own lane: their own admission queue and two launch
 //    slots on a stream created at the device's greatest priority, batched
@@ -28,11 +32,13 @@
 //    about one capped bulk launch for SM slots: when a bulk kernel's
 //    persistent CTAs retire, the block scheduler dispatches the
 //    higher-priority small batch before the bulk batch queued behind it.
-//    FIFO order holds within each lane.
-//  * Completion.  The scheduler polls each in-flight slot's last event
-//    (cudaEventQuery); nothing host-side sits in the stream, so the batch
-//    queued behind it starts the moment the kernel before it ends.  Launch
-//    and completion times are read from CUDA events and mapped onto the host
+//    Bulk batches can also leave reserve_sms SMs' worth of CTA slots free
+//    (0 by default).  FIFO order holds within each lane.
+//  * Completion.  Each scheduler polls the end event of its stream's older
+//    in-flight batch (cudaEventQuery; batches on a stream finish in issue
+//    order); nothing host-side sits in the stream, so the batch queued
+//    behind it starts the moment the kernel before it ends.  Launch and
+//    completion times are read from CUDA events and mapped onto the host
 //    clock, so latencies are device-accurate.
 #include <cuda_runtime.h>
 
@@ -51,6 +57,7 @@
 #include "../../include/lscan.h"
 #include "kernel_table.h"
 #include "lscan_internal.h"
+#include "resident.h"
 #include "scan_common.h"
 
 namespace lscan {
@@ -61,9 +68,18 @@ constexpr int64_t kMaxBatchTiles = 65536;   // ~1 GiB of 16 KiB tiles per launch
 constexpr int kSlotsPerStream = 2;          // a second batch queues behind the first
 constexpr int64_t kMinTileBytes = 8192;     // smallest input tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
-constexpr int64_t kDefaultSmallMax = int64_t{1} << 16;  // elements
+constexpr int64_t kDefaultSmallMax = int64_t{1} << 14;  // elements
 constexpr int64_t kDefaultBulkCap = 8192;               // tiles per bulk batch
-constexpr int kLanes = 2;                               // 0 bulk, 1 small
+constexpr int kDefaultReserveSms = 8;                   // SMs for the resident lane
+constexpr int kResCtasPerSm = 2;                        // resident CTAs per reserved SM
+constexpr int64_t kResRing = 4096;                      // resident ring entries
+constexpr uint64_t kResIdleNs = 20000000;               // resident CTAs leave after 20 ms idle
+constexpr int kLanes = 2;                               // 0 bulk, 1 resident (small)
+// A stream whose other slot is still running forms its next batch only once
+// that batch would be worth a launch (half the tile cap) or its oldest
+// request has waited this long: the batch would queue behind the running
+// one anyway, and waiting lets it grow.
+constexpr double kQueuedBatchDelayUs = 30.0;
 
 double now_us(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0)
@@ -137,7 +153,9 @@ struct Request {
     lscan_req_stats st{};
     bool done = false;
     int64_t tag = -1;  // index in a replayed trace, -1 otherwise
-    int lane = 0;      // 0 bulk, 1 small
+    int lane = 0;      // 0 bulk, 1 resident (small)
+    int kind = -1;     // resident lane: the kernel's kind id
+    int64_t res_idx = -1;  // resident lane: its ring entry number
 };
 
 struct Batch {
@@ -189,12 +207,25 @@ struct lscan_server {
     int64_t small_max = kDefaultSmallMax;    // lane 1: n <= small_max (mu)
     int64_t bulk_cap = kDefaultBulkCap;      // tiles per lane-0 batch (mu)
     int64_t slot_words = 0;                  // status words per tile, reserved
+    // resident lane: ring and control words in host memory mapped for the
+    // device, the claim counter in device memory
+    ResReq *res_ring = nullptr;       // kResRing entries
+    uint64_t *res_ctl = nullptr;      // [0] published, [8] stop (as uint32)
+    uint64_t *res_done = nullptr;     // kResRing done words
+    unsigned long long *res_claim = nullptr;
+    uint64_t res_published = 0;       // entries written (mu)
+    cudaStream_t res_stream = nullptr;
+    cudaEvent_t res_end = nullptr;    // after the running resident kernel
+    std::vector<Request *> res_out;   // published, not yet done (resident worker)
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;     // requests, pool, slots
-    std::mutex cb_mu;  // wake-up flag only
+    std::mutex cb_mu;  // wake-up counter only
     std::condition_variable cv_sched, cv_done;
-    bool kick = false;
-    std::thread sched;
+    uint64_t kicks = 0;                // bumped by every kick (cb_mu)
+    int sleepers = 0;                  // schedulers waiting on cv_sched (cb_mu)
+    std::vector<std::thread> workers;  // one scheduler per stream
+    int n_str = 0;                     // streams (bulk + small lane)
+    int reserve_sms = kDefaultReserveSms;  // SMs kept for the resident lane (mu)
     bool stop = false;
     bool hold = false;  // admit and queue, launch nothing (mu)
     uint64_t next_id = 1;
@@ -284,10 +315,12 @@ void retire_locked(lscan_server *srv, int si, bool cuda_ok) {
 
 // Choose one batch for an idle slot and fill the slot's pinned array list.
 // Caller holds mu; the CUDA calls happen later in issue_batch, outside it.
-bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd) {
+bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd, bool queued,
+                          bool *deferred) {
     Slot &sl = srv->slots[si];
     auto &admitted = srv->admitted[sl.lane];
     const int64_t cap = sl.lane == 0 ? srv->bulk_cap : kMaxBatchTiles;
+    *deferred = false;
     // plan with the head's kind (dummy disjoint aligned pointers, n = 1); a
     // head whose kind is not built fails and the next one is tried
     LaunchSpec ls;
@@ -306,6 +339,21 @@ bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd) {
     }
     if (head == nullptr) return false;
     const int tile = planned_tile(ls);
+    if (queued) {
+        // behind a running batch: wait until this one is worth a launch
+        const double t = now_us(srv->t0);
+        if (t - head->st.admit_us < kQueuedBatchDelayUs) {
+            int64_t want = 0;
+            for (const Request *r : admitted) {
+                if (same_kind(r, head)) want += (r->n + tile - 1) / tile;
+                if (2 * want >= cap) break;
+            }
+            if (2 * want < cap) {
+                *deferred = true;
+                return false;
+            }
+        }
+    }
     Batch *b = new Batch();
     int64_t tiles = 0;
     bool aligned = true;
@@ -345,6 +393,8 @@ bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd) {
     ls.list_tiles = tiles;
     ls.n = 0;
     ls.err_host = sl.d_err;
+    // bulk batches leave CTA slots of reserve_sms SMs free for small ones
+    if (srv->small_max > 0) ls.reserve_sms = srv->reserve_sms;
     const double t = now_us(srv->t0);
     for (Request *r : b->reqs) {
         r->st.launch_us = t;
@@ -359,8 +409,8 @@ bool prepare_batch_locked(lscan_server *srv, int si, Pending *pd) {
 }
 
 // Launch a prepared batch: one copy of its array list, the kernel between
-// two events (the second is the one the scheduler polls).  Only the
-// scheduler thread touches a slot, so no lock is held.
+// two events (the second is the one the scheduler polls).  Only the slot's
+// stream scheduler touches a slot, so no lock is held.
 void issue_batch(lscan_server *srv, const Pending &pd) {
     Slot &sl = srv->slots[pd.slot];
     Batch *b = sl.inflight;
@@ -385,62 +435,216 @@ void issue_batch(lscan_server *srv, const Pending &pd) {
         for (Request *r : b->reqs) r->st.status = st;
 }
 
-// The scheduler sleeps while no batch is in flight; otherwise it polls the
-// in-flight slots' last events (only this thread launches or retires
-// batches, so it reads the slots without the lock) and takes the lock only
-// when a batch has finished or a client has kicked it.
-void scheduler_main(lscan_server *srv) {
+void kick(lscan_server *srv);
+
+// One scheduler thread per stream: it owns that stream's two launch slots
+// (the second batch queues behind the first, so the stream never waits for
+// the host between batches), sleeps while neither is in flight and its lane
+// has nothing to launch, and otherwise polls the older in-flight batch's end
+// event.  It takes the lock only to retire a batch, admit waiting requests
+// and choose the next batch; the CUDA calls are made after releasing it, so
+// the streams' schedulers issue in parallel and never block submissions.
+void worker_main(lscan_server *srv, int stream_idx) {
     cudaSetDevice(srv->device);
-    std::vector<std::pair<int, bool>> done;  // (slot, CUDA ok)
-    std::vector<Pending> todo;               // batches to launch
-    bool busy = false;
+    const int si[2] = {stream_idx, stream_idx + srv->n_str};
+    const int lane = srv->slots[si[0]].lane;
+    uint64_t seen = 0;
+    std::vector<Pending> todo;
+    std::deque<int> order;  // in-flight slots in issue order (they finish in it)
+    bool deferred = false;  // a batch was held back: look again without a kick
+    double last_look = 0.0;
     while (true) {
         bool kicked;
         {
             std::unique_lock<std::mutex> lk(srv->cb_mu);
-            if (!busy) srv->cv_sched.wait(lk, [&] { return srv->kick; });
-            kicked = srv->kick;
-            srv->kick = false;
+            if (order.empty() && srv->kicks == seen) {
+                ++srv->sleepers;
+                srv->cv_sched.wait(lk, [&] { return srv->kicks != seen; });
+                --srv->sleepers;
+            }
+            kicked = srv->kicks != seen;
+            seen = srv->kicks;
         }
-        done.clear();
-        for (size_t si = 0; si < srv->slots.size(); ++si) {
-            const Slot &sl = srv->slots[si];
-            if (!sl.inflight) continue;
-            const cudaError_t q = cudaEventQuery(sl.ev_done);
-            if (q != cudaErrorNotReady) done.emplace_back(static_cast<int>(si), q == cudaSuccess);
+        int done_slot = -1;
+        bool cuda_ok = true;
+        if (!order.empty()) {
+            const cudaError_t q = cudaEventQuery(srv->slots[order.front()].ev_done);
+            if (q != cudaErrorNotReady) {
+                done_slot = order.front();
+                cuda_ok = q == cudaSuccess;
+                order.pop_front();
+            }
         }
-        if (!kicked && done.empty()) {
+        // a held-back batch is looked at again every few microseconds
+        const bool recheck = deferred && now_us(srv->t0) - last_look > 4.0;
+        if (!kicked && done_slot < 0 && !recheck) {
             std::this_thread::yield();
             continue;
         }
+        last_look = now_us(srv->t0);
         todo.clear();
-        bool leave = false;
+        bool leave = false, more = false;
+        deferred = false;
         {
             std::lock_guard<std::mutex> lk(srv->mu);
-            for (auto &d : done) retire_locked(srv, d.first, d.second);
+            if (done_slot >= 0) retire_locked(srv, done_slot, cuda_ok);
             admit_locked(srv);
             if (!srv->hold || srv->stop)
-                for (size_t si = 0; si < srv->slots.size(); ++si) {
-                    if (srv->slots[si].inflight) continue;
+                for (int s : si) {
+                    if (srv->slots[s].inflight) continue;
                     Pending pd;
-                    if (prepare_batch_locked(srv, static_cast<int>(si), &pd)) todo.push_back(pd);
+                    bool dfr = false;
+                    const bool queued = !order.empty() || !todo.empty();
+                    if (prepare_batch_locked(srv, s, &pd, queued && !srv->stop, &dfr))
+                        todo.push_back(pd);
+                    deferred = deferred || dfr;
                 }
-            busy = false;
-            for (auto &sl : srv->slots) busy = busy || sl.inflight;
-            leave = srv->stop && !busy && srv->admitted[0].empty() && srv->admitted[1].empty();
+            leave = srv->stop && order.empty() && todo.empty() && srv->admitted[lane].empty();
+            // requests this stream did not take: wake the others only if one
+            // of them has a free slot (or the resident lane is asleep)
+            bool idle_slot = false;
+            for (const Slot &o : srv->slots) idle_slot = idle_slot || !o.inflight;
+            more = (!srv->admitted[0].empty() && idle_slot) ||
+                   (!srv->admitted[1].empty() && srv->res_out.empty());
         }
-        for (const Pending &pd : todo) issue_batch(srv, pd);
+        for (const Pending &pd : todo) {
+            issue_batch(srv, pd);
+            order.push_back(pd.slot);
+        }
+        if (more) kick(srv);
         if (leave) break;
     }
 }
 
-// Wake the scheduler (never blocks on srv->mu).
+// Release/acquire accesses of the resident lane's words in mapped host
+// memory (the device reads and writes them with .sys-scope accesses).
+void store_release(uint64_t *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
+uint64_t load_acquire(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
+
+// The resident lane's scheduler: publishes admitted small requests to the
+// ring (an entry is reused only after the request that held it is done),
+// keeps the resident kernel running while work is outstanding (it leaves by
+// itself after kResIdleNs without work; a request published as it left is
+// picked up by the next launch), and retires requests whose done word has
+// been written.  Their launch time is the publication, their completion the
+// first poll that saw the done word (host clock).
+void resident_main(lscan_server *srv) {
+    cudaSetDevice(srv->device);
+    uint64_t seen = 0;
+    bool running = false;
+    double last_query = 0.0;
+    auto &out = srv->res_out;
+    while (true) {
+        bool kicked;
+        {
+            std::unique_lock<std::mutex> lk(srv->cb_mu);
+            if (out.empty() && srv->kicks == seen) {
+                ++srv->sleepers;
+                srv->cv_sched.wait(lk, [&] { return srv->kicks != seen; });
+                --srv->sleepers;
+            }
+            kicked = srv->kicks != seen;
+            seen = srv->kicks;
+        }
+        // the kernel ended (idle): it is launched again below if needed (the
+        // driver is asked at most every 50 us)
+        const double tq = now_us(srv->t0);
+        if (running && tq - last_query > 50.0) {
+            last_query = tq;
+            if (cudaEventQuery(srv->res_end) != cudaErrorNotReady) running = false;
+        }
+        // done words need no lock (only this thread changes res_out)
+        bool any_done = false;
+        for (const Request *r : out)
+            if (load_acquire(srv->res_done + (r->res_idx % kResRing)) ==
+                static_cast<uint64_t>(r->res_idx) + 1) {
+                any_done = true;
+                break;
+            }
+        if (!kicked && !any_done && (running || out.empty())) {
+            std::this_thread::yield();
+            continue;
+        }
+        bool leave = false;
+        uint64_t published = 0;
+        size_t n_done = 0;
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            // retire
+            const double t = now_us(srv->t0);
+            for (size_t i = 0; i < out.size();) {
+                Request *r = out[i];
+                const uint64_t d = load_acquire(srv->res_done + (r->res_idx % kResRing));
+                if (d == static_cast<uint64_t>(r->res_idx) + 1) {
+                    r->st.done_us = t;
+                    r->st.batch_requests = 1;
+                    finish_locked(srv, r);
+                    out[i] = out.back();
+                    out.pop_back();
+                    ++n_done;
+                } else {
+                    ++i;
+                }
+            }
+            if (n_done) srv->cv_done.notify_all();
+            admit_locked(srv);
+            // publish
+            auto &q = srv->admitted[1];
+            while (!q.empty() && (!srv->hold || srv->stop)) {
+                const uint64_t idx = srv->res_published;
+                if (idx >= static_cast<uint64_t>(kResRing) &&
+                    load_acquire(srv->res_done + (idx % kResRing)) != idx - kResRing + 1)
+                    break;  // that entry's earlier request is still running
+                Request *r = q.front();
+                q.pop_front();
+                ResReq &e = srv->res_ring[idx % kResRing];
+                e.x = r->x;
+                e.y = r->y;
+                e.n = r->n;
+                e.kind = r->kind;
+                e.inclusive = r->inclusive;
+                r->res_idx = static_cast<int64_t>(idx);
+                r->st.launch_us = t;
+                srv->res_published = idx + 1;
+                out.push_back(r);
+            }
+            published = srv->res_published;
+            leave = srv->stop && out.empty() && srv->admitted[1].empty();
+        }
+        if (published > 0) store_release(srv->res_ctl, published);  // entries first
+        if (!out.empty() && !running) {
+            ResParams rp;
+            rp.ring = srv->res_ring;
+            rp.published = srv->res_ctl;
+            rp.stop = reinterpret_cast<const uint32_t *>(srv->res_ctl + 1);
+            rp.claim = srv->res_claim;
+            rp.done = srv->res_done;
+            rp.ring_size = kResRing;
+            rp.idle_ns = kResIdleNs;
+            int sms = 1;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, srv->device);
+            int reserve = srv->reserve_sms > 0 ? srv->reserve_sms : 1;
+            if (reserve > sms) reserve = sms;
+            if (launch_resident(rp, reserve * kResCtasPerSm, srv->res_stream) == LSCAN_OK &&
+                cudaEventRecord(srv->res_end, srv->res_stream) == cudaSuccess)
+                running = true;
+        }
+        if (leave) break;
+    }
+    // tell a still-running kernel to leave, and wait for it
+    __atomic_store_n(reinterpret_cast<uint32_t *>(srv->res_ctl + 1), 1u, __ATOMIC_RELEASE);
+    cudaStreamSynchronize(srv->res_stream);
+}
+
+// Wake every scheduler (never blocks on srv->mu).
 void kick(lscan_server *srv) {
+    bool wake;
     {
         std::lock_guard<std::mutex> lk(srv->cb_mu);
-        srv->kick = true;
+        ++srv->kicks;
+        wake = srv->sleepers > 0;  // the others poll the counter
     }
-    srv->cv_sched.notify_one();
+    if (wake) srv->cv_sched.notify_all();
 }
 
 void release_request_locked(lscan_server *srv, Request *r) {
@@ -469,8 +673,9 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     const size_t list_b = up((kMaxBatchRequests + 1) * sizeof(int64_t) +
                              kMaxBatchRequests * sizeof(SegDesc));
     const size_t slot_b = ctl_b + st_b + list_b;
-    // n_streams bulk streams and one small-lane stream, two slots each
-    const size_t reserve = slot_b * (n_streams + 1) * kSlotsPerStream;
+    // n_streams streams, two slots each; then the resident lane's claim
+    // counter
+    const size_t reserve = slot_b * n_streams * kSlotsPerStream + kPoolAlign;
     if (hbm_budget_bytes < reserve + (size_t{1} << 20)) {
         delete srv;
         return nullptr;
@@ -484,9 +689,8 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
     srv->pool = srv->mem + reserve;
     srv->pool_size = hbm_budget_bytes - reserve;
     srv->alloc.init(srv->pool_size);
-    // slots: [0, n) bulk streams, n the small-lane stream; then a second
-    // slot for each of them on the same stream
-    const int n_str = n_streams + 1;
+    // slots: [0, n) one per stream, then a second slot for each stream
+    const int n_str = n_streams;
     const int n_slots = n_str * kSlotsPerStream;
     int prio_least = 0, prio_greatest = 0;
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
@@ -497,10 +701,9 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         sl.ctl = reinterpret_cast<uint32_t *>(base);
         sl.status = reinterpret_cast<uint64_t *>(base + ctl_b);
         sl.d_list = base + ctl_b + st_b;
-        sl.lane = (i % n_str) == n_streams ? 1 : 0;
+        sl.lane = 0;
         if (i < n_str)
-            cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking,
-                                         sl.lane == 1 ? prio_greatest : prio_least);
+            cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio_least);
         else
             sl.stream = srv->slots[i - n_str].stream;  // shares the stream
         sl.owns_stream = i < n_str;
@@ -516,6 +719,16 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         cudaEventCreate(&sl.ev_start);
         cudaEventCreate(&sl.ev_done);
     }
+    // resident lane: ring, control and done words in mapped host memory
+    srv->res_claim = reinterpret_cast<unsigned long long *>(
+        srv->mem + slot_b * n_streams * kSlotsPerStream);
+    cudaHostAlloc(&srv->res_ring, kResRing * sizeof(ResReq), cudaHostAllocMapped);
+    cudaHostAlloc(&srv->res_ctl, 128, cudaHostAllocMapped);
+    cudaHostAlloc(&srv->res_done, kResRing * sizeof(uint64_t), cudaHostAllocMapped);
+    if (srv->res_ctl) memset(srv->res_ctl, 0, 128);
+    if (srv->res_done) memset(srv->res_done, 0, kResRing * sizeof(uint64_t));
+    cudaStreamCreateWithPriority(&srv->res_stream, cudaStreamNonBlocking, prio_greatest);
+    cudaEventCreateWithFlags(&srv->res_end, cudaEventDisableTiming);
     cudaEventCreate(&srv->ref_ev);
     cudaEventRecord(srv->ref_ev, srv->slots[0].stream);
     cudaEventSynchronize(srv->ref_ev);
@@ -524,7 +737,13 @@ lscan_server *lscan_server_create(size_t hbm_budget_bytes, int n_streams) {
         lscan_server_destroy(srv);
         return nullptr;
     }
-    srv->sched = std::thread(scheduler_main, srv);
+    if (!srv->res_ring || !srv->res_ctl || !srv->res_done) {
+        lscan_server_destroy(srv);
+        return nullptr;
+    }
+    srv->n_str = n_str;
+    for (int i = 0; i < n_str; ++i) srv->workers.emplace_back(worker_main, srv, i);
+    srv->workers.emplace_back(resident_main, srv);
     return srv;
 }
 
@@ -543,7 +762,8 @@ void lscan_server_destroy(lscan_server *srv) {
         }
     }
     kick(srv);
-    if (srv->sched.joinable()) srv->sched.join();
+    for (auto &w : srv->workers)
+        if (w.joinable()) w.join();
     cudaSetDevice(srv->device);
     for (Slot &sl : srv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
@@ -556,6 +776,14 @@ void lscan_server_destroy(lscan_server *srv) {
     for (Slot &sl : srv->slots)
         if (sl.owns_stream && sl.stream) cudaStreamDestroy(sl.stream);
     if (srv->ref_ev) cudaEventDestroy(srv->ref_ev);
+    if (srv->res_stream) {
+        cudaStreamSynchronize(srv->res_stream);
+        cudaStreamDestroy(srv->res_stream);
+    }
+    if (srv->res_end) cudaEventDestroy(srv->res_end);
+    if (srv->res_ring) cudaFreeHost(srv->res_ring);
+    if (srv->res_ctl) cudaFreeHost(srv->res_ctl);
+    if (srv->res_done) cudaFreeHost(srv->res_done);
     for (auto &kv : srv->reqs) delete kv.second;
     if (srv->mem) cudaFree(srv->mem);
     delete srv;
@@ -572,14 +800,15 @@ lscan_status lscan_server_hold(lscan_server *srv, int hold) {
 }
 
 lscan_status lscan_server_set_lanes(lscan_server *srv, int64_t small_max_elems,
-                                   int64_t bulk_batch_tiles) {
+                                   int64_t bulk_batch_tiles, int32_t reserve_sms) {
     if (!srv || small_max_elems < 0 || bulk_batch_tiles < 1 ||
-        bulk_batch_tiles > kMaxBatchTiles)
+        bulk_batch_tiles > kMaxBatchTiles || reserve_sms < 0 || reserve_sms > 64)
         return LSCAN_ERR_INVALID;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         srv->small_max = small_max_elems;
         srv->bulk_cap = bulk_batch_tiles;
+        srv->reserve_sms = reserve_sms;
     }
     kick(srv);
     return LSCAN_OK;
@@ -612,10 +841,10 @@ lscan_status lscan_server_free(lscan_server *srv, void *dptr) {
 // Submission.  A replayed request carries its trace index (tag >= 0) and its
 // scheduled arrival time, both set under the same lock that makes it visible
 // to the scheduler.
-static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtype,
-                                int inclusive, const void *x, void *y, int64_t n,
-                                uint64_t *ticket, int64_t tag, double arrival_us) {
-    if (!srv || !ticket || n < 0) return LSCAN_ERR_INVALID;
+// A checked request (not yet visible to the schedulers), or an error.
+static lscan_status make_request(lscan_op op, lscan_dtype dtype, int inclusive,
+                                 const void *x, void *y, int64_t n, Request **out) {
+    if (n < 0) return LSCAN_ERR_INVALID;
     if (op != LSCAN_ADD && op != LSCAN_MAX) return LSCAN_ERR_INVALID;
     const int isz = dtype_size(dtype);
     if (isz == 0) return LSCAN_ERR_INVALID;
@@ -629,6 +858,9 @@ static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtyp
         const bool disjoint = a1 <= b0 || b1 <= a0;
         if (!disjoint && !(a0 == b0 && isz == osz)) return LSCAN_ERR_INVALID;
     }
+    // one request must fit one launch's status words
+    const int64_t min_tile = kMinTileBytes / isz;  // elements
+    if ((n + min_tile - 1) / min_tile > kMaxBatchTiles) return LSCAN_ERR_INVALID;
     Request *r = new Request();
     r->op = op;
     r->dtype = dtype;
@@ -638,38 +870,61 @@ static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtyp
     r->n = n;
     r->st.n = n;
     r->st.y = y;
+    *out = r;
+    return LSCAN_OK;
+}
+
+// Makes a checked request visible: ticket, lane, admission (at once when the
+// pool has room and nothing of its lane waits before it).  Caller holds mu;
+// the caller kicks the schedulers afterwards.  On error r is deleted.
+static lscan_status enqueue_locked(lscan_server *srv, Request *r, int64_t tag,
+                                   double arrival_us, uint64_t *ticket) {
+    if (srv->stop) {
+        delete r;
+        return LSCAN_ERR_INVALID;
+    }
+    const size_t need =
+        r->y ? 0 : static_cast<size_t>(r->n) * dtype_size(out_dtype_of(r->op, r->dtype));
+    if (need > srv->pool_size) {
+        delete r;
+        return LSCAN_ERR_NOMEM;  // can never be admitted
+    }
+    r->id = srv->next_id++;
+    r->tag = tag;
+    // the resident lane takes small requests of the kinds it scans
+    int kind = -1;
+    if (r->n > 0 && r->n <= srv->small_max &&
+        resolve_kind(r->op, r->dtype, nullptr, &kind, nullptr) == LSCAN_OK &&
+        resident_kind_supported(kind)) {
+        r->lane = 1;
+        r->kind = kind;
+    }
+    r->st.submit_us = tag >= 0 ? arrival_us : now_us(srv->t0);
+    srv->reqs[r->id] = r;
+    if (r->y) {
+        r->st.admit_us = r->st.submit_us;
+        srv->admitted[r->lane].push_back(r);
+    } else {
+        srv->waiting[r->lane].push_back(r);
+        admit_locked(srv);
+    }
+    *ticket = r->id;
+    return LSCAN_OK;
+}
+
+static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtype,
+                                int inclusive, const void *x, void *y, int64_t n,
+                                uint64_t *ticket) {
+    if (!srv || !ticket) return LSCAN_ERR_INVALID;
+    Request *r = nullptr;
+    lscan_status st = make_request(op, dtype, inclusive, x, y, n, &r);
+    if (st != LSCAN_OK) return st;
     {
         std::lock_guard<std::mutex> lk(srv->mu);
-        if (srv->stop) {
-            delete r;
-            return LSCAN_ERR_INVALID;
-        }
-        const size_t need = y ? 0 : static_cast<size_t>(n) * osz;
-        // one request must fit one launch's status words
-        const int64_t min_tile = kMinTileBytes / isz;  // elements
-        if ((n + min_tile - 1) / min_tile > kMaxBatchTiles) {
-            delete r;
-            return LSCAN_ERR_INVALID;
-        }
-        if (need > srv->pool_size) {
-            delete r;
-            return LSCAN_ERR_NOMEM;  // can never be admitted
-        }
-        r->id = srv->next_id++;
-        r->tag = tag;
-        r->lane = n <= srv->small_max ? 1 : 0;
-        r->st.submit_us = tag >= 0 ? arrival_us : now_us(srv->t0);
-        srv->reqs[r->id] = r;
-        if (y) {
-            r->st.admit_us = r->st.submit_us;
-            srv->admitted[r->lane].push_back(r);
-        } else {
-            srv->waiting[r->lane].push_back(r);
-        }
-        *ticket = r->id;
+        st = enqueue_locked(srv, r, -1, 0.0, ticket);
     }
-    kick(srv);
-    return LSCAN_OK;
+    if (st == LSCAN_OK) kick(srv);
+    return st;
 }
 
 extern "C" {
@@ -677,7 +932,7 @@ extern "C" {
 lscan_status lscan_server_submit(lscan_server *srv, lscan_op op, lscan_dtype dtype,
                                  int inclusive, const void *x, void *y, int64_t n,
                                  uint64_t *ticket) {
-    return submit_impl(srv, op, dtype, inclusive, x, y, n, ticket, -1, 0.0);
+    return submit_impl(srv, op, dtype, inclusive, x, y, n, ticket);
 }
 
 static lscan_status server_get(lscan_server *srv, uint64_t ticket, lscan_req_stats *out,
@@ -728,23 +983,47 @@ lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace
     std::atomic<int64_t> n_sub{0};
     const double base = now_us(srv->t0);
     std::atomic<int> sub_err{LSCAN_OK};
-    // open-loop submitter: each request enters at its arrival time
+    // open-loop submitter: each request enters at its arrival time; the
+    // requests already due enter together, under one lock
     std::thread submitter([&] {
-        for (int64_t i = 0; i < n_req; ++i) {
+        std::vector<Request *> group;
+        int64_t i = 0;
+        while (i < n_req && sub_err.load() == LSCAN_OK) {
             const double due = base + trace[i].arrival_us;
             while (now_us(srv->t0) < due) {
                 const double left = due - now_us(srv->t0);
                 if (left > 200) std::this_thread::sleep_for(std::chrono::microseconds(100));
             }
-            uint64_t tk = 0;
-            const lscan_status st = submit_impl(
-                srv, static_cast<lscan_op>(trace[i].op), static_cast<lscan_dtype>(trace[i].dtype),
-                trace[i].inclusive, trace[i].x, nullptr, trace[i].n, &tk, i, due);
-            if (st != LSCAN_OK) {
-                sub_err.store(st);
-                break;
+            const double now = now_us(srv->t0);
+            const int64_t i0 = i;
+            group.clear();
+            for (; i < n_req && base + trace[i].arrival_us <= now; ++i) {
+                Request *r = nullptr;
+                const lscan_status st = make_request(
+                    static_cast<lscan_op>(trace[i].op), static_cast<lscan_dtype>(trace[i].dtype),
+                    trace[i].inclusive, trace[i].x, nullptr, trace[i].n, &r);
+                if (st != LSCAN_OK) {
+                    sub_err.store(st);
+                    break;
+                }
+                group.push_back(r);
             }
-            n_sub.fetch_add(1);
+            {
+                std::lock_guard<std::mutex> lk(srv->mu);
+                for (size_t g = 0; g < group.size(); ++g) {
+                    uint64_t tk = 0;
+                    const int64_t idx = i0 + static_cast<int64_t>(g);
+                    const lscan_status st =
+                        enqueue_locked(srv, group[g], idx, base + trace[idx].arrival_us, &tk);
+                    if (st != LSCAN_OK) {
+                        sub_err.store(st);
+                        for (size_t h = g + 1; h < group.size(); ++h) delete group[h];
+                        break;
+                    }
+                    n_sub.fetch_add(1);
+                }
+            }
+            kick(srv);
         }
         kick(srv);  // lets the collector see the end of submission
         srv->cv_done.notify_all();
