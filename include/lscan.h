@@ -242,10 +242,11 @@ int32_t lscan_carry_bytes(lscan_op op, lscan_dtype dtype,
  * identity for n = 0).  One pass over x (16-byte loads when x is 16-byte
  * aligned; any element-aligned x is accepted).  Per 16-byte chunk the
  * elements are folded in the scan's in-tile arithmetic and the chunks in the
- * carry arithmetic; float max keeps the first occurrence (+0 / -0).
- * Scratch (1024 partials and a done word per (device, stream)) is owned by
- * the library, allocated on first use (LSCAN_ERR_BUSY during capture) and
- * freed by lscan_shutdown.  Asynchronous on stream. */
+ * carry arithmetic; float max keeps the first occurrence (+0 / -0).  The
+ * CTAs' partials are combined through the scan's inter-block carry chain
+ * (status slots of the stream's scratch, shared with lscan_scan; a bounded
+ * wait that runs out is reported by lscan_stream_status as
+ * LSCAN_ERR_TIMEOUT).  Asynchronous on stream. */
 lscan_status lscan_reduce(lscan_op op, lscan_dtype dtype, const void *x,
                           int64_t n, const lscan_options *opts, void *d_total,
                           void *stream);

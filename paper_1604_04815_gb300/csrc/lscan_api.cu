@@ -411,6 +411,21 @@ lscan_status run_planned(const LaunchSpec &ls, void *stream) {
 
 std::mutex &api_mutex() { return g_mu; }
 
+lscan_status acquire_stream_scratch(void *stream, size_t words, DevBuffers *out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Scratch *sc = nullptr;
+    lscan_status st = get_scratch(stream, words, &sc);
+    if (st != LSCAN_OK) return st;
+    st = epoch_maintenance(sc, static_cast<cudaStream_t>(stream));
+    if (st != LSCAN_OK) return st;
+    *out = DevBuffers{sc->ctl, sc->status};
+    return LSCAN_OK;
+}
+
+uint64_t current_wait_limit_ns() { return g_wait_limit_ns.load(); }
+
+int64_t take_skip_tile() { return g_skip_tile.exchange(-1); }
+
 int planned_tile(const LaunchSpec &ls) {
     return g_kernels[ls.kind][ls.mode][ls.variant].tile;
 }
@@ -510,7 +525,6 @@ lscan_status lscan_reserve(void *stream, int64_t max_elems) {
 void lscan_shutdown(void) {
     shutdown_host_pipes();
     shutdown_radix();
-    shutdown_reduce();
     std::lock_guard<std::mutex> lk(g_mu);
     int cur = 0;
     cudaGetDevice(&cur);

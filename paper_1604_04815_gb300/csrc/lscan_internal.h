@@ -65,10 +65,15 @@ int64_t planned_tiles(const LaunchSpec &ls);
 void ensure_kernels_registered();
 
 std::mutex &api_mutex();
+// the (device, stream) scratch of the scan (grown to `words` status words,
+// epoch kept from wrapping), for other chained kernels on the stream
+lscan_status acquire_stream_scratch(void *stream, size_t words, DevBuffers *out);
+// the device wait limit, and the fault-injection tile of the next launch
+uint64_t current_wait_limit_ns();
+int64_t take_skip_tile();
 void shutdown_graphs_locked();
 void shutdown_host_pipes();  // frees the staging of lscan_scan_host
 void shutdown_radix();       // frees the counters of lscan_radix_offsets
-void shutdown_reduce();      // frees the partials of lscan_reduce
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
 // entry = configuration | carry << 8

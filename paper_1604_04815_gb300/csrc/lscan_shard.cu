@@ -36,14 +36,7 @@
 namespace lscan {
 namespace {
 
-constexpr int kReduceMaxGrid = 1024;
-
-struct ReduceScratch {
-    uint8_t *mem = nullptr;  // partials [kReduceMaxGrid] x 8 B, indices, done word
-};
-
 std::mutex g_red_mu;
-std::map<std::pair<int, void *>, ReduceScratch> g_red_scratch;
 std::map<std::pair<int, const void *>, int> g_red_bps;  // CTAs per SM
 
 // ---- host restatement of the carry operators ----------------------------
@@ -203,20 +196,6 @@ void carry_identity(CarryOp op, uint8_t *out) {
 
 }  // namespace
 
-void shutdown_reduce() {
-    std::lock_guard<std::mutex> lk(g_red_mu);
-    int cur = 0;
-    cudaGetDevice(&cur);
-    for (auto &kv : g_red_scratch) {
-        cudaSetDevice(kv.first.first);
-        cudaDeviceSynchronize();
-        if (kv.second.mem) cudaFree(kv.second.mem);
-    }
-    g_red_scratch.clear();
-    g_red_bps.clear();
-    cudaSetDevice(cur);
-}
-
 }  // namespace lscan
 
 using namespace lscan;
@@ -250,25 +229,9 @@ lscan_status lscan_reduce(lscan_op op, lscan_dtype dtype, const void *x, int64_t
     cudaStream_t cs = static_cast<cudaStream_t>(stream);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
-    ReduceScratch sc;
     int bps = 1;
     {
         std::lock_guard<std::mutex> lk(g_red_mu);
-        ReduceScratch &s = g_red_scratch[{dev, stream}];
-        if (s.mem == nullptr) {
-            cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-            if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) return LSCAN_ERR_CUDA;
-            if (cap != cudaStreamCaptureStatusNone) return LSCAN_ERR_BUSY;
-            // partials (8 B each), their element indices, the done word on
-            // its own 128-byte line
-            const size_t bytes = kReduceMaxGrid * 16 + 128;
-            if (cudaMalloc(&s.mem, bytes) != cudaSuccess) {
-                s.mem = nullptr;
-                return LSCAN_ERR_NOMEM;
-            }
-            if (cudaMemsetAsync(s.mem, 0, bytes, cs) != cudaSuccess) return LSCAN_ERR_CUDA;
-        }
-        sc = s;
         int &nb = g_red_bps[{dev, fn}];
         if (nb == 0) {
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kReduceThreads, 0) !=
@@ -281,21 +244,30 @@ lscan_status lscan_reduce(lscan_op op, lscan_dtype dtype, const void *x, int64_t
     int sms = 1;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         sms = 1;
-    const int epc = 16 / isz;
-    const int64_t per_cta = static_cast<int64_t>(kReduceThreads) * kReduceUnroll * epc;
+    // ranges: 16-byte chunks when x is aligned (elements otherwise), at least
+    // one round of in-flight loads per thread each
+    const bool aligned = reinterpret_cast<uintptr_t>(x) % 16 == 0;
+    const int64_t units = aligned ? n / (16 / isz) : n;
+    const int64_t min_units = static_cast<int64_t>(kReduceThreads) * kReduceUnroll;
     int64_t grid = static_cast<int64_t>(bps) * sms;
-    if (grid > kReduceMaxGrid) grid = kReduceMaxGrid;
-    const int64_t useful = (n + per_cta - 1) / per_cta;
+    const int64_t useful = (units + min_units - 1) / min_units;
     if (grid > useful) grid = useful;
     if (grid < 1) grid = 1;
+    const int64_t per = (units + grid - 1) / grid;
+    // the scan's per-stream scratch: control block and a status slot per CTA
+    DevBuffers db{nullptr, nullptr};
+    st = acquire_stream_scratch(stream, static_cast<size_t>(grid) * 4, &db);
+    if (st != LSCAN_OK) return st;
     ReduceParams rp;
     rp.x = x;
     rp.n = n;
-    rp.aligned = reinterpret_cast<uintptr_t>(x) % 16 == 0 ? 1 : 0;
+    rp.units_per_cta = per > 0 ? per : 1;
+    rp.aligned = aligned ? 1 : 0;
     rp.reserved = 0;
-    rp.partials = sc.mem;
-    rp.part_idx = reinterpret_cast<int64_t *>(sc.mem + kReduceMaxGrid * 8);
-    rp.done = reinterpret_cast<uint32_t *>(sc.mem + kReduceMaxGrid * 16);
+    rp.ctl = db.ctl;
+    rp.status = db.status;
+    rp.wait_limit_ns = current_wait_limit_ns();
+    rp.skip_tile = take_skip_tile();
     rp.total_out = d_total;
     void *args[] = {&rp};
     if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(kReduceThreads), args, 0,

@@ -34,28 +34,32 @@ std::mutex g_tab_mu;
 
 lscan_status load_file(const char *path);
 
-// Fastest configuration per kind at N = 2^28 on GB300 (GB/s in the
-// comments), single arrays and (first six configurations) batched scans.
-int default_variant(int kind, int mode) {
+// Fastest configuration per kind on GB300 (GB/s in the comments), single
+// arrays and (first six configurations) batched scans.  Measured at 2^28,
+// and at 2^22 .. 2^26 for the kinds whose best depends on the size: 4- and
+// 8-byte kinds take configuration 8 (32 KiB tiles of 32 items x 8 warps,
+// 64-byte status slots) from 2^22 up; bf16 takes 3-stage 32 KiB tiles
+// (11) from 2^23 up and smaller tiles below.
+int default_variant(int kind, int mode, int size_cls = 28) {
     const bool single = mode == MODE_SINGLE;
     switch (kind) {
-        case KIND_I32_ADD: return 6;              // 6155
-        case KIND_I32_MAX: return single ? 8 : 6; // 6140
-        case KIND_F32_MAX: return single ? 8 : 5; // 6084
-        case KIND_BF16_MAX: return single ? 11 : 5;  // 4415
-        case KIND_F32_ADD_PLAIN: return 6;        // 6180
-        case KIND_F32_ADD_F64: return single ? 12 : 5;
-        case KIND_F32_ADD_DF: return single ? 8 : 5;   // 5880
-        case KIND_F32_ADD_COMP: return single ? 8 : 3;
+        case KIND_I32_ADD: return single ? 8 : 6;      // 6147 (2^28), 5634 (2^26)
+        case KIND_I32_MAX: return single ? 8 : 6;      // 6140, 5634
+        case KIND_F32_MAX: return single ? 8 : 5;      // 6084, 5541
+        case KIND_BF16_MAX: return single ? (size_cls >= 25 ? 11 : 5) : 5;  // 4415
+        case KIND_F32_ADD_PLAIN: return single ? 8 : 6;  // 6175
+        case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5747
+        case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5880, 5327
+        case KIND_F32_ADD_COMP: return single ? 8 : 3;   // 4543
         case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6225
         case KIND_BF16_ADD_F64_F32: return single ? 7 : 5;
-        case KIND_BF16_ADD_DF_F32: return single ? 11 : 2;
+        case KIND_BF16_ADD_DF_F32: return single ? (size_cls >= 23 ? 11 : 13) : 2;  // 5424
         case KIND_BF16_ADD_COMP_F32: return single ? 13 : 4;
         case KIND_BF16_ADD_PLAIN_BF16: return single ? 13 : 4;
         case KIND_BF16_ADD_F64_BF16: return single ? 11 : 5;
         case KIND_BF16_ADD_DF_BF16: return single ? 11 : 5;
         case KIND_BF16_ADD_COMP_BF16: return single ? 13 : 4;
-        case KIND_I64_ADD: return single ? 8 : 5;      // 5906
+        case KIND_I64_ADD: return single ? 8 : 5;      // 5906, 5625
         case KIND_I64_MAX: return single ? 8 : 5;
         case KIND_F64_MAX: return single ? 8 : 4;
         case KIND_F64_ADD: return single ? 10 : 4;
@@ -71,7 +75,7 @@ bool variant_built(int kind, int mode, int v) {
 void fill_defaults(int (&t)[kNumKinds][MODE_COUNT][kSizeClasses]) {
     for (int k = 0; k < kNumKinds; ++k)
         for (int m = 0; m < MODE_COUNT; ++m)
-            for (int &v : t[k][m]) v = default_variant(k, m);
+            for (int c = 0; c < kSizeClasses; ++c) t[k][m][c] = default_variant(k, m, c);
 }
 
 void init_table() {
@@ -94,7 +98,7 @@ int tuned_variant(int kind, int mode, int64_t n, int *carry) {
     const int e = g_table[kind][mode][size_class(n)];
     if (carry) *carry = e >> 8;
     const int v = e & 0xff;
-    return variant_built(kind, mode, v) ? v : default_variant(kind, mode);
+    return variant_built(kind, mode, v) ? v : default_variant(kind, mode, size_class(n));
 }
 
 void set_tuned_variant(int kind, int mode, int size_cls, int entry) {
@@ -199,7 +203,7 @@ lscan_status lscan_autotune(lscan_op op, lscan_dtype dtype, int inclusive, const
     if (best == 0) return LSCAN_ERR_UNSUPPORTED;
     res.config = best;
     res.carry = best_carry;
-    res.default_config = default_variant(kind, mode);
+    res.default_config = default_variant(kind, mode, size_class(n));
     if (res.default_config >= 1 && res.default_config <= LSCAN_TUNE_MAX_CONFIGS)
         res.default_ms = res.ms_by_config[res.default_config - 1];
     // the look-back is what AUTO means already: record only a chained win
@@ -220,7 +224,7 @@ lscan_status lscan_tune_save(const char *path) {
     for (int k = 0; k < kNumKinds; ++k)
         for (int m = 0; m < MODE_COUNT; ++m)
             for (int c = 0; c < kSizeClasses; ++c)
-                if (g_table[k][m][c] != default_variant(k, m)) {
+                if (g_table[k][m][c] != default_variant(k, m, c)) {
                     std::fprintf(f, "%s[%d, %d, %d, %d, %d]", first ? "" : ", ", k, m, c,
                                  g_table[k][m][c] & 0xff, g_table[k][m][c] >> 8);
                     first = false;

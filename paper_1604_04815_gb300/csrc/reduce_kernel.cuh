@@ -9,21 +9,27 @@
 // totals as its carry-in: 3N bytes moved instead of the 4N of
 // scan-then-add.
 //
-// Precision follows the kind: each 16-byte chunk is folded in the in-tile
-// type Acc (the compensated kinds with their exact two-sum step), and the
-// chunk totals are accumulated in the carry type Car (FP64 or double-float
-// for the float adds that carry that way), so a shard total is as accurate
-// as the carry chain of a single-array scan.  Max kinds whose equal values
-// may differ in bits (float max: +0 / -0) keep the first occurrence by
-// tracking element indices, so the grouping of the reduction does not
-// matter.  The CTA partials are folded in CTA order by the CTA that
-// finishes last (a done counter; no CTA waits), which writes the total and
-// re-arms the counter.
+// Blocks: CTA c reduces a contiguous range of the array (whole 16-byte
+// chunks when x is 16-byte aligned; the ragged tail goes to the last CTA),
+// so CTA order is element order.  Within a CTA each thread folds the chunks
+// c0 + tid, c0 + tid + 256, ... (each chunk in the scan's in-tile
+// arithmetic, the kinds with an exact two-sum step included, and the chunk
+// totals in the carry type, so the total is as accurate as the carry chain
+// of a single-array scan), and the threads' partials are combined with
+// element indices deciding ties of float max (+0 / -0: the first occurrence
+// wins).  The CTAs' partials then travel through the inter-block carry
+// chain (tile_chain.cuh): every CTA publishes its partial as its tile's
+// aggregate (CTA 0 as inclusive), and the CTA that owns the last range looks
+// back for the fold of all earlier ones -- the same bounded, epoch-tagged
+// protocol as the scan, so a wait that runs out is reported on the stream
+// instead of hanging, and no clearing is needed between launches.
 #pragma once
 #include <cstdint>
 
 #include "kinds.cuh"
+#include "scan_common.h"
 #include "scan_kernel.cuh"
+#include "tile_chain.cuh"
 
 namespace lscan {
 
@@ -33,31 +39,25 @@ constexpr int kReduceUnroll = 4;  // 16-byte loads in flight per thread
 struct ReduceParams {
     const void *x;
     int64_t n;
-    int32_t aligned;     // x starts on a 16-byte boundary
+    int64_t units_per_cta;  // 16-byte chunks (aligned x) or elements per CTA
+    int32_t aligned;        // x starts on a 16-byte boundary
     int32_t reserved;
-    void *partials;      // Car[gridDim.x]
-    int64_t *part_idx;   // [gridDim.x]: element index of a max partial
-    uint32_t *done;      // CTAs finished: zero on entry and on exit
-    void *total_out;     // Car
+    uint32_t *ctl;          // control block (epoch, error, ticket, done)
+    uint64_t *status;       // a status slot per CTA
+    uint64_t wait_limit_ns;
+    int64_t skip_tile;      // fault injection: this CTA never publishes (-1 off)
+    void *total_out;        // Car
 };
 
-// Load of a word-sized value through L2 only (another CTA wrote it).
-template <class T>
-__device__ __forceinline__ T ld_cg(const T *p) {
-    static_assert(sizeof(T) % 4 == 0, "word-sized types only");
-    constexpr int W = sizeof(T) / 4;
-    uint32_t w[W];
-    const unsigned int *q = reinterpret_cast<const unsigned int *>(p);
-#pragma unroll
-    for (int i = 0; i < W; ++i) w[i] = __ldcg(q + i);
-    T r;
-    memcpy(&r, w, sizeof(T));
-    return r;
+// Status words per CTA: the carry's words, at least 2 (16-byte slots).
+template <class K>
+constexpr int reduce_slot_words() {
+    return int(sizeof(typename K::Car)) / 4 > 2 ? int(sizeof(typename K::Car)) / 4 : 2;
 }
 
 // Running total in the carry type; for tie-ordered max the index of the
 // element it came from, so that equal values keep the earliest one whatever
-// the order of combination.
+// the order of combination within the CTA.
 template <class K>
 struct RFold {
     using Car = typename K::Car;
@@ -107,46 +107,60 @@ __global__ void __launch_bounds__(kReduceThreads) lscan_reduce_kernel(const Redu
     using In = typename K::In;
     using Car = typename K::Car;
     constexpr int EPC = 16 / int(sizeof(In));
+    constexpr int SLOT = reduce_slot_words<K>();
     const In *x = static_cast<const In *>(p.x);
     const int64_t n = p.n;
-    const int64_t nchunks = p.aligned ? n / EPC : 0;
-    const int64_t gtid = static_cast<int64_t>(blockIdx.x) * kReduceThreads + threadIdx.x;
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * kReduceThreads;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t epoch = *reinterpret_cast<volatile uint32_t *>(p.ctl + CTL_EPOCH);
+    const uint32_t ebase = (epoch & kEpochMask) << 2;
+    const WaitCtx wc{p.ctl, p.wait_limit_ns, epoch};
+    const int64_t c = blockIdx.x;
+    const bool last_cta = c == gridDim.x - 1;
 
     RFold<K> f;
     f.init();
-    // whole 16-byte chunks, kReduceUnroll loads in flight per thread; each
-    // thread visits its chunks in increasing order
-    const uint4 *xv = reinterpret_cast<const uint4 *>(x);
-    for (int64_t c0 = gtid; c0 < nchunks; c0 += stride * kReduceUnroll) {
-        uint4 q[kReduceUnroll];
+    if (p.aligned) {
+        // this CTA's 16-byte chunks, kReduceUnroll loads in flight per thread
+        const int64_t nchunks = n / EPC;
+        const int64_t u0 = c * p.units_per_cta;
+        const int64_t u1 = last_cta ? nchunks : min(nchunks, u0 + p.units_per_cta);
+        const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+        for (int64_t k0 = u0 + tid; k0 < u1; k0 += kReduceThreads * kReduceUnroll) {
+            uint4 q[kReduceUnroll];
 #pragma unroll
-        for (int u = 0; u < kReduceUnroll; ++u) {
-            const int64_t c = c0 + u * stride;
-            if (c < nchunks) q[u] = __ldcs(xv + c);
-        }
+            for (int u = 0; u < kReduceUnroll; ++u) {
+                const int64_t k = k0 + u * kReduceThreads;
+                if (k < u1) q[u] = __ldcs(xv + k);
+            }
 #pragma unroll
-        for (int u = 0; u < kReduceUnroll; ++u) {
-            const int64_t c = c0 + u * stride;
-            if (c < nchunks) {
-                const uint4 qa[1] = {q[u]};
-                In e[EPC];
-                unpack_chunks<In, EPC, 1>(qa, e);
-                fold_chunk<K, EPC>(e, c * EPC, f);
+            for (int u = 0; u < kReduceUnroll; ++u) {
+                const int64_t k = k0 + u * kReduceThreads;
+                if (k < u1) {
+                    const uint4 qa[1] = {q[u]};
+                    In e[EPC];
+                    unpack_chunks<In, EPC, 1>(qa, e);
+                    fold_chunk<K, EPC>(e, k * EPC, f);
+                }
             }
         }
-    }
-    // the rest (everything when x is not 16-byte aligned), one element each
-    for (int64_t i = nchunks * EPC + gtid; i < n; i += stride) {
-        const In e[1] = {x[i]};
-        fold_chunk<K, 1>(e, i, f);
+        // the ragged tail belongs to the last range
+        if (last_cta)
+            for (int64_t i = nchunks * EPC + tid; i < n; i += kReduceThreads) {
+                const In e[1] = {x[i]};
+                fold_chunk<K, 1>(e, i, f);
+            }
+    } else {
+        const int64_t i0 = c * p.units_per_cta;
+        const int64_t i1 = last_cta ? n : min(n, i0 + p.units_per_cta);
+        for (int64_t i = i0 + tid; i < i1; i += kReduceThreads) {
+            const In e[1] = {x[i]};
+            fold_chunk<K, 1>(e, i, f);
+        }
     }
 
-    // CTA total: shuffle tree in each warp, then warp 0 over the warp totals
+    // CTA partial: shuffle tree in each warp, then warp 0 over the warp totals
     __shared__ Car wv[kReduceThreads / 32];
     __shared__ int64_t wi[kReduceThreads / 32];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
         const Car ov = shfl_down_any(f.v, off);
@@ -158,29 +172,25 @@ __global__ void __launch_bounds__(kReduceThreads) lscan_reduce_kernel(const Redu
         wi[warp] = f.i;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
         RFold<K> b;
         b.init();
-        for (int w = 0; w < kReduceThreads / 32; ++w) b.add(wv[w], wi[w]);
-        static_cast<Car *>(p.partials)[blockIdx.x] = b.v;
-        p.part_idx[blockIdx.x] = b.i;
-        __threadfence();
-        const uint32_t prev = atomicAdd(p.done, 1u);
-        last = prev == gridDim.x - 1;
+        if (lane == 0)
+            for (int w = 0; w < kReduceThreads / 32; ++w) b.add(wv[w], wi[w]);
+        const Car part = shfl_idx_any(b.v, 0);
+        // publish this range's partial (range 0: the inclusive prefix)
+        if (lane == 0 && c != p.skip_tile)
+            StatusIO<K, SLOT>::publish(p.status, c,
+                                       ebase | (c == 0 ? ST_INCLUSIVE : ST_AGGREGATE), part);
+        if (last_cta) {
+            // the fold of every earlier range, then this one (earlier first)
+            Car total = part;
+            if (c > 0) total = K::cop(lookback<K, SLOT>(p.status, wc, c, ebase, lane), part);
+            if (lane == 0) *static_cast<Car *>(p.total_out) = total;
+        }
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        // every other CTA's partial is visible (each fenced before counting);
-        // read them from L2 (ld.cg), past this SM's L1
-        __threadfence();
-        RFold<K> t;
-        t.init();
-        for (unsigned c = 0; c < gridDim.x; ++c)
-            t.add(ld_cg<Car>(static_cast<const Car *>(p.partials) + c),
-                  ld_cg<int64_t>(p.part_idx + c));
-        *static_cast<Car *>(p.total_out) = t.v;
-        *p.done = 0u;
-    }
+    if (tid == 0) (void)chain_launch_end(p.ctl, epoch);
 }
 
 }  // namespace lscan

@@ -230,9 +230,9 @@ def test_tune_table_json_roundtrip(lib, tmp_path):
     assert lib.lscan_tune_reset() == lib.LSCAN_OK
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
     assert json.loads(out.read_text())["entries"] == []
-    # defaults are per kind and mode (kind 0, int32 add, defaults to
-    # configuration 6): only entries that differ from them are saved
-    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 6], [0, 0, 27, 2]]}')
+    # defaults are per kind, mode and size (kind 0, int32 add, defaults to
+    # configuration 8): only entries that differ from them are saved
+    p.write_text('{"lscan_tune": 1, "entries": [[0, 0, 28, 8], [0, 0, 27, 2]]}')
     assert lib.lscan_tune_load(p) == lib.LSCAN_OK
     assert lib.lscan_tune_save(out) == lib.LSCAN_OK
     assert json.loads(out.read_text())["entries"] == [[0, 0, 27, 2, 0]]
