@@ -414,6 +414,29 @@ __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane
     }
 }
 
+// Two signed 16-bit maxima in one instruction (per half of the word).
+__device__ __forceinline__ uint32_t vmax_s16x2(uint32_t a, uint32_t b) {
+    uint32_t d;
+    asm("max.s16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// bf16 max scanned on packed pairs of raw bits.  Once the running maximum
+// is a positive float, the order of positive floats is the order of their
+// bits read as signed 16-bit integers, and every negative value or zero
+// reads as a smaller integer than any positive one: the running maximum of
+// the raw bits is then bit-exact (equal positive values have equal bits).
+// A pair (lo, hi) with running maximum R in both halves gives, with two
+// 16-bit SIMD maxima and two byte permutes, its inclusive outputs
+// (max(R, lo), max(R, lo, hi)) and the next R.
+template <bool INCL>
+__device__ __forceinline__ uint32_t packed_max_step(uint32_t w, uint32_t &R) {
+    const uint32_t ps = vmax_s16x2(vmax_s16x2(w, __byte_perm(w, 0u, 0x1010u)), R);
+    const uint32_t o = INCL ? ps : __byte_perm(R, ps, 0x5410u);  // (R, max(R, lo))
+    R = __byte_perm(ps, 0u, 0x3232u);
+    return o;
+}
+
 // ------------------------------------------------------------------ kernel
 template <class K, class Cfg, int MODE, bool TMA>
 __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
@@ -867,6 +890,182 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
         // then be stale) or when the previous tile's carry did not arrive or
         // came with the abort flag.
         bool stop_next = false;
+
+        // bf16 max, one array: the tile on packed pairs of raw bits
+        // (packed_max_step) -- the thread total from 16-bit SIMD maxima, the
+        // outputs from a 16-bit SIMD running maximum.  A thread whose total
+        // or base is not a positive float (a running maximum that is a zero
+        // or negative, where +0 / -0 ties keep the first zero's bits) folds
+        // its elements one by one with the kind's tie-ordered operator.
+        constexpr bool kPackedMax =
+            has_raw_max<K>::value && sizeof(In) == 2 && !SEG && !is_select<K>::value;
+        auto packed_max_tile = [&](int s, int64_t k, int64_t t, int nt, bool full_tile,
+                                   const In *tx, Out *ty) -> bool {
+            (void)t;
+            if constexpr (!kPackedMax) {
+                return false;
+            } else {
+            constexpr int NW = ITEMS / 2;  // packed words per thread
+            uint32_t w[NW];
+            if (TMA && full_tile) {
+                lds_blocked<uint32_t, NW>(smem + L::off_in + s * TILE * sizeof(In), tid, lane,
+                                          w);
+            } else {
+                const uint16_t *src =
+                    TMA ? reinterpret_cast<const uint16_t *>(smem + L::off_in +
+                                                             s * TILE * sizeof(In))
+                        : reinterpret_cast<const uint16_t *>(tx);
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    const int j = e0 + 2 * i;  // elements past the end: -inf
+                    const uint32_t lo = j < nt ? static_cast<uint32_t>(src[j]) : 0xff80u;
+                    const uint32_t hi = j + 1 < nt ? static_cast<uint32_t>(src[j + 1]) : 0xff80u;
+                    w[i] = lo | (hi << 16);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+            // element j of this thread (j a compile-time index) as a float
+            auto elem = [&](int j) -> Acc {
+                const uint32_t b = (j & 1) ? (w[j >> 1] >> 16) : (w[j >> 1] & 0xffffu);
+                return __uint_as_float(b << 16);
+            };
+
+            // ---- thread total ----
+            uint32_t m = w[0];
+#pragma unroll
+            for (int i = 1; i < NW; ++i) m = vmax_s16x2(m, w[i]);
+            const int32_t m1 =
+                max(int32_t(int16_t(m & 0xffffu)), int32_t(int16_t(m >> 16)));
+            Acc tot;
+            if (m1 > 0) {
+                tot = __uint_as_float(static_cast<uint32_t>(m1) << 16);
+            } else {
+                tot = K::ident();
+#pragma unroll
+                for (int j = 0; j < ITEMS; ++j) tot = K::op(tot, elem(j));
+            }
+
+            // ---- warp scan, block scan of warp totals (Algorithm 3) ----
+            Acc wv = tot;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const Acc ov = shfl_up_any(wv, d);
+                if (lane >= d) wv = K::op(ov, wv);
+            }
+            Acc lv = shfl_up_any(wv, 1);
+            if (lane == 0) lv = K::ident();
+            WarpTotal<Acc> *wt = wtot + (k & 1) * CW;
+            if (lane == 31) {
+                wt[warp].v = wv;
+                wt[warp].f = 0u;
+            }
+            named_bar_sync(1, CT);
+            Acc bv = lane < CW ? wt[lane].v : K::ident();
+#pragma unroll
+            for (int d = 1; d < CW; d <<= 1) {
+                const Acc ov = shfl_up_any(bv, d);
+                if (lane >= d) bv = K::op(ov, bv);
+            }
+            Acc wev = shfl_idx_any(bv, warp > 0 ? warp - 1 : 0);
+            if (warp == 0) wev = K::ident();
+            const Acc tbv = K::op(wev, lv);
+
+            // ---- carry from the carry warp (Section 4.3) ----
+            const int cslot = static_cast<int>(k % CR);
+            const bool okc = __all_sync(
+                0xffffffffu,
+                wait_phase(&carried[cslot], static_cast<uint32_t>((k / CR) & 1), wc));
+            if (!okc && lane == 0) *abort_s = 1;
+            const CarA cin = carry_s[cslot];
+            const bool stop = !okc || stop_s[cslot] != 0u;
+            const CarA B = K::base(cin, tbv);
+
+            // ---- apply carry and write y once (Section 4.4) ----
+            uint32_t o[NW];
+            if (B > 0.0f) {
+                const uint32_t bb = __float_as_uint(B) >> 16;
+                uint32_t R = bb | (bb << 16);
+                if (p.inclusive) {
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) o[i] = packed_max_step<true>(w[i], R);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) o[i] = packed_max_step<false>(w[i], R);
+                }
+            } else {
+                Acc r = B;
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    uint32_t ob[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const Acc x = elem(2 * i + h);
+                        if (p.inclusive) {
+                            r = K::op(r, x);
+                            ob[h] = f32_to_bf16_bits_exact(r);
+                        } else {
+                            ob[h] = f32_to_bf16_bits_exact(r);
+                            r = K::op(r, x);
+                        }
+                    }
+                    o[i] = ob[0] | (ob[1] << 16);
+                }
+            }
+            if (TMA && full_tile && OS == 0) {
+                constexpr int C = NW * 4 / 16;
+                uint4 ov[C];
+                pack_chunks<uint32_t, NW, C>(o, ov);
+                uint4 *dst = reinterpret_cast<uint4 *>(ty + e0);
+#pragma unroll
+                for (int j = 0; j < C; ++j) dst[j] = ov[j];
+            } else if (TMA && full_tile) {
+                constexpr int WBYTES = 32 * ITEMS * int(sizeof(Out));
+                uint8_t *region = smem + L::off_out +
+                                  (OS == 2 ? (k & 1) : 0) * (TILE * sizeof(Out)) +
+                                  warp * WBYTES;
+                if (lane == 0) {
+                    if constexpr (OS == 2) {
+                        bulk_wait_read<1>();
+                    } else {
+                        bulk_wait_read<0>();
+                    }
+                }
+                __syncwarp();
+                sts_blocked<uint32_t, NW>(region, lane, lane, o);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
+                    bulk_commit();
+                }
+            } else if (TMA && OS >= 1) {
+                // partial tile: through this warp's staging region
+                constexpr int WE = 32 * ITEMS;
+                uint8_t *rb = smem + L::off_out +
+                              (OS == 2 ? (k & 1) : 0) * (TILE * sizeof(Out)) +
+                              warp * WE * sizeof(Out);
+                if (lane == 0) bulk_wait_read<0>();
+                __syncwarp();
+#pragma unroll
+                for (int i = 0; i < NW; ++i) reinterpret_cast<uint32_t *>(rb)[lane * NW + i] = o[i];
+                __syncwarp();
+                const Out *region = reinterpret_cast<const Out *>(rb);
+                const int wbase = warp * WE;
+                const int valid = nt - wbase < WE ? nt - wbase : WE;
+                for (int j = lane; j < valid; j += 32) ty[wbase + j] = region[j];
+                __syncwarp();
+            } else {
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    if (e0 + 2 * i < nt) ty[e0 + 2 * i] = static_cast<Out>(o[i] & 0xffffu);
+                    if (e0 + 2 * i + 1 < nt) ty[e0 + 2 * i + 1] = static_cast<Out>(o[i] >> 16);
+                }
+            }
+            return stop;
+            }
+        };
+
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             const uint32_t par = static_cast<uint32_t>((k / ST) & 1);
@@ -879,6 +1078,11 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             Out *ty = slot_y[s];
             const int nt = slot_nt[s];
             const bool full_tile = nt == TILE;
+
+            if constexpr (kPackedMax) {
+                stop_next = packed_max_tile(s, k, t, nt, full_tile, tx, ty);
+                continue;
+            }
 
             // ---- load (Section 4.1 step 1) ----
             Acc v[ITEMS];
