@@ -13,13 +13,11 @@
 //    for 64-bit keys with 8-bit digits, so warps do not contend).
 //  * Merge.  Each CTA sums its copies and adds the non-zero counters to a
 //    per-stream global array with 64-bit atomics.
-//  * Scan.  The CTA that finishes last (a done counter; no CTA ever waits)
-//    scans each position's B counters, one warp per position: each lane
-//    takes ceil(B / 32) consecutive buckets and scans them serially (the row
-//    scan of Section 2.3), and a 5-round shuffle scan of the lane totals
-//    (Section 2.1, Algorithm 2) gives each lane its offset.  It writes the
-//    offsets and zeroes the global counters and the done counter, so the
-//    next launch on the stream starts clean.
+//  * Scan.  The CTA that finishes last scans each position's counters into
+//    the offsets and re-arms the scratch (finish_offsets).
+// With 8-bit digits and at least 2^20 keys the histograms come from joint
+// histograms of digit pairs instead (radix_pairs_kernel): half the shared-
+// memory atomics per key, each key read by P / 2 CTAs (once from HBM).
 // HBM traffic: the keys once (4 or 8 B per key) plus 8 B per counter.
 #include <cuda_runtime.h>
 
@@ -52,7 +50,58 @@ struct RadixParams {
     int32_t positions;           // P
     int32_t copies;              // histogram copies in shared memory
     int32_t aligned;             // keys start on a 16-byte boundary
+    int32_t groups;              // pair kernel: CTAs that read the same keys
 };
+
+// After a CTA has added its counts to p.counts: the CTA that finishes last
+// (a done counter; no CTA ever waits) scans each position's B counters, one
+// warp per position: each lane takes ceil(B / 32) consecutive buckets and
+// scans them serially (the row scan of Section 2.3), and a 5-round shuffle
+// scan of the lane totals (Section 2.1, Algorithm 2) gives each lane its
+// offset.  It writes the offsets and zeroes the global counters and the done
+// counter, so the next launch on the stream starts clean.
+template <int THREADS>
+__device__ void finish_offsets(const RadixParams &p) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int P = p.positions, B = 1 << p.digit_bits;
+    __threadfence();  // this thread's counter updates before the done count
+    __syncthreads();
+    __shared__ uint32_t is_last;
+    if (tid == 0) is_last = atomicAdd(p.done, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (is_last == 0u) return;
+    __threadfence();
+
+    const int per_lane = (B + 31) / 32;  // 1 .. 8 consecutive buckets per lane
+    for (int q = warp; q < P; q += THREADS / 32) {
+        unsigned long long c[8];
+        unsigned long long tot = 0ull;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int v = lane * per_lane + j;
+            c[j] = (j < per_lane && v < B) ? __ldcg(p.counts + q * B + v) : 0ull;
+            tot += c[j];
+        }
+        unsigned long long inc = tot;  // inclusive scan of the lane totals
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        unsigned long long run = inc - tot;  // buckets of the lanes before
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int v = lane * per_lane + j;
+            if (j < per_lane && v < B) {
+                p.offsets[q * B + v] = static_cast<int64_t>(run);
+                p.counts[q * B + v] = 0ull;
+            }
+            run += c[j];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *p.done = 0u;
+}
 
 template <class Key>
 __device__ __forceinline__ void count_key(uint32_t *h, Key k, int P, int b, int B,
@@ -62,7 +111,7 @@ __device__ __forceinline__ void count_key(uint32_t *h, Key k, int P, int b, int 
 }
 
 template <class Key>
-__global__ void __launch_bounds__(kRadixThreads) radix_offsets_kernel(const RadixParams p) {
+__global__ void __launch_bounds__(kRadixThreads, 3) radix_offsets_kernel(const RadixParams p) {
     extern __shared__ uint32_t hist[];  // copies x P x B
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b = p.digit_bits, P = p.positions, B = 1 << b;
@@ -106,44 +155,110 @@ __global__ void __launch_bounds__(kRadixThreads) radix_offsets_kernel(const Radi
         for (int c = 0; c < p.copies; ++c) s += hist[c * NB + i];
         if (s != 0u) atomicAdd(p.counts + i, static_cast<unsigned long long>(s));
     }
-    __threadfence();  // this thread's counter updates before the done count
-    __syncthreads();
-    __shared__ uint32_t is_last;
-    if (tid == 0) is_last = atomicAdd(p.done, 1u) == gridDim.x - 1 ? 1u : 0u;
-    __syncthreads();
-    if (is_last == 0u) return;
-    __threadfence();
+    finish_offsets<kRadixThreads>(p);
+}
 
-    // ---- last CTA: exclusive scan of each position's buckets ----
-    const int per_lane = (B + 31) / 32;  // 1 .. 8 consecutive buckets per lane
-    for (int q = warp; q < P; q += kRadixWarps) {
-        unsigned long long c[8];
-        unsigned long long tot = 0ull;
+// ---- joint histograms of digit pairs (8-bit digits, n >= kPairMinKeys) ----
+//
+// Four shared-memory atomics per 32-bit key (one per digit position) bound
+// the kernel above by the shared-memory atomic rate, not by HBM.  Counting
+// two adjacent 8-bit digits at once halves them: the 65536-bin histogram of
+// the 16-bit field (d_{2m+1}, d_{2m}) gives both digits' histograms as its
+// row and column sums.  Its counters are 16 bits wide, two per word (128
+// KiB per CTA, one CTA per SM), so one CTA holds one pair: the grid is made
+// of groups of G = P / 2 CTAs that read the same keys (the second read of a
+// line comes from L2) and member m of a group counts pair m.  Each 16-bit
+// half is a 15-bit count below a guard bit: the increment that takes a count
+// from 0x7fff to 0x8000 (the atomic returns the old word) clears the guard
+// again and adds 32768 to both digits' global counters, so a half never
+// carries into its neighbour and the count stays exact for any key
+// distribution (a bin needs 32768 more increments to reach the guard's
+// neighbour, far more than land while one thread clears it).
+constexpr int kPairThreads = 1024;
+constexpr int kPairWords = 32768;                       // 65536 16-bit counters
+constexpr int kPairSmem = kPairWords * 4 + 2 * 256 * 4;  // table + row/column sums
+constexpr int64_t kPairMinKeys = int64_t{1} << 20;
+
+template <class Key>
+__device__ __forceinline__ void count_pair(uint32_t *tab, Key k, int sh, int m,
+                                           unsigned long long *counts) {
+    const uint32_t bin = static_cast<uint32_t>(k >> sh) & 0xffffu;
+    const uint32_t s = (bin & 1u) * 16u;
+    const uint32_t old = atomicAdd(tab + (bin >> 1), 1u << s);
+    if (((old >> s) & 0xffffu) == 0x7fffu) {
+        // this increment set the guard bit: clear it, count 32768 globally
+        atomicAdd(tab + (bin >> 1), 0u - (0x8000u << s));
+        atomicAdd(counts + (2 * m) * 256 + (bin & 255u), 32768ull);
+        atomicAdd(counts + (2 * m + 1) * 256 + (bin >> 8), 32768ull);
+    }
+}
+
+template <class Key>
+__global__ void __launch_bounds__(kPairThreads, 1) radix_pairs_kernel(const RadixParams p) {
+    extern __shared__ uint32_t tab[];  // kPairWords, then row and column sums
+    uint32_t *srow = tab + kPairWords;     // [256] by the high digit of the pair
+    uint32_t *scol = srow + 256;           // [256] by the low digit
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i < kPairWords + 512; i += kPairThreads) tab[i] = 0u;
+    __syncthreads();
+
+    const int G = p.groups;
+    const int m = static_cast<int>(blockIdx.x) % G;    // the pair this CTA counts
+    const int64_t c = blockIdx.x / G, C = gridDim.x / G;  // key stream of the group
+    const int sh = 16 * m;
+    const Key *keys = static_cast<const Key *>(p.keys);
+    const int64_t gtid = c * kPairThreads + tid;
+    const int64_t gstride = C * kPairThreads;
+    int64_t rest = 0;
+    if (p.aligned) {
+        constexpr int EPV = 16 / int(sizeof(Key));
+        const int64_t nv = p.n / EPV;
+        const uint4 *kv = reinterpret_cast<const uint4 *>(keys);
+        for (int64_t i = gtid; i < nv; i += kRadixUnroll * gstride) {
+            uint4 q[kRadixUnroll];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int v = lane * per_lane + j;
-            c[j] = (j < per_lane && v < B) ? __ldcg(p.counts + q * B + v) : 0ull;
-            tot += c[j];
-        }
-        unsigned long long inc = tot;  // inclusive scan of the lane totals
+            for (int u = 0; u < kRadixUnroll; ++u)
+                if (i + u * gstride < nv) q[u] = kv[i + u * gstride];
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += o;
-        }
-        unsigned long long run = inc - tot;  // buckets of the lanes before
+            for (int u = 0; u < kRadixUnroll; ++u) {
+                if (i + u * gstride >= nv) break;
+                Key e[EPV];
+                memcpy(e, &q[u], 16);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int v = lane * per_lane + j;
-            if (j < per_lane && v < B) {
-                p.offsets[q * B + v] = static_cast<int64_t>(run);
-                p.counts[q * B + v] = 0ull;
+                for (int x = 0; x < EPV; ++x) count_pair<Key>(tab, e[x], sh, m, p.counts);
             }
-            run += c[j];
         }
+        rest = nv * EPV;
+    }
+    for (int64_t j = rest + gtid; j < p.n; j += gstride) count_pair<Key>(tab, keys[j], sh, m, p.counts);
+    __syncthreads();
+
+    // row sums (high digit) and column sums (low digit) of the 256 x 256
+    // table: word hi * 128 + lo / 2 holds lo even (low half) and lo odd.
+    // Thread t reads column word t % 128 of rows t / 128, t / 128 + 8, ...
+    {
+        const int cw = tid & 127;
+        uint32_t c0 = 0u, c1 = 0u;
+        for (int hi = tid >> 7; hi < 256; hi += kPairThreads / 128) {
+            const uint32_t w = tab[hi * 128 + cw];
+            c0 += w & 0xffffu;
+            c1 += w >> 16;
+            uint32_t r = (w & 0xffffu) + (w >> 16);
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) r += __shfl_down_sync(0xffffffffu, r, d);
+            if (lane == 0) atomicAdd(srow + hi, r);
+        }
+        atomicAdd(scol + 2 * cw, c0);
+        atomicAdd(scol + 2 * cw + 1, c1);
     }
     __syncthreads();
-    if (tid == 0) *p.done = 0u;
+    for (int i = tid; i < 512; i += kPairThreads) {
+        const uint32_t v = i < 256 ? scol[i] : srow[i - 256];
+        const int pos = i < 256 ? 2 * m : 2 * m + 1;
+        if (v != 0u)
+            atomicAdd(p.counts + pos * 256 + (i & 255), static_cast<unsigned long long>(v));
+    }
+    finish_offsets<kPairThreads>(p);
 }
 
 struct RadixScratch {
@@ -207,12 +322,21 @@ extern "C" lscan_status lscan_radix_offsets(const void *keys, int32_t key_bytes,
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LSCAN_ERR_CUDA;
 
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 1;
+    // 8-bit digits on a large array: joint histograms of digit pairs
+    const bool pairs = digit_bits == 8 && n >= kPairMinKeys && sms >= P / 2;
     // histogram copies: one per warp while they fit the budget
     int copies = kRadixWarps;
     while (copies > 1 && copies * NB * 4 > kRadixSmemBudget) copies /= 2;
     const int smem = copies * NB * 4;
-    const void *fn = key_bytes == 4 ? reinterpret_cast<const void *>(&radix_offsets_kernel<uint32_t>)
-                                    : reinterpret_cast<const void *>(&radix_offsets_kernel<uint64_t>);
+    const void *fn =
+        pairs ? (key_bytes == 4 ? reinterpret_cast<const void *>(&radix_pairs_kernel<uint32_t>)
+                                : reinterpret_cast<const void *>(&radix_pairs_kernel<uint64_t>))
+              : (key_bytes == 4 ? reinterpret_cast<const void *>(&radix_offsets_kernel<uint32_t>)
+                                : reinterpret_cast<const void *>(&radix_offsets_kernel<uint64_t>));
+    const int fn_smem = pairs ? kPairSmem : smem;
     RadixScratch sc;
     int bps = 1;
     {
@@ -232,32 +356,33 @@ extern "C" lscan_status lscan_radix_offsets(const void *keys, int32_t key_bytes,
             s.done = reinterpret_cast<unsigned int *>(s.counts + kRadixMaxCounters);
         }
         sc = s;
-        // the function's shared-memory limit: the budget, once per device
+        // the function's shared-memory limit, once per device
         bool &attr = g_radix_attr[{dev, fn}];
         if (!attr) {
             if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kRadixSmemBudget) != cudaSuccess)
+                                     pairs ? kPairSmem : kRadixSmemBudget) != cudaSuccess)
                 return LSCAN_ERR_CUDA;
             attr = true;
         }
-        int &nb = g_radix_bps[{{dev, fn}, smem}];
+        int &nb = g_radix_bps[{{dev, fn}, fn_smem}];
         if (nb == 0) {
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kRadixThreads, smem) !=
-                    cudaSuccess ||
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &nb, fn, pairs ? kPairThreads : kRadixThreads, fn_smem) != cudaSuccess ||
                 nb < 1)
                 nb = 1;
         }
         bps = nb;
     }
-    int sms = 1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        sms = 1;
-    // no more CTAs than there are groups of in-flight 16-byte loads
-    const int64_t per_cta = static_cast<int64_t>(kRadixThreads) * kRadixUnroll * (16 / key_bytes);
-    int64_t grid = static_cast<int64_t>(bps) * sms;
+    // no more CTAs (pair kernel: groups) than there are groups of in-flight
+    // 16-byte loads
+    const int threads = pairs ? kPairThreads : kRadixThreads;
+    const int group = pairs ? P / 2 : 1;
+    const int64_t per_cta = static_cast<int64_t>(threads) * kRadixUnroll * (16 / key_bytes);
+    int64_t streams = static_cast<int64_t>(bps) * sms / group;
     const int64_t useful = (n + per_cta - 1) / per_cta;
-    if (grid > useful) grid = useful;
-    if (grid < 1) grid = 1;
+    if (streams > useful) streams = useful;
+    if (streams < 1) streams = 1;
+    const int64_t grid = streams * group;
 
     RadixParams rp;
     rp.keys = keys;
@@ -269,8 +394,9 @@ extern "C" lscan_status lscan_radix_offsets(const void *keys, int32_t key_bytes,
     rp.positions = P;
     rp.copies = copies;
     rp.aligned = reinterpret_cast<uintptr_t>(keys) % 16 == 0 ? 1 : 0;
+    rp.groups = group;
     void *args[] = {&rp};
-    if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(kRadixThreads), args, smem,
+    if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(threads), args, fn_smem,
                          cs) != cudaSuccess)
         return LSCAN_ERR_CUDA;
     note_launch();

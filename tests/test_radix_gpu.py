@@ -118,3 +118,22 @@ def test_full_size_workload():
     from paper_1604_04815_gb300 import workloads
     k = workloads.radix_keys(N_FULL)
     assert np.array_equal(_run(k, 8), oracle.radix_offsets(k, 8))
+
+
+@pytest.mark.parametrize("kdt", [np.uint32, np.uint64], ids=["u32", "u64"])
+@pytest.mark.parametrize("kind", ["equal", "few"])
+def test_pair_histograms_with_many_guard_overflows(kdt, kind):
+    """8-bit digits on 2^24 keys take the joint digit-pair histograms; with
+    one to three distinct keys each CTA's bin passes its 15-bit count many
+    times (the guard bit is cleared and 32768 counted globally each time)."""
+    k = _keys(kdt, (1 << 24) + 3, seed=77, kind=kind)
+    assert np.array_equal(_run(k, 8), oracle.radix_offsets(k, 8))
+
+
+def test_pair_histograms_at_the_size_threshold():
+    """Just below and at 2^20 keys (the smallest array the pair kernel takes)
+    and unaligned keys there (plain loads in the pair kernel)."""
+    for i, n in enumerate([(1 << 20) - 1, 1 << 20, (1 << 20) + 1]):
+        k = _keys(np.uint32, n, seed=300 + i)
+        assert np.array_equal(_run(k, 8), oracle.radix_offsets(k, 8)), n
+        assert np.array_equal(_run(k, 8, pad_front=1), oracle.radix_offsets(k, 8)), n
