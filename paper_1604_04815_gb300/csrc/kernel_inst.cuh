@@ -104,6 +104,19 @@ struct Cfgs<1> {
     using G = TileCfg<16, 8, 6, 1, 2>;
     using C1 = TileCfg<16, 8, 6, 1, 2>;
 };
+// stream compaction with its values staged in the ring beside the flags:
+// 16384-element tiles (a quarter of the carry hops of 4096-element tiles),
+// 2 slots, 64-byte status slots, one CTA per SM (2- and 4-byte values: 80
+// KiB per slot for 4-byte values plus the 64 KiB output tile); 8-byte values
+// take 8192-element tiles to fit
+template <int VSZ>
+struct SelStagedCfg {
+    using C = TileCfg<32, 16, 2, 1, 1, 1, 1, 8>;
+};
+template <>
+struct SelStagedCfg<8> {
+    using C = TileCfg<16, 16, 2, 1, 1, 1, 1, 8>;
+};
 
 // shared memory one CTA may use (sm_100 family: 227 KiB)
 constexpr int kMaxSmemPerCta = 227 * 1024;
@@ -155,6 +168,9 @@ void fill_select(int kind) {
     using C = Cfgs<1>;
     fill_entry<K, typename C::G, MODE_SINGLE, false>(kind, 0);
     fill_entry<K, typename C::C1, MODE_SINGLE, true>(kind, 1);
+    using V = typename K::Out;
+    fill_entry<KSelectStaged<V>, typename SelStagedCfg<int(sizeof(V))>::C, MODE_SINGLE, true>(kind,
+                                                                                           2);
 }
 
 template <class K>

@@ -443,6 +443,18 @@ struct is_select : std::false_type {};
 template <class K>
 struct is_select<K, std::void_t<decltype(K::kSelect)>> : std::bool_constant<K::kSelect> {};
 
+// stream compaction whose values travel through the bulk-copy ring with the
+// flags (both arrays 16-byte aligned), instead of loads into registers
+template <class V>
+struct KSelectStaged : KSelect<V> {
+    static constexpr bool kStagedValues = true;
+};
+template <class K, class = void>
+struct is_staged_select : std::false_type {};
+template <class K>
+struct is_staged_select<K, std::void_t<decltype(K::kStagedValues)>>
+    : std::bool_constant<K::kStagedValues> {};
+
 // ------------------------------------------------- kind ids (host + device)
 enum KindId : int {
     KIND_I32_ADD = 0,

@@ -598,7 +598,12 @@ lscan_status lscan_select_flagged(lscan_dtype dtype, const void *x, const uint8_
     LaunchSpec ls;
     ls.kind = vsz == 2 ? KIND_SEL16 : vsz == 4 ? KIND_SEL32 : KIND_SEL64;
     ls.mode = MODE_SINGLE;
-    ls.variant = reinterpret_cast<uintptr_t>(flags) % 16 == 0 ? 1 : 0;
+    // flags by bulk copy when 16-byte aligned; the values too (staged in
+    // the ring) when they are as well
+    ls.variant = reinterpret_cast<uintptr_t>(flags) % 16 != 0 ? 0
+                 : reinterpret_cast<uintptr_t>(x) % 16 == 0 && g_kernels[ls.kind][MODE_SINGLE][2].fn
+                     ? 2
+                     : 1;
     const KernelEntry &e = g_kernels[ls.kind][MODE_SINGLE][ls.variant];
     if (e.fn == nullptr) return LSCAN_ERR_UNSUPPORTED;
     const int64_t n_tiles = (n + e.tile - 1) / e.tile;

@@ -94,8 +94,12 @@ struct Layout {
                                     : 0;
     static constexpr int kBits =
         MODE != MODE_SINGLE ? Cfg::STAGES * Cfg::TILE / 8 : 0;
+    // stream compaction with staged values: each slot's values
+    static constexpr int kVal =
+        is_staged_select<K>::value ? Cfg::STAGES * Cfg::TILE * int(sizeof(Out)) : 0;
     static constexpr int off_in = 0;
-    static constexpr int off_out = align_up_c(off_in + kIn, 128);
+    static constexpr int off_val = align_up_c(off_in + kIn, 128);
+    static constexpr int off_out = align_up_c(off_val + kVal, 128);
     static constexpr int off_bits = align_up_c(off_out + kOut, 128);
     // carry hand-off ring (carry warps -> consumers), deeper than the tile ring
     // so that no input slot waits for a look-back
@@ -119,7 +123,9 @@ struct Layout {
     static constexpr int bytes = align_up_c(off_abort + 16, 128);
     // every field is naturally aligned (a misaligned 8-byte shared access
     // faults the launch)
-    static_assert(off_in % 16 == 0 && off_out % 16 == 0 && off_bits % 16 == 0, "ring");
+    static_assert(off_in % 16 == 0 && off_val % 16 == 0 && off_out % 16 == 0 &&
+                      off_bits % 16 == 0,
+                  "ring");
     static_assert(off_bar % 8 == 0 && off_tile % 8 == 0 && off_tr % 8 == 0 &&
                       off_agg % 8 == 0, "8-byte");
     static_assert(off_carry % 8 == 0 && off_sx % 8 == 0 && off_snt % 4 == 0, "8-byte");
@@ -624,6 +630,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             // memory like a full tile.
             const uint32_t tbytes = static_cast<uint32_t>(nt) * uint32_t(sizeof(In));
             const uint32_t bulk_bytes = TMA ? (tbytes & ~15u) : 0u;
+            // stream compaction with staged values: the tile's values follow
+            // its flags into the slot (a bulk copy of their 16-byte prefix
+            // when the flags take one, the rest by the lanes)
+            constexpr bool SV = is_staged_select<K>::value;
+            const Out *tv = SV ? static_cast<const Out *>(p.values) + ts : nullptr;
+            const uint32_t vbulk =
+                (SV && bulk_bytes > 0u) ? (static_cast<uint32_t>(nt) * uint32_t(sizeof(Out))) & ~15u
+                                        : 0u;
             if (lane == 0) {
                 slot_x[s] = tx;
                 slot_y[s] = ty;
@@ -631,8 +645,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 if (bulk_bytes > 0u) {
                     // start the copy now; the slot's phase also needs the
                     // arrival below, made once the head bitmap is written
-                    mbar_expect_tx(&full[s], bulk_bytes);
+                    mbar_expect_tx(&full[s], bulk_bytes + vbulk);
                     bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bulk_bytes, &full[s]);
+                    if (vbulk > 0u)
+                        bulk_g2s(smem + L::off_val + s * TILE * sizeof(Out), tv, vbulk, &full[s]);
                     armed_mask |= 1u << s;
                     par_mask = (par_mask & ~(1u << s)) |
                                (static_cast<uint32_t>((k / ST) & 1) << s);
@@ -647,6 +663,14 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                         sin[i] = tx[i];
                     // these generic writes precede the slot's next bulk copy
                     fence_proxy_async_smem();
+                }
+                if constexpr (SV) {
+                    if (vbulk < static_cast<uint32_t>(nt) * uint32_t(sizeof(Out))) {
+                        Out *sv = reinterpret_cast<Out *>(smem + L::off_val + s * TILE * sizeof(Out));
+                        for (int i = static_cast<int>(vbulk / sizeof(Out)) + lane; i < nt; i += 32)
+                            sv[i] = tv[i];
+                        fence_proxy_async_smem();
+                    }
                 }
             }
             if constexpr (MODE == MODE_LIST) {
@@ -1110,13 +1134,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 const uint32_t w = bits[s * (TILE / 32) + (e0 >> 5)];
                 hb = (w >> (e0 & 31)) & (ITEMS == 32 ? 0xffffffffu : ((1u << ITEMS) - 1u));
             }
+            // (staged compaction values are read from the slot after the
+            // block scan: the slot is released then)
+            constexpr bool SV = is_staged_select<K>::value;
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+            if (!SV && lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
             // stream compaction: start loading this thread's values now, so
             // they arrive while the tile is scanned and its carry awaited
-            constexpr int SELN = is_select<K>::value ? ITEMS : 1;
+            constexpr int SELN = (is_select<K>::value && !SV) ? ITEMS : 1;
             Out selv[SELN];
-            if constexpr (is_select<K>::value) {
+            if constexpr (is_select<K>::value && !SV) {
                 const Out *xv = static_cast<const Out *>(p.values) +
                                 t * static_cast<int64_t>(TILE) + e0;
                 if (full_tile && (reinterpret_cast<uintptr_t>(p.values) & 15u) == 0u) {
@@ -1199,6 +1226,25 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             }
             const uint32_t tbf = SG ? (wef | lf) : 0u;
 
+            if constexpr (SV) {
+                // staged compaction: the in-tile index of each kept value is
+                // known (thread base + v[i] - 1), so compact the tile into the
+                // staging buffer now and free the slot before the carry wait
+                // (the previous tile's copy out of the buffer ended before
+                // this tile's vote, which every consumer thread passed)
+                Out *stg = reinterpret_cast<Out *>(smem + L::off_out);
+                Out vals[ITEMS];
+                lds_blocked<Out, ITEMS>(smem + L::off_val + s * TILE * sizeof(Out), tid, lane,
+                                        vals);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);  // slot may be refilled
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
+                    if (e0 + i < nt && kept != 0u) stg[tbv + v[i] - 1u] = vals[i];
+                }
+            }
+
             // ---- carry from the carry warp (Section 4.3) ----
             const int cslot = static_cast<int>(k % CR);
             const bool okc = __all_sync(
@@ -1219,10 +1265,12 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 static_assert(L::kOut >= TILE * int(sizeof(Out)),
                               "compaction needs a whole tile of staging");
                 Out *stg = reinterpret_cast<Out *>(smem + L::off_out);
+                if constexpr (!SV) {
 #pragma unroll
-                for (int i = 0; i < ITEMS; ++i) {
-                    const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
-                    if (e0 + i < nt && kept != 0u) stg[tbv + v[i] - 1u] = selv[i];
+                    for (int i = 0; i < ITEMS; ++i) {
+                        const Acc kept = i == 0 ? v[0] : v[i] - v[i - 1];
+                        if (e0 + i < nt && kept != 0u) stg[tbv + v[i] - 1u] = selv[i];
+                    }
                 }
                 const Acc tile_kept = shfl_idx_any(bv, CW - 1);  // block total
                 named_bar_sync(3, CT);

@@ -87,3 +87,29 @@ def test_select_torch_front():
     k = int(count.item())
     assert k == 33334
     assert torch.equal(out[:k], x[x % 3 == 0])
+
+
+@pytest.mark.parametrize("dtype", ["i32", "bf16", "i64"])
+def test_select_each_load_variant(dtype):
+    """Flags and values each 16-byte aligned or not: plain loads (flags
+    unaligned), flags by bulk copy with values loaded into registers (values
+    unaligned), and both through the bulk-copy ring (both aligned), with a
+    ragged last tile whose values are copied by the lanes."""
+    rng = np.random.default_rng(17)
+    esz = np.dtype(np.uint16 if dtype == "bf16" else
+                   np.int32 if dtype == "i32" else np.int64).itemsize
+    for n in (4096 + 5, 16384 + 5, 5 * 16384 + 13, (1 << 18) + 3):
+        x = random_array(dtype, n, rng, kind="full" if dtype != "bf16" else "signed")
+        f = _flags(n, 0.45, rng)
+        want = oracle.select_flagged(x, f)
+        for f_pad in (0, 5):
+            for x_pad in (0, 1):
+                xd = to_device(x, dtype, pad_front=x_pad)
+                assert (xd.data_ptr() % 16 == 0) == (x_pad == 0) or esz * x_pad % 16 == 0
+                fb = torch.empty(n + f_pad, dtype=torch.uint8, device="cuda")
+                fb[f_pad:] = torch.from_numpy(f)
+                yd = torch.empty_like(xd)
+                k = _run(dtype, xd, fb[f_pad:], yd, n)
+                assert k == want.shape[0], (n, f_pad, x_pad)
+                got = to_host(yd)[:k]
+                assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (n, f_pad, x_pad)
