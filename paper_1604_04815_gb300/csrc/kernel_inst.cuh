@@ -17,11 +17,12 @@ namespace lscan {
 //  - G loads straight from global memory (pointers not 16-byte aligned).
 //  - List: the bulk-copy configurations 1..N of a single-array scan; the
 //    first kMultiCfg are also built for batched (segmented, list) scans.
-//    Every list names input tiles of 8, 16, 32 or 64 KiB: ITEMS scales
+//    Every list names input tiles of 8, 16, 32, 48 or 64 KiB: ITEMS scales
 //    inversely with the element size, so a configuration number means the
 //    same bytes per tile for every type (bf16 entry 12 excepted, below).
-// Configurations whose shared memory does not fit one CTA are skipped when
-// the table is filled (their entry stays empty).
+// A kind whose shared memory does not fit one CTA with a configuration's
+// slots takes fewer of them (fill_entry); one that does not fit with two is
+// skipped when the table is filled (its entry stays empty).
 template <class... Cs>
 struct CfgList {};
 
@@ -46,7 +47,8 @@ struct Cfgs<4> {
         TileCfg<16, 8, 4, 1, 2, 1, 1, 4>,   // 13: 16 KiB, 4 stages
         TileCfg<16, 16, 2, 1, 2, 1, 2, 8>,  // 14: = 5, runs of 2 tiles
         TileCfg<32, 8, 3, 1, 1, 1, 1, 8>,   // 15: 32 KiB, 8 warps, 3 stages
-        TileCfg<8, 16, 3, 1, 2, 1, 1, 4>>;  // 16: 16 KiB, 16 warps, 3 stages
+        TileCfg<8, 16, 3, 1, 2, 1, 1, 4>,   // 16: 16 KiB, 16 warps, 3 stages
+        TileCfg<32, 12, 3, 1, 1, 1, 1, 8>>; // 17: 48 KiB, 12 warps, 3 stages
 };
 template <>
 struct Cfgs<8> {
@@ -67,13 +69,15 @@ struct Cfgs<8> {
         TileCfg<8, 8, 4, 1, 2, 1, 1, 4>,
         TileCfg<8, 16, 2, 1, 2, 1, 2, 8>,
         TileCfg<16, 8, 3, 1, 1, 1, 1, 8>,
-        TileCfg<4, 16, 3, 1, 2, 1, 1, 4>>;
+        TileCfg<4, 16, 3, 1, 2, 1, 1, 4>,
+        TileCfg<16, 12, 3, 1, 1, 1, 1, 8>>;
 };
 // bf16: twice the items for the same bytes.  Items stay <= 32 (a thread's
 // segment-head bits fit one word), so where the 4-byte entry has 32 items
 // the bf16 entry doubles the warps instead, or (entries 8, 10, 15) takes
 // the same tile bytes with another slot width or run; entry 12 (64 KiB of
-// 4-byte input) is 32 KiB of bf16 with 3 stages and runs of 2.
+// 4-byte input) is 56 KiB of bf16, the largest tile whose 28 consumer warps
+// and 3 service warps fit one 1024-thread CTA.
 template <>
 struct Cfgs<2> {
     using G = TileCfg<16, 8, 4, 1, 3>;
@@ -89,11 +93,12 @@ struct Cfgs<2> {
         TileCfg<32, 4, 4, 1, 4, 1, 1, 4>,     //  9: 8 KiB, 4 warps
         TileCfg<32, 8, 3, 1, 2, 1, 1, 8>,     // 10: 16 KiB, 64-byte slots
         TileCfg<32, 16, 3, 1, 1, 1, 1, 8>,    // 11: 32 KiB, 3 stages
-        TileCfg<32, 16, 3, 1, 1, 1, 2, 8>,    // 12: 32 KiB, 3 stages, runs of 2
+        TileCfg<32, 28, 2, 1, 1, 1, 1, 8>,    // 12: 56 KiB, 28 warps
         TileCfg<32, 8, 4, 1, 2, 1, 1, 4>,     // 13: 16 KiB, 4 stages
         TileCfg<32, 16, 2, 1, 1, 1, 2, 8>,    // 14: 32 KiB, runs of 2
         TileCfg<32, 16, 3, 1, 1, 1, 1, 16>,   // 15: 32 KiB, 3 stages, 128 B
-        TileCfg<16, 16, 3, 1, 2, 1, 1, 4>>;   // 16: 16 KiB, 16 warps
+        TileCfg<16, 16, 3, 1, 2, 1, 1, 4>,    // 16: 16 KiB, 16 warps
+        TileCfg<32, 24, 3, 1, 1, 1, 1, 8>>;   // 17: 48 KiB, 24 warps, 3 stages
 };
 // flags of a stream compaction: 4096 flags per tile, 16 per thread, whose
 // values are loaded early and held in registers (2 CTAs/SM leave room for
@@ -121,10 +126,21 @@ struct SelStagedCfg<8> {
 // shared memory one CTA may use (sm_100 family: 227 KiB)
 constexpr int kMaxSmemPerCta = 227 * 1024;
 
+// the configuration with S tile slots instead of Cfg's
+template <class Cfg, int S>
+using WithStages = TileCfg<Cfg::ITEMS, Cfg::CWARPS, S, Cfg::OSTAGES, Cfg::MINB, Cfg::NCARRY,
+                           Cfg::RUN, Cfg::SLOTW>;
+
+// A configuration names the tile; where a kind's shared memory (wider
+// output staging, e.g. bf16 in, fp32 out) does not fit one CTA with Cfg's
+// tile slots, the entry takes one slot fewer, down to two.
 template <class K, class Cfg, int MODE, bool TMA>
 void fill_entry(int kind, int variant) {
     using L = Layout<K, Cfg, MODE, TMA>;
-    if constexpr (L::bytes <= kMaxSmemPerCta) {
+    if constexpr (L::bytes > kMaxSmemPerCta) {
+        if constexpr (Cfg::STAGES > 2 && (Cfg::STAGES - 1) % Cfg::NCARRY == 0)
+            fill_entry<K, WithStages<Cfg, Cfg::STAGES - 1>, MODE, TMA>(kind, variant);
+    } else {
         KernelEntry &e = g_kernels[kind][MODE][variant];
         e.fn = reinterpret_cast<const void *>(&lscan_kernel<K, Cfg, MODE, TMA>);
         e.threads = Cfg::THREADS;

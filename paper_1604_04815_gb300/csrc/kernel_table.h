@@ -9,7 +9,7 @@ namespace lscan {
 // Variant 0 is the plain-load path for pointers that are not 16-byte
 // aligned; variants 1..kNumTmaCfg are bulk-copy (TMA) tile configurations
 // of single-array scans, of which batched scans have the first kMultiCfg.
-constexpr int kNumTmaCfg = 16;
+constexpr int kNumTmaCfg = 17;
 constexpr int kMultiCfg = 6;
 constexpr int kNumVariants = 1 + kNumTmaCfg;
 constexpr int kNumKinds = 23;

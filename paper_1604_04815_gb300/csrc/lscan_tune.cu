@@ -1,6 +1,6 @@
 // lscan_tune.cu -- tile-configuration table and the autotuner that fills it.
 //
-// Entries are (kind, mode, log2 size class) -> configuration number (1..16
+// Entries are (kind, mode, log2 size class) -> configuration number (1..17
 // for single arrays, 1..6 for batched scans; kernel_inst.cuh lists them).
 // The defaults are each kind's fastest configuration on a 2^28-element
 // array measured on GB300 (for batched modes, the fastest of the first six).
@@ -38,26 +38,29 @@ lscan_status load_file(const char *path);
 // arrays and (first six configurations) batched scans.  Measured at 2^28,
 // and at 2^22 .. 2^26 for the kinds whose best depends on the size: 4- and
 // 8-byte kinds take configuration 8 (32 KiB tiles of 32 items x 8 warps,
-// 64-byte status slots) from 2^22 up; bf16 takes 3-stage 32 KiB tiles
-// (11) from 2^23 up and smaller tiles below.
+// 64-byte status slots) from 2^22 up; bf16 takes 48 or 56 KiB tiles (17,
+// 12) from 2^25 up, 3-stage 32 KiB tiles (11) from 2^23 and smaller ones
+// below.
 int default_variant(int kind, int mode, int size_cls = 28) {
     const bool single = mode == MODE_SINGLE;
     switch (kind) {
         case KIND_I32_ADD: return single ? 8 : 6;      // 6147 (2^28), 5634 (2^26)
         case KIND_I32_MAX: return single ? 8 : 6;      // 6140, 5634
         case KIND_F32_MAX: return single ? 8 : 5;      // 6084, 5541
-        case KIND_BF16_MAX: return single ? (size_cls >= 25 ? 11 : 5) : 5;  // 4415
+        case KIND_BF16_MAX:  // 5290 (2^28)
+            return single ? (size_cls >= 25 ? 17 : size_cls >= 23 ? 11 : 5) : 5;
         case KIND_F32_ADD_PLAIN: return single ? 8 : 6;  // 6175
         case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5747
         case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5880, 5327
         case KIND_F32_ADD_COMP: return single ? 8 : 3;   // 4543
         case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6225
         case KIND_BF16_ADD_F64_F32: return single ? 7 : 5;
-        case KIND_BF16_ADD_DF_F32: return single ? (size_cls >= 23 ? 11 : 13) : 2;  // 5424
+        case KIND_BF16_ADD_DF_F32:  // 5621
+            return single ? (size_cls >= 25 ? 12 : size_cls >= 23 ? 11 : 13) : 2;
         case KIND_BF16_ADD_COMP_F32: return single ? 13 : 4;
         case KIND_BF16_ADD_PLAIN_BF16: return single ? 13 : 4;
         case KIND_BF16_ADD_F64_BF16: return single ? 11 : 5;
-        case KIND_BF16_ADD_DF_BF16: return single ? 11 : 5;
+        case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4548
         case KIND_BF16_ADD_COMP_BF16: return single ? 13 : 4;
         case KIND_I64_ADD: return single ? 8 : 5;      // 5906, 5625
         case KIND_I64_MAX: return single ? 8 : 5;

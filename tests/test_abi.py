@@ -34,8 +34,8 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(so, name), name
 
 
-# input tile bytes of configurations 1..16 (the autotuner's search space)
-TILE_KIB = [8, 16, 32, 16, 32, 32, 16, 32, 8, 16, 32, 64, 16, 32, 32, 16]
+# input tile bytes of configurations 1..17 (the autotuner's search space)
+TILE_KIB = [8, 16, 32, 16, 32, 32, 16, 32, 8, 16, 32, 64, 16, 32, 32, 16, 48]
 
 
 def test_version_and_configs(lib):
@@ -48,13 +48,15 @@ def test_version_and_configs(lib):
             assert info["tile"] == info["items"] * info["threads"]
             assert info["stages"] >= 2
     # a configuration number means the same input bytes per tile for every
-    # element size (bf16 entry 12: 32 KiB, items per thread are capped at 32)
+    # element size (bf16 entry 12: 56 KiB, items per thread are capped at 32
+    # and a CTA at 1024 threads)
+    nc = len(TILE_KIB)
     assert [lib.lscan_config_info(c, lib.LSCAN_I32)["tile"] * 4 // 1024
-            for c in range(1, 17)] == TILE_KIB
+            for c in range(1, nc + 1)] == TILE_KIB
     assert [lib.lscan_config_info(c, lib.LSCAN_I64)["tile"] * 8 // 1024
-            for c in range(1, 17)] == TILE_KIB
+            for c in range(1, nc + 1)] == TILE_KIB
     assert [lib.lscan_config_info(c, lib.LSCAN_BF16)["tile"] * 2 // 1024
-            for c in range(1, 17)] == TILE_KIB[:11] + [32] + TILE_KIB[12:]
+            for c in range(1, nc + 1)] == TILE_KIB[:11] + [56] + TILE_KIB[12:]
 
 
 def test_host_argument_checks(lib):

@@ -88,7 +88,7 @@ def _sizes(tile):
 
 
 # every tile configuration the autotuner may choose for a single array
-ALL_CONFIGS = list(range(1, 17))
+ALL_CONFIGS = list(range(1, 18))
 
 
 @pytest.mark.parametrize("config", ALL_CONFIGS)
