@@ -143,7 +143,7 @@ void fill_entry(int kind, int variant) {
     } else {
         KernelEntry &e = g_kernels[kind][MODE][variant];
         e.fn = reinterpret_cast<const void *>(&lscan_kernel<K, Cfg, MODE, TMA>);
-        e.threads = Cfg::THREADS;
+        e.threads = kernel_threads<K, Cfg, MODE, TMA>();
         e.smem = L::bytes;
         e.tile = Cfg::TILE;
         e.items = Cfg::ITEMS;

@@ -269,6 +269,11 @@ struct KFAddDF {
 template <class InT, class OutT>
 struct KFAddComp {
     static constexpr bool kTieOrdered = false;
+    // two reducer warps fold a tile's halves where one CTA runs per SM (a
+    // compensated fold per element is as much arithmetic as the consumers'
+    // scan: one reducer warp on one SM sub-partition carries twice the load
+    // of the others)
+    static constexpr bool kSplitReduce = true;
     using In = InT;
     using Out = OutT;
     using Acc = float2;
@@ -442,6 +447,12 @@ template <class K, class = void>
 struct is_select : std::false_type {};
 template <class K>
 struct is_select<K, std::void_t<decltype(K::kSelect)>> : std::bool_constant<K::kSelect> {};
+
+template <class K, class = void>
+struct has_split_reduce : std::false_type {};
+template <class K>
+struct has_split_reduce<K, std::void_t<decltype(K::kSplitReduce)>>
+    : std::bool_constant<K::kSplitReduce> {};
 
 // stream compaction whose values travel through the bulk-copy ring with the
 // flags (both arrays 16-byte aligned), instead of loads into registers

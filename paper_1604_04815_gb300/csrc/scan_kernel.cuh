@@ -81,6 +81,20 @@ struct alignas(16) WarpTotal {
     uint32_t f;
 };
 
+// Kinds whose tile aggregate two reducer warps fold (halves of a full tile
+// in shared memory; single arrays) in configurations of one CTA per SM --
+// with two CTAs per SM the second CTA's reducer already sits on another
+// sub-partition, and the hand-off costs more than it saves (measured) --
+// and the CTA's thread count.
+template <class K, class Cfg, int MODE, bool TMA>
+constexpr bool split_reduce() {
+    return has_split_reduce<K>::value && MODE == MODE_SINGLE && TMA && Cfg::MINB == 1;
+}
+template <class K, class Cfg, int MODE, bool TMA>
+constexpr int kernel_threads() {
+    return Cfg::THREADS + (split_reduce<K, Cfg, MODE, TMA>() ? 32 : 0);
+}
+
 // Shared-memory layout of one CTA.
 template <class K, class Cfg, int MODE, bool TMA>
 struct Layout {
@@ -120,7 +134,11 @@ struct Layout {
     static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
     // warp totals, double-buffered by tile parity (one barrier per tile)
     static constexpr int off_abort = off_wtot + 2 * 16 * Cfg::CWARPS;
-    static constexpr int bytes = align_up_c(off_abort + 16, 128);
+    // split reduce: the second reducer warp's half-tile totals (two, by ring
+    // use parity) and mbarriers half_done[2], half_free[2]
+    static constexpr int off_half = align_up_c(off_abort + 16, 16);
+    static constexpr int off_hbar = off_half + 2 * 16;
+    static constexpr int bytes = align_up_c(off_hbar + 4 * 8, 128);
     // every field is naturally aligned (a misaligned 8-byte shared access
     // faults the launch)
     static_assert(off_in % 16 == 0 && off_val % 16 == 0 && off_out % 16 == 0 &&
@@ -130,6 +148,8 @@ struct Layout {
                       off_agg % 8 == 0, "8-byte");
     static_assert(off_carry % 8 == 0 && off_sx % 8 == 0 && off_snt % 4 == 0, "8-byte");
     static_assert(off_wtot % 16 == 0 && off_abort % 4 == 0, "totals");
+    static_assert(off_half % 16 == 0 && off_hbar % 8 == 0 && sizeof(typename K::Acc) <= 16,
+                  "split reduce");
 };
 
 // ------------------------------------------ element <-> 16-byte chunk packs
@@ -445,7 +465,7 @@ __device__ __forceinline__ uint32_t packed_max_step(uint32_t w, uint32_t &R) {
 
 // ------------------------------------------------------------------ kernel
 template <class K, class Cfg, int MODE, bool TMA>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
+__global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB)
     lscan_kernel(const ScanParams p) {
     using In = typename K::In;
     using Out = typename K::Out;
@@ -464,6 +484,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     constexpr int CR = L::CR;
     constexpr int SLOT = status_slot_words<K, Cfg>();  // status words per tile
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
+    // split reduce: a second reducer warp after the carry warps
+    constexpr bool SPLIT = split_reduce<K, Cfg, MODE, TMA>();
+    constexpr int W_RED2 = W_CARRY + NC;
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
     // Each carry warp must see every phase of the ring entries it waits on
@@ -493,6 +516,9 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
+    Acc *half_s = reinterpret_cast<Acc *>(smem + L::off_half);         // [2]
+    uint64_t *half_done = reinterpret_cast<uint64_t *>(smem + L::off_hbar);  // [2]
+    uint64_t *half_free = half_done + 2;                                 // [2]
     const In *volatile *slot_x = reinterpret_cast<const In *volatile *>(smem + L::off_sx);
     Out *volatile *slot_y = reinterpret_cast<Out *volatile *>(smem + L::off_sy);
     volatile int32_t *slot_nt = reinterpret_cast<int32_t *>(smem + L::off_snt);
@@ -504,7 +530,7 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
     if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW + 1);  // consumer warps + reducer
+            mbar_init(&empty[s], CW + 1 + (SPLIT ? 1 : 0));  // consumer warps + reducer(s)
             tile_of[s] = INT64_MAX;
             inner_s[s] = 0;
         }
@@ -516,6 +542,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
             head_r[c] = 0;
             head0_r[c] = 0;
             stop_s[c] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&half_done[b], 1);
+            mbar_init(&half_free[b], 1);
         }
         *abort_s = 0;
         fence_mbar_init();
@@ -742,10 +772,16 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 if (armed_mask & (1u << s))
                     (void)wait_phase(&full[s], (par_mask >> s) & 1u, wc);
         }
-    } else if (warp == W_RED) {
+    } else if (warp == W_RED || (SPLIT && warp == W_RED2)) {
         // ======================= reducer warp =========================
         // Publishes each tile's aggregate as soon as its data lands, so the
         // carry of later tiles never waits on this CTA's consumer queue.
+        // Split reduce: the second reducer warp folds the second half of a
+        // full tile and hands its total to the first (half_done), which
+        // combines the halves in order and publishes; the first frees the
+        // hand-off buffer (half_free) for the use two tiles later.  Both
+        // waits are bounded like every other.
+        const bool second = SPLIT && warp == W_RED2;
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             const bool ok = wait_phase(&full[s], static_cast<uint32_t>((k / ST) & 1), wc);
@@ -796,7 +832,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     TileReduce<K> ra[EPC];
 #pragma unroll
                     for (int u = 0; u < EPC; ++u) ra[u].init();
-                    for (int c = lane; c < TILE / EPC; c += 32) {
+                    constexpr int NCH = TILE / EPC;  // 16-byte chunks
+                    const int c0 = second ? NCH / 2 : 0;
+                    const int c1 = (SPLIT && !second) ? NCH / 2 : NCH;
+                    for (int c = c0 + lane; c < c1; c += 32) {
                         const uint4 q = *reinterpret_cast<const uint4 *>(tsm + 16 * c);
                         const uint4 qa[1] = {q};
                         In e[EPC];
@@ -817,8 +856,10 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                     const In *src = TMA ? reinterpret_cast<const In *>(
                                               smem + L::off_in + s * TILE * sizeof(In))
                                         : tx;
-                    for (int i = lane; i < nt; i += 32)
-                        if (!SG || i >= start) r.add(K::load(src[i]), i);
+                    // (split reduce: a partial tile is the first warp's alone)
+                    if (!second)
+                        for (int i = lane; i < nt; i += 32)
+                            if (!SG || i >= start) r.add(K::load(src[i]), i);
                 }
             };
             if (inner) {
@@ -827,6 +868,36 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB)
                 reduce_tile(std::false_type{});
             }
             r.warp_all();
+            if constexpr (SPLIT) {
+                const int b = static_cast<int>(k & 1);
+                if (second) {
+                    // buffer b was last used two tiles ago: wait until the
+                    // first warp has taken that total
+                    bool okf = true;
+                    if (k >= 2 && lane == 0)
+                        okf = wait_phase(&half_free[b], static_cast<uint32_t>(((k - 2) >> 1) & 1), wc);
+                    okf = __shfl_sync(0xffffffffu, okf, 0);
+                    if (lane == 0) {
+                        if (!okf) *abort_s = 1;
+                        half_s[b] = r.v;
+                        mbar_arrive(&half_done[b]);
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[s]);
+                    continue;
+                }
+                bool okh = true;
+                if (lane == 0) okh = wait_phase(&half_done[b], static_cast<uint32_t>((k >> 1) & 1), wc);
+                okh = __shfl_sync(0xffffffffu, okh, 0);
+                if (lane == 0) {
+                    if (okh) {
+                        r.v = K::op(r.v, half_s[b]);  // first half, then second
+                    } else {
+                        *abort_s = 1;
+                    }
+                    mbar_arrive(&half_free[b]);
+                }
+            }
             if (lane == 0) {
                 const Car agg = K::to_car(r.v);
                 // tile 0 of a single-array scan with a carry-in publishes
