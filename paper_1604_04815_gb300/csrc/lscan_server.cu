@@ -81,6 +81,16 @@ constexpr int kLanes = 2;                               // 0 bulk, 1 resident (s
 // one anyway, and waiting lets it grow.
 constexpr double kQueuedBatchDelayUs = 30.0;
 
+// Takes m, trying for a short while before blocking: the threads on a small
+// request's path (submitters, the resident worker) would otherwise sleep in
+// the kernel for microseconds whenever another thread holds the lock for a
+// moment.  Plain try_lock polling, no processor-specific pause.
+std::unique_lock<std::mutex> spin_lock(std::mutex &m) {
+    for (int i = 0; i < 2048; ++i)
+        if (m.try_lock()) return std::unique_lock<std::mutex>(m, std::adopt_lock);
+    return std::unique_lock<std::mutex>(m);
+}
+
 double now_us(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0)
         .count();
@@ -217,6 +227,7 @@ struct lscan_server {
     cudaStream_t res_stream = nullptr;
     cudaEvent_t res_end = nullptr;    // after the running resident kernel
     std::vector<Request *> res_out;   // published, not yet done (resident worker)
+    std::vector<Request *> res_new;   // published by a submitter, not yet in res_out (mu)
     std::unordered_map<uint64_t, Request *> reqs;
     std::mutex mu;     // requests, pool, slots
     std::mutex cb_mu;  // wake-up counter only
@@ -521,13 +532,44 @@ void worker_main(lscan_server *srv, int stream_idx) {
 void store_release(uint64_t *p, uint64_t v) { __atomic_store_n(p, v, __ATOMIC_RELEASE); }
 uint64_t load_acquire(const uint64_t *p) { return __atomic_load_n(p, __ATOMIC_ACQUIRE); }
 
+// Writes admitted small requests into the resident lane's ring and makes
+// them visible to the device kernel (srv->mu held, so the published counter
+// only grows): called by the resident worker and by the submitting thread
+// itself, so that a small request reaches the device without a hand-off
+// between host threads.  The resident worker adopts them from res_new.
+void publish_resident_locked(lscan_server *srv, double t) {
+    auto &q = srv->admitted[1];
+    bool any = false;
+    while (!q.empty() && (!srv->hold || srv->stop)) {
+        const uint64_t idx = srv->res_published;
+        if (idx >= static_cast<uint64_t>(kResRing) &&
+            load_acquire(srv->res_done + (idx % kResRing)) != idx - kResRing + 1)
+            break;  // that entry's earlier request is still running
+        Request *r = q.front();
+        q.pop_front();
+        ResReq &e = srv->res_ring[idx % kResRing];
+        e.x = r->x;
+        e.y = r->y;
+        e.n = r->n;
+        e.kind = r->kind;
+        e.inclusive = r->inclusive;
+        r->res_idx = static_cast<int64_t>(idx);
+        r->st.launch_us = t;
+        srv->res_published = idx + 1;
+        srv->res_new.push_back(r);
+        any = true;
+    }
+    if (any) store_release(srv->res_ctl, srv->res_published);  // entries first
+}
+
 // The resident lane's scheduler: publishes admitted small requests to the
-// ring (an entry is reused only after the request that held it is done),
-// keeps the resident kernel running while work is outstanding (it leaves by
-// itself after kResIdleNs without work; a request published as it left is
-// picked up by the next launch), and retires requests whose done word has
-// been written.  Their launch time is the publication, their completion the
-// first poll that saw the done word (host clock).
+// ring as the submitting threads do (an entry is reused only after the
+// request that held it is done), keeps the resident kernel running while
+// work is outstanding (it leaves by itself after kResIdleNs without work; a
+// request published as it left is picked up by the next launch), and
+// retires requests whose done word has been written.  Their launch time is
+// the publication, their completion the first poll that saw the done word
+// (host clock).
 void resident_main(lscan_server *srv) {
     cudaSetDevice(srv->device);
     uint64_t seen = 0;
@@ -566,10 +608,9 @@ void resident_main(lscan_server *srv) {
             continue;
         }
         bool leave = false;
-        uint64_t published = 0;
         size_t n_done = 0;
         {
-            std::lock_guard<std::mutex> lk(srv->mu);
+            auto lk = spin_lock(srv->mu);
             // retire
             const double t = now_us(srv->t0);
             for (size_t i = 0; i < out.size();) {
@@ -588,30 +629,12 @@ void resident_main(lscan_server *srv) {
             }
             if (n_done) srv->cv_done.notify_all();
             admit_locked(srv);
-            // publish
-            auto &q = srv->admitted[1];
-            while (!q.empty() && (!srv->hold || srv->stop)) {
-                const uint64_t idx = srv->res_published;
-                if (idx >= static_cast<uint64_t>(kResRing) &&
-                    load_acquire(srv->res_done + (idx % kResRing)) != idx - kResRing + 1)
-                    break;  // that entry's earlier request is still running
-                Request *r = q.front();
-                q.pop_front();
-                ResReq &e = srv->res_ring[idx % kResRing];
-                e.x = r->x;
-                e.y = r->y;
-                e.n = r->n;
-                e.kind = r->kind;
-                e.inclusive = r->inclusive;
-                r->res_idx = static_cast<int64_t>(idx);
-                r->st.launch_us = t;
-                srv->res_published = idx + 1;
-                out.push_back(r);
-            }
-            published = srv->res_published;
+            publish_resident_locked(srv, t);
+            // take over what this thread and the submitters published
+            out.insert(out.end(), srv->res_new.begin(), srv->res_new.end());
+            srv->res_new.clear();
             leave = srv->stop && out.empty() && srv->admitted[1].empty();
         }
-        if (published > 0) store_release(srv->res_ctl, published);  // entries first
         if (!out.empty() && !running) {
             ResParams rp;
             rp.ring = srv->res_ring;
@@ -908,6 +931,9 @@ static lscan_status enqueue_locked(lscan_server *srv, Request *r, int64_t tag,
         srv->waiting[r->lane].push_back(r);
         admit_locked(srv);
     }
+    // a small request goes to the device from here (the resident worker
+    // only relaunches the kernel when it has ended, and retires requests)
+    if (r->lane == 1) publish_resident_locked(srv, now_us(srv->t0));
     *ticket = r->id;
     return LSCAN_OK;
 }
@@ -920,7 +946,7 @@ static lscan_status submit_impl(lscan_server *srv, lscan_op op, lscan_dtype dtyp
     lscan_status st = make_request(op, dtype, inclusive, x, y, n, &r);
     if (st != LSCAN_OK) return st;
     {
-        std::lock_guard<std::mutex> lk(srv->mu);
+        auto lk = spin_lock(srv->mu);
         st = enqueue_locked(srv, r, -1, 0.0, ticket);
     }
     if (st == LSCAN_OK) kick(srv);
@@ -1009,7 +1035,7 @@ lscan_status lscan_server_replay(lscan_server *srv, const lscan_trace_req *trace
                 group.push_back(r);
             }
             {
-                std::lock_guard<std::mutex> lk(srv->mu);
+                auto lk = spin_lock(srv->mu);
                 for (size_t g = 0; g < group.size(); ++g) {
                     uint64_t tk = 0;
                     const int64_t idx = i0 + static_cast<int64_t>(g);

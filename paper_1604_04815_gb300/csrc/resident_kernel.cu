@@ -3,22 +3,25 @@
 // memory mapped for the device, with no CUDA call per request.
 //
 // Not in the paper (the serving pattern of this library).  Each request is
-// scanned by ONE CTA: its elements in chunks of up to 4096, each chunk
-// staged through shared memory and scanned like the single-CTA kernel (a
-// thread-serial scan of 16 items per thread as in Section 2.3, the shuffle
-// scan of Algorithm 2 over thread totals, a block scan of warp totals as in
-// Algorithm 3), with the running total of the earlier chunks as the carry-in
-// of the next (Section 4.4 applied within one CTA).  No CTA waits on another
-// CTA.  The host publishes a request by writing its ring entry and then
-// bumping a counter (release); a CTA claims the next published entry with
-// an atomic compare-and-swap on a counter in device memory, scans it, makes
-// its output visible system-wide and writes the entry's done word (release)
-// for the host to poll.  A CTA that finds nothing to claim for idle_ns
-// leaves (bounded wait); the host launches the kernel again when it
-// publishes work and the kernel has ended.
+// scanned by ONE CTA of 512 threads: its elements in chunks of 16384 (8192
+// for 8-byte types), each chunk loaded at once (one round trip to memory),
+// staged through shared memory (one pad element per 32 elements keeps the
+// thread-blocked reads free of bank conflicts) and scanned like the
+// single-CTA kernel (a thread-serial scan of 32 or 16 items per thread as
+// in Section 2.3, the shuffle scan of Algorithm 2 over thread totals, a
+// block scan of warp totals as in Algorithm 3), with the running total of
+// the earlier chunks as the carry-in of the next (Section 4.4 applied
+// within one CTA).  No CTA waits on another CTA.  The host publishes a
+// request by writing its ring entry and then bumping a counter (release); a
+// CTA claims the next published entry with an atomic compare-and-swap on a
+// counter in device memory, scans it, makes its output visible system-wide
+// and writes the entry's done word (release) for the host to poll.  A CTA
+// that finds nothing to claim for idle_ns leaves (bounded wait); the host
+// launches the kernel again when it publishes work and the kernel has ended.
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "kinds.cuh"
 #include "lscan_internal.h"
@@ -28,9 +31,19 @@
 namespace lscan {
 namespace {
 
-constexpr int kResItems = kTinyItems;          // 16 per thread
-constexpr int kResChunk = kTinyMax;            // 4096 elements
-constexpr int kResWarps = kTinyThreads / 32;   // 8
+constexpr int kResThreads = 512;
+constexpr int kResWarps = kResThreads / 32;  // 16
+// staging (dynamic shared memory): a chunk with one pad element per 32, so
+// that thread-blocked reads (lane L reads elements 32L .. 32L + 31) fall in
+// distinct banks
+constexpr int kResChunkBytes = 66 * 1024;
+__device__ __forceinline__ int res_pad(int i) { return i + (i >> 5); }
+// elements per chunk: 16384 of up to 4 bytes (32 per thread), 8192 of 8
+template <class K>
+constexpr int res_chunk() {
+    return int(sizeof(typename K::In)) <= 4 && int(sizeof(typename K::Out)) <= 4 ? 16384 : 8192;
+}
+constexpr int kResSmem = kResChunkBytes + kResWarps * 16 + 16;
 
 __device__ __forceinline__ uint64_t ld_acquire_sys(const uint64_t *p) {
     uint64_t v;
@@ -53,16 +66,24 @@ __device__ __forceinline__ void ld_relaxed_sys_v2(const void *p, uint64_t &a, ui
                  : "memory");
 }
 
-// One request scanned by the whole CTA: chunks of up to kResChunk elements,
-// the running carry (the kind's carry type) passed from chunk to chunk.
+// One request scanned by the whole CTA: chunks of res_chunk<K>() elements
+// (one chunk for every request of the small lane with 4-byte types), each
+// loaded at once -- every thread issues all of its strided loads before the
+// chunk is scanned, so a chunk costs one round trip to memory -- and the
+// running carry (the kind's carry type) passed from chunk to chunk.
 template <class K>
-__device__ void res_scan(const void *xv, void *yv, int64_t n, int inclusive,
+__device__ __noinline__ void res_scan(const void *xv, void *yv, int64_t n, int inclusive,
                          uint8_t *buf, uint8_t *wbuf, uint8_t *cbuf) {
     using In = typename K::In;
     using Out = typename K::Out;
     using Acc = typename K::Acc;
     using Car = typename K::Car;
     using CarA = typename K::CarA;
+    constexpr int CHUNK = res_chunk<K>();
+    constexpr int ITEMS = CHUNK / kResThreads;  // 32 or 16
+    static_assert((CHUNK + CHUNK / 32) * int(sizeof(In)) <= kResChunkBytes &&
+                      (CHUNK + CHUNK / 32) * int(sizeof(Out)) <= kResChunkBytes,
+                  "chunk staging");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const In *x = static_cast<const In *>(xv);
     Out *y = static_cast<Out *>(yv);
@@ -71,38 +92,30 @@ __device__ void res_scan(const void *xv, void *yv, int64_t n, int inclusive,
     Acc *wsum = reinterpret_cast<Acc *>(wbuf);
     Car *carry = reinterpret_cast<Car *>(cbuf);
     if (tid == 0) *carry = K::cident();
-    // a chunk's loads all issued at once (a strided slice per thread); the
-    // next chunk's are in flight while the current one is scanned
-    In pre[kResItems];
-    auto fetch = [&](int64_t base) {
-        const int64_t left = n - base;
+    for (int64_t c0 = 0; c0 < n; c0 += CHUNK) {
+        const int m = static_cast<int>(n - c0 < CHUNK ? n - c0 : CHUNK);
+        In ld[ITEMS];
 #pragma unroll
-        for (int k = 0; k < kResItems; ++k) {
-            const int i = tid + k * kTinyThreads;
-            if (i < left) pre[k] = x[base + i];
+        for (int k = 0; k < ITEMS; ++k) {
+            const int i = tid + k * kResThreads;
+            if (i < m) ld[k] = x[c0 + i];
         }
-    };
-    fetch(0);
-    __syncthreads();
-    for (int64_t c0 = 0; c0 < n; c0 += kResChunk) {
-        const int m = static_cast<int>(n - c0 < kResChunk ? n - c0 : kResChunk);
 #pragma unroll
-        for (int k = 0; k < kResItems; ++k) {
-            const int i = tid + k * kTinyThreads;
-            if (i < m) sx[i] = pre[k];
+        for (int k = 0; k < ITEMS; ++k) {
+            const int i = tid + k * kResThreads;
+            if (i < m) sx[res_pad(i)] = ld[k];
         }
-        if (c0 + kResChunk < n) fetch(c0 + kResChunk);
         __syncthreads();
-        const int e0 = tid * kResItems;
-        Acc v[kResItems];
+        const int e0 = tid * ITEMS;
+        Acc v[ITEMS];
 #pragma unroll
-        for (int i = 0; i < kResItems; ++i)
-            v[i] = (e0 + i < m) ? K::load(sx[e0 + i]) : K::ident();
+        for (int i = 0; i < ITEMS; ++i)
+            v[i] = (e0 + i < m) ? K::load(sx[res_pad(e0 + i)]) : K::ident();
         const Car cin = *carry;
         __syncthreads();  // sx and the carry are reused below
 #pragma unroll
-        for (int i = 1; i < kResItems; ++i) v[i] = op_step<K>(v[i - 1], v[i]);
-        Acc wv = v[kResItems - 1];
+        for (int i = 1; i < ITEMS; ++i) v[i] = op_step<K>(v[i - 1], v[i]);
+        Acc wv = v[ITEMS - 1];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const Acc ov = shfl_up_any(wv, d);
@@ -124,24 +137,24 @@ __device__ void res_scan(const void *xv, void *yv, int64_t n, int inclusive,
         const CarA B = K::base(K::to_apply(cin), tbv);
         // the last thread's inclusive value covers the chunk (identities pad
         // it): the carry of the next chunk
-        if (tid == kTinyThreads - 1)
-            *carry = K::cop(cin, K::to_car(K::op(tbv, v[kResItems - 1])));
+        if (tid == kResThreads - 1) *carry = K::cop(cin, K::to_car(K::op(tbv, v[ITEMS - 1])));
 #pragma unroll
-        for (int i = 0; i < kResItems; ++i) {
+        for (int i = 0; i < ITEMS; ++i) {
             if (e0 + i >= m) break;
             const Acc pv = inclusive ? v[i] : (i == 0 ? K::ident() : v[i - 1]);
-            sy[e0 + i] = K::fin(B, pv);
+            sy[res_pad(e0 + i)] = K::fin(B, pv);
         }
         __syncthreads();
-        for (int i = tid; i < m; i += kTinyThreads) y[c0 + i] = sy[i];
+        for (int i = tid; i < m; i += kResThreads) y[c0 + i] = sy[res_pad(i)];
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kTinyThreads) lscan_resident_kernel(const ResParams p) {
-    __shared__ __align__(16) uint8_t buf[kResChunk * 8];
-    __shared__ __align__(16) uint8_t wbuf[kResWarps * 16];
-    __shared__ __align__(16) uint8_t cbuf[16];
+__global__ void __launch_bounds__(kResThreads, 2) lscan_resident_kernel(const ResParams p) {
+    extern __shared__ __align__(16) uint8_t res_smem[];  // kResSmem bytes
+    uint8_t *buf = res_smem;                        // chunk staging
+    uint8_t *wbuf = res_smem + kResChunkBytes;      // warp totals
+    uint8_t *cbuf = wbuf + kResWarps * 16;          // running carry
     __shared__ long long s_idx;
     __shared__ ResReq s_req;
     const int tid = threadIdx.x;
@@ -226,10 +239,17 @@ bool resident_kind_supported(int kind) {
 }
 
 lscan_status launch_resident(const ResParams &p, int ctas, cudaStream_t s) {
+    static std::once_flag attr_once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(attr_once, [] {
+        attr_err = cudaFuncSetAttribute(reinterpret_cast<const void *>(&lscan_resident_kernel),
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmem);
+    });
+    if (attr_err != cudaSuccess) return LSCAN_ERR_CUDA;
     ResParams q = p;
     void *args[] = {&q};
     if (cudaLaunchKernel(reinterpret_cast<const void *>(&lscan_resident_kernel), dim3(ctas),
-                         dim3(kTinyThreads), args, 0, s) != cudaSuccess)
+                         dim3(kResThreads), args, kResSmem, s) != cudaSuccess)
         return LSCAN_ERR_CUDA;
     note_launch();
     return LSCAN_OK;
