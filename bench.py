@@ -75,7 +75,8 @@ def _inputs(case, n):
 # Sources that do not build or launch the bench's scan kernels: other
 # kernels (radix offsets) and entry points the timed scans do not go through.
 _NOT_SCAN_SOURCES = {"radix_offsets.cu", "lscan_host.cu", "lscan_server.cu",
-                     "lscan_graph.cu", "lscan_noalloc.cu"}
+                     "lscan_graph.cu", "lscan_noalloc.cu", "resident_kernel.cu",
+                     "resident.h", "lscan_shard.cu"}
 
 
 def _kernel_source_hash():
@@ -98,14 +99,17 @@ def _kernel_source_hash():
 # reported traffic null until it is measured again (files listed in
 # _NOT_SCAN_SOURCES excepted).
 _TRAFFIC = {
-    "kernel_source_hash": "0694dacb42c5f58e",
+    "kernel_source_hash": "488fb445bdca0fbb",
     "bytes_per_launch": {  # (case, tile configuration)
-        ("i32_add", 2): 1074849280 + 1018741248,
-        ("i32_max", 2): 1074917120 + 1016145664,
-        ("f32_add", 2): 1073816576 + 1015674624,
-        ("i32_add", 3): 1074322176 + 1018503168,
-        ("i32_max", 3): 1074567936 + 1015757312,
-        ("f32_add", 3): 1074862336 + 1016258560,
+        ("i32_add", 6): 1078063616 + 1019414528,
+        ("i32_max", 6): 1078009600 + 1016260096,
+        ("f32_add", 6): 1078002944 + 1016312320,
+        ("i32_add", 8): 1075936000 + 1018903040,
+        ("i32_max", 8): 1075922688 + 1015488512,
+        ("f32_add", 8): 1075930112 + 1015948544,
+        ("i32_add", 17): 1075218176 + 1018685696,
+        ("i32_max", 17): 1075228416 + 1015949824,
+        ("f32_add", 17): 1075238912 + 1015441408,
     },
 }
 
