@@ -3,7 +3,7 @@
 One step = one pass of the scan path over the single-array workload: an
 inclusive int32 add-scan (uniform [-2^15, 2^15]), an inclusive int32
 max-scan (full int32 range) and an inclusive fp32 add-scan (uniform [0, 1),
-FP64 carry), each over N = 2^28 elements already resident in HBM.
+double-float carry), each over N = 2^28 elements already resident in HBM.
 value = bytes moved (each element read once and written once) / time, summed
 over ranks.  Inputs are 1 GiB per array, far above the 129 MB L2, so no L2
 flush is needed between steps.
@@ -12,11 +12,19 @@ Also reported on the same line:
   roofline     dominant kernel's algorithmic GB/s vs the measured HBM copy peak
   e2e          the same scans from pinned HOST buffers through the C ABI's
                host entry point (lscan_scan_host: chunked copy-in, scan and
-               copy-out overlapped), all copies inside the timed region
+               copy-out overlapped), all copies inside the timed region, with
+               the host link's own pinned-copy ceiling measured beside it
+  cub          CUB's device scan on the same resident inputs (comparator)
   batched      4096 log-uniform arrays (lengths 1..2^20) in one persistent
                launch replayed from a CUDA graph, vs 4096 plain launches
+  dtypes       add scans of the paper's types (int32, fp32, int64, double)
+  precision    fp32 and bf16 add at 2^26 on log-normal input, every carry
+               path, with the error against a float64 reference
+  bf16         bf16 max and add (fp32 and bf16 output) at 2^28
+  small        latency of an L2-resident 2^20 scan and of a 1000-element one
   select       stream compaction (a scan consumer), 2^28 int32, half kept
   radix        radix-sort digit offsets (a scan consumer), 2^28 uint32 keys
+  serving      Poisson request streams through the scan server
   cpu_baseline the sequential CPU oracle timed on a bounded sample
   clocks       nvidia-smi samples taken during the timed region
 
@@ -447,6 +455,11 @@ def run_gpu(args, ws, rank, local):
         e2e["host_link"] = link
         e2e["frac_of_duplex_copy"] = round(e2e["value"] / link["duplex_gbs"], 4)
 
+    # ---- comparator: CUB's device scan on the same resident inputs ----
+    cub = None
+    if not args.no_cub and ws == 1 and not args.sharded:
+        cub = bench_cub(dev, stream, peak, xs, ys, launch, N)
+
     # ---- batched: one graph-replayed persistent launch vs 4096 launches ----
     batched = None
     if not args.no_batched:
@@ -499,6 +512,7 @@ def run_gpu(args, ws, rank, local):
         "small": small,
         "select": select,
         "radix": radix,
+        "cub": cub,
         "serving": serving,
         "clocks": clk,
     }
@@ -658,6 +672,65 @@ def bench_bf16(args, dev, stream, peak, log2n=28):
                      "frac_measured": round(gbs / peak, 4)}
         del y
     _lib.check(_lib.lscan_stream_status(sp), "bf16")
+    return out
+
+
+def bench_cub(dev, stream, peak, xs, ys, launch, n, reps=10):
+    """Comparator: CUB's single-pass device scan (cub::DeviceScan, built from
+    the CUDA toolkit's headers into libcubcmp.so beside liblscan.so) on the
+    headline's resident 2^28-element inputs, timed the same way and
+    alternating with this library's scans on the same buffers.  For the
+    int32 scans its output is compared with this library's bit for bit."""
+    import ctypes
+
+    import torch
+
+    from paper_1604_04815_gb300 import build as _build
+    path = _build.CMP_LIB
+    if not os.path.exists(path):
+        return {"unavailable": "libcubcmp.so was not built (CUB headers missing?)"}
+    lib = ctypes.CDLL(path)
+    lib.cubcmp_temp_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.cubcmp_inclusive.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_longlong,
+                                     ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]
+    sp = stream.cuda_stream
+    y2 = torch.empty(n, dtype=torch.int32, device=dev)
+    out = {"n": n, "source": "cub::DeviceScan::InclusiveSum / InclusiveScan "
+           "(cuda::maximum) from the CUDA toolkit's CCCL headers"}
+    for c, op, dt in CASES:
+        opc, dtc = (0 if op == "add" else 1), (0 if dt == "i32" else 1)
+        nb = ctypes.c_size_t(0)
+        if lib.cubcmp_temp_bytes(opc, dtc, n, ctypes.byref(nb)) != 0:
+            return {"unavailable": "cub temp-storage query failed"}
+        tmp = torch.empty(max(1, nb.value), dtype=torch.uint8, device=dev)
+        x = xs[c]
+
+        def run_cub():
+            if lib.cubcmp_inclusive(opc, dtc, x.data_ptr(), y2.data_ptr(), n,
+                                    tmp.data_ptr(), nb.value, sp) != 0:
+                raise RuntimeError("cub scan failed")
+        with torch.cuda.stream(stream):
+            t_cub, t_ls = [], []
+            for _ in range(3):
+                run_cub()
+                launch(c, op, dt)
+            for _ in range(3):  # alternate, best of three batches each
+                t_cub.append(_time_launches(stream, run_cub, reps))
+                t_ls.append(_time_launches(stream, lambda: launch(c, op, dt), reps))
+        tc, tl = min(t_cub), min(t_ls)
+        gb = 8 * n / 1e9
+        r = {"cub_us": round(tc * 1e6, 1), "cub_gbs": round(gb / tc, 1),
+             "cub_frac_measured": round(gb / tc / peak, 4),
+             "lscan_us": round(tl * 1e6, 1), "lscan_gbs": round(gb / tl, 1),
+             "lscan_over_cub": round(tc / tl, 3)}
+        if dt == "i32":
+            stream.synchronize()
+            r["same_output"] = bool(torch.equal(y2, ys[c]))
+        out[c] = r
+        del tmp
     return out
 
 
@@ -1011,6 +1084,8 @@ def main():
                          "instead of independent replicas")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-radix", action="store_true")
+    ap.add_argument("--no-cub", action="store_true",
+                    help="skip the CUB device-scan comparator")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="elements per chunk of lscan_scan_host (0 = the "
                          "library's ramped schedule)")

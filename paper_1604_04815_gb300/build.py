@@ -18,6 +18,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblscan.so")
+# the benchmark's comparator (CUB's device scan), a library of its own
+CMP_SRC = os.path.join(HERE, "compare", "cub_scan.cu")
+CMP_LIB = os.path.join(OUT, "libcubcmp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
@@ -47,7 +50,7 @@ def _headers():
 
 def _stamp():
     h = hashlib.sha256()
-    for f in _sources() + _headers() + [os.path.abspath(__file__)]:
+    for f in _sources() + _headers() + [CMP_SRC, os.path.abspath(__file__)]:
         with open(f, "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -70,7 +73,9 @@ def build(force=False, jobs=None, verbose=False):
         obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         cmds.append([nvcc] + ARCH + NVCC_FLAGS + ["-c", src, "-o", obj])
-    jobs = jobs or max(1, min(len(cmds), os.cpu_count() or 4))
+    cmp_obj = os.path.join(OUT, "cub_scan.o")
+    cmp_cmd = [nvcc] + ARCH + NVCC_FLAGS + ["-c", CMP_SRC, "-o", cmp_obj]
+    jobs = jobs or max(1, min(len(cmds) + 1, os.cpu_count() or 4))
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -82,13 +87,30 @@ def build(force=False, jobs=None, verbose=False):
         return cmd[-1]
 
     with cf.ThreadPoolExecutor(jobs) as ex:
+        cmp_job = ex.submit(run, cmp_cmd) if os.path.exists(CMP_SRC) else None
         list(ex.map(run, cmds))
+        cmp_err = None
+        if cmp_job is not None:
+            try:
+                cmp_job.result()
+            except RuntimeError as e:  # the comparator is optional
+                cmp_err = e
     tmp = LIB + f".tmp{os.getpid()}"
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
+    # the comparator library: bench.py reports its section as unavailable
+    # when it did not build
+    if cmp_job is not None and cmp_err is None:
+        tmp = CMP_LIB + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, cmp_obj],
+                           capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, CMP_LIB)
+    elif cmp_err is not None and verbose:
+        print(f"comparator not built: {cmp_err}", file=sys.stderr)
     with open(stamp_file, "w") as f:
         f.write(stamp)
     return LIB
