@@ -199,7 +199,7 @@ lscan_status lscan_scan_host(lscan_op op, lscan_dtype dtype, int inclusive,
  *    CUDA's lazy module loading, the moment the driver loads the module and
  *    places the array) and clears it with cudaMemsetAsync on `stream`.  Make
  *    that first call at initialisation, outside any context that must not
- *    allocate, and before any stream capture.
+ *    allocate.
  *  - Every call shares the array (it keeps the last call's contents; each
  *    launch re-arms it for the next one).  Calls that overlap on the GPU race
  *    on it: keep them on one stream or synchronise between them.

@@ -20,8 +20,7 @@
 //    device address (under lazy module loading this loads the library's
 //    module, which is when the driver places the array) and clears it with
 //    cudaMemsetAsync on the caller's stream.  Make it at initialisation,
-//    outside any context that must not allocate, and before any stream
-//    capture.
+//    outside any context that must not allocate.
 //  - All calls share the one array.  Each launch re-arms the ticket and
 //    advances the epoch itself at its end, so consecutive calls need no
 //    clearing, but calls that overlap on the GPU (different streams without
