@@ -47,6 +47,13 @@ __device__ __forceinline__ uint16_t f32_to_bf16_bits_exact(float f) {
 __device__ __forceinline__ uint16_t f32_to_bf16_bits_rn(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
+// Two fp32 values rounded to bf16 (to nearest, ties to even) and packed in
+// one instruction: lo in bits 0..15, hi in bits 16..31.
+__device__ __forceinline__ uint32_t f32x2_to_bf16x2_rn(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
 
 // s + e == a + b exactly (Knuth two-sum)
 __device__ __forceinline__ float2 two_sum(float a, float b) {
@@ -193,9 +200,9 @@ struct KFAddPlain {
     __device__ static CarA to_apply(Car c) { return c; }
     __device__ static CarA base(CarA c, Acc tb) { return __fadd_rn(c, tb); }
     __device__ static CarA base_local(Acc tb) { return tb; }
-    __device__ static Out fin(CarA b, Acc v) {
-        return FloatOut<OutT>::cvt(__fadd_rn(b, v));
-    }
+    // the output before its rounding to Out (fp32)
+    __device__ static float fin_f(CarA b, Acc v) { return __fadd_rn(b, v); }
+    __device__ static Out fin(CarA b, Acc v) { return FloatOut<OutT>::cvt(fin_f(b, v)); }
     __device__ static Car car_of_out(Out o) { return FloatIn<OutT>::load(o); }
 };
 
@@ -220,9 +227,8 @@ struct KFAddF64 {
         return make_float2(s.x, __fadd_rn(s.y, c.y));
     }
     __device__ static CarA base_local(Acc tb) { return make_float2(tb, 0.0f); }
-    __device__ static Out fin(CarA b, Acc v) {
-        return FloatOut<OutT>::cvt(__fadd_rn(b.x, __fadd_rn(v, b.y)));
-    }
+    __device__ static float fin_f(CarA b, Acc v) { return __fadd_rn(b.x, __fadd_rn(v, b.y)); }
+    __device__ static Out fin(CarA b, Acc v) { return FloatOut<OutT>::cvt(fin_f(b, v)); }
     __device__ static Car car_of_out(Out o) {
         return static_cast<double>(FloatIn<OutT>::load(o));
     }
@@ -251,9 +257,8 @@ struct KFAddDF {
         return make_float2(s.x, __fadd_rn(s.y, c.y));
     }
     __device__ static CarA base_local(Acc tb) { return make_float2(tb, 0.0f); }
-    __device__ static Out fin(CarA b, Acc v) {
-        return FloatOut<OutT>::cvt(__fadd_rn(b.x, __fadd_rn(v, b.y)));
-    }
+    __device__ static float fin_f(CarA b, Acc v) { return __fadd_rn(b.x, __fadd_rn(v, b.y)); }
+    __device__ static Out fin(CarA b, Acc v) { return FloatOut<OutT>::cvt(fin_f(b, v)); }
     __device__ static Car car_of_out(Out o) {
         return make_float2(FloatIn<OutT>::load(o), 0.0f);
     }
@@ -295,9 +300,10 @@ struct KFAddComp {
     __device__ static CarA to_apply(Car c) { return c; }
     __device__ static CarA base(CarA c, Acc tb) { return df_add(c, tb); }
     __device__ static CarA base_local(Acc tb) { return tb; }
-    __device__ static Out fin(CarA b, Acc v) {
-        return FloatOut<OutT>::cvt(__fadd_rn(__fadd_rn(b.x, v.x), __fadd_rn(b.y, v.y)));
+    __device__ static float fin_f(CarA b, Acc v) {
+        return __fadd_rn(__fadd_rn(b.x, v.x), __fadd_rn(b.y, v.y));
     }
+    __device__ static Out fin(CarA b, Acc v) { return FloatOut<OutT>::cvt(fin_f(b, v)); }
     __device__ static Car car_of_out(Out o) {
         return make_float2(FloatIn<OutT>::load(o), 0.0f);
     }
@@ -447,6 +453,14 @@ template <class K, class = void>
 struct is_select : std::false_type {};
 template <class K>
 struct is_select<K, std::void_t<decltype(K::kSelect)>> : std::bool_constant<K::kSelect> {};
+
+// kinds whose output is a rounding of an fp32 value (K::fin_f): a bf16
+// output pair is rounded and packed by one conversion
+template <class K, class = void>
+struct has_fin_f : std::false_type {};
+template <class K>
+struct has_fin_f<K, std::void_t<decltype(K::fin_f(typename K::CarA{}, typename K::Acc{}))>>
+    : std::true_type {};
 
 template <class K, class = void>
 struct has_split_reduce : std::false_type {};

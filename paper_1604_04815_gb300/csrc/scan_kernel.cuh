@@ -1369,7 +1369,10 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
             const CarA B = K::base(cin, tbv);            // carry (+) thread base
             const CarA BL = K::base_local(tbv);          // head earlier in tile
             const CarA BI = K::base_local(K::ident());   // head earlier in thread
+            constexpr bool kPackBf16Out =
+                has_fin_f<K>::value && sizeof(Out) == 2 && ITEMS % 2 == 0;
             Out o[ITEMS];
+            float of[kPackBf16Out ? ITEMS : 1];
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 Acc pv;
@@ -1388,7 +1391,20 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     pf = SG && ((hb & ((1u << i) - 1u)) != 0u);
                 }
                 const CarA b = pf ? BI : ((SG && tbf) ? BL : B);
-                o[i] = K::fin(b, pv);
+                if constexpr (kPackBf16Out) {
+                    of[i] = K::fin_f(b, pv);
+                } else {
+                    o[i] = K::fin(b, pv);
+                }
+            }
+            if constexpr (kPackBf16Out) {
+                // bf16 output: each pair rounded and packed by one conversion
+#pragma unroll
+                for (int i = 0; i < ITEMS; i += 2) {
+                    const uint32_t w = f32x2_to_bf16x2_rn(of[i], of[i + 1]);
+                    o[i] = static_cast<Out>(w & 0xffffu);
+                    o[i + 1] = static_cast<Out>(w >> 16);
+                }
             }
             if (TMA && full_tile && OS == 0) {
                 // 16-byte stores straight from registers (no staging buffer)
