@@ -53,15 +53,15 @@ int default_variant(int kind, int mode, int size_cls = 28) {
         case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5747
         case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5880, 5327
         case KIND_F32_ADD_COMP: return single ? 8 : 3;   // 4543
-        case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6225
-        case KIND_BF16_ADD_F64_F32: return single ? 7 : 5;
+        case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6214
+        case KIND_BF16_ADD_F64_F32: return single ? (size_cls >= 25 ? 12 : 7) : 5;  // 5581
         case KIND_BF16_ADD_DF_F32:  // 5621
             return single ? (size_cls >= 25 ? 12 : size_cls >= 23 ? 11 : 13) : 2;
         case KIND_BF16_ADD_COMP_F32: return single ? (size_cls >= 25 ? 17 : 13) : 4;  // 3602
-        case KIND_BF16_ADD_PLAIN_BF16: return single ? 13 : 4;
-        case KIND_BF16_ADD_F64_BF16: return single ? 11 : 5;
-        case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4548
-        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 3 : 13) : 4;  // 2580
+        case KIND_BF16_ADD_PLAIN_BF16: return single ? (size_cls >= 25 ? 17 : 13) : 4;  // 4871
+        case KIND_BF16_ADD_F64_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4778
+        case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4644
+        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 11 : 13) : 4;  // 2657
         case KIND_I64_ADD: return single ? 8 : 5;      // 5906, 5625
         case KIND_I64_MAX: return single ? 8 : 5;
         case KIND_F64_MAX: return single ? 8 : 4;
