@@ -107,17 +107,17 @@ def _kernel_source_hash():
 # reported traffic null until it is measured again (files listed in
 # _NOT_SCAN_SOURCES excepted).
 _TRAFFIC = {
-    "kernel_source_hash": "488fb445bdca0fbb",
+    "kernel_source_hash": "20238651f5923232",
     "bytes_per_launch": {  # (case, tile configuration)
-        ("i32_add", 6): 1078063616 + 1019414528,
-        ("i32_max", 6): 1078009600 + 1016260096,
-        ("f32_add", 6): 1078002944 + 1016312320,
-        ("i32_add", 8): 1075936000 + 1018903040,
-        ("i32_max", 8): 1075922688 + 1015488512,
-        ("f32_add", 8): 1075930112 + 1015948544,
-        ("i32_add", 17): 1075218176 + 1018685696,
-        ("i32_max", 17): 1075228416 + 1015949824,
-        ("f32_add", 17): 1075238912 + 1015441408,
+        ("i32_add", 6): 1077993216 + 1019591936,
+        ("i32_max", 6): 1078065408 + 1016542464,
+        ("f32_add", 6): 1078019840 + 1016318208,
+        ("i32_add", 8): 1075976704 + 1018890496,
+        ("i32_max", 8): 1076095744 + 1016697856,
+        ("f32_add", 8): 1075994368 + 1015994112,
+        ("i32_add", 17): 1075382272 + 1018702592,
+        ("i32_max", 17): 1075233024 + 1016229376,
+        ("f32_add", 17): 1075398400 + 1015774464,
     },
 }
 
