@@ -1109,7 +1109,7 @@ def main():
                          "0 = every request in the bulk lane")
     ap.add_argument("--serving-bulk-tiles", type=int, default=16384,
                     help="tiles per bulk-lane batch")
-    ap.add_argument("--serving-reserve-sms", type=int, default=8,
+    ap.add_argument("--serving-reserve-sms", type=int, default=4,
                     help="SMs kept for the resident lane's kernel")
     ap.add_argument("--log2n", type=int, default=28,
                     help="array size 2^k (28 = the benchmarked workload; "

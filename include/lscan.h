@@ -341,14 +341,19 @@ void lscan_server_destroy(lscan_server *srv);
  * Destroying a held server still runs everything it admitted. */
 lscan_status lscan_server_hold(lscan_server *srv, int hold);
 /* Size-class lanes.  Requests of at most small_max_elems elements (default
- * 2^16) have their own admission queue and two launch slots on a stream of
- * the device's greatest priority, and are batched only with each other;
- * bulk batches hold at most bulk_batch_tiles tiles (default 8192, 1 ..
- * 65536), so a small batch waits at most about one capped bulk launch for
- * SM slots, and launch CTAs for (SMs - reserve_sms) SMs only (default 0,
- * at most 64), leaving that many SMs' worth of CTA slots to small batches.
- * small_max_elems = 0 puts every request in the bulk lane.  Applies to
- * requests submitted afterwards.  (Not in the paper.) */
+ * 2^14) of the kinds the resident kernel scans (int32 add and max, fp32 and
+ * bf16 max, fp32 and bf16 add with the default double-float carry and fp32
+ * output, int64 add and max, double add and max) take the resident lane: a
+ * persistent kernel on reserve_sms SMs (default 4, 0 .. 64; 0 reserves none
+ * and the kernel shares the SMs) takes each request from a ring of
+ * descriptors in host memory mapped for the device, scans it with one CTA
+ * and writes its done word -- no launch per request; the submitting thread
+ * publishes the request itself.  The kernel leaves after 20 ms without work
+ * and is launched again when work arrives.  Other requests form bulk
+ * batches of at most bulk_batch_tiles tiles (default 8192, 1 .. 65536),
+ * launched for (SMs - reserve_sms) SMs.  small_max_elems = 0 puts every
+ * request in the bulk lane.  Applies to requests submitted afterwards.
+ * (Not in the paper.) */
 lscan_status lscan_server_set_lanes(lscan_server *srv, int64_t small_max_elems,
                                    int64_t bulk_batch_tiles, int32_t reserve_sms);
 /* Client buffers from the pool (count against the budget); NOMEM if full. */

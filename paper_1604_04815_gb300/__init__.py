@@ -300,12 +300,12 @@ class Server:
         return _lib.device_view(stats["y"], stats["n"],
                                 out_dtype_for(op, dtype))
 
-    def set_lanes(self, small_max_elems=1 << 16, bulk_batch_tiles=8192,
-                  reserve_sms=0):
-        """Size-class lanes: requests of at most small_max_elems elements get
-        their own high-priority stream; bulk batches hold at most
-        bulk_batch_tiles tiles and leave reserve_sms SMs' worth of CTA
-        slots free."""
+    def set_lanes(self, small_max_elems=1 << 14, bulk_batch_tiles=8192,
+                  reserve_sms=4):
+        """Size-class lanes (the library's defaults): requests of at most
+        small_max_elems elements go to the resident kernel on reserve_sms
+        SMs; bulk batches hold at most bulk_batch_tiles tiles and run on the
+        other SMs (lscan_server_set_lanes)."""
         _lib.check(_lib.load().lscan_server_set_lanes(
             self._h, int(small_max_elems), int(bulk_batch_tiles),
             int(reserve_sms)), "lscan_server_set_lanes")

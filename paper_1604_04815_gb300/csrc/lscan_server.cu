@@ -70,7 +70,7 @@ constexpr int64_t kMinTileBytes = 8192;     // smallest input tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
 constexpr int64_t kDefaultSmallMax = int64_t{1} << 14;  // elements
 constexpr int64_t kDefaultBulkCap = 8192;               // tiles per bulk batch
-constexpr int kDefaultReserveSms = 8;                   // SMs for the resident lane
+constexpr int kDefaultReserveSms = 4;                   // SMs for the resident lane
 constexpr int kResCtasPerSm = 2;                        // resident CTAs per reserved SM
 constexpr int64_t kResRing = 4096;                      // resident ring entries
 constexpr uint64_t kResIdleNs = 20000000;               // resident CTAs leave after 20 ms idle
