@@ -15,6 +15,7 @@ Also reported on the same line:
                copy-out overlapped), all copies inside the timed region, with
                the host link's own pinned-copy ceiling measured beside it
   cub          CUB's device scan on the same resident inputs (comparator)
+  cpu_parallel a multi-threaded scan on all host cores (comparator)
   batched      4096 log-uniform arrays (lengths 1..2^20) in one persistent
                launch replayed from a CUDA graph, vs 4096 plain launches
   dtypes       add scans of the paper's types (int32, fp32, int64, double)
@@ -455,10 +456,14 @@ def run_gpu(args, ws, rank, local):
         e2e["host_link"] = link
         e2e["frac_of_duplex_copy"] = round(e2e["value"] / link["duplex_gbs"], 4)
 
-    # ---- comparator: CUB's device scan on the same resident inputs ----
+    # ---- comparators: CUB's device scan on the same resident inputs, and a
+    # multi-threaded scan on the host cores ----
     cub = None
     if not args.no_cub and ws == 1 and not args.sharded:
         cub = bench_cub(dev, stream, peak, xs, ys, launch, N)
+    cpu_par = None
+    if not args.no_cpu_parallel and ws == 1 and not args.sharded:
+        cpu_par = bench_cpu_parallel(host, N)
 
     # ---- batched: one graph-replayed persistent launch vs 4096 launches ----
     batched = None
@@ -513,6 +518,7 @@ def run_gpu(args, ws, rank, local):
         "select": select,
         "radix": radix,
         "cub": cub,
+        "cpu_parallel": cpu_par,
         "serving": serving,
         "clocks": clk,
     }
@@ -731,6 +737,43 @@ def bench_cub(dev, stream, peak, xs, ys, launch, n, reps=10):
             r["same_output"] = bool(torch.equal(y2, ys[c]))
         out[c] = r
         del tmp
+    return out
+
+
+def bench_cpu_parallel(host, n, reps=3):
+    """Comparator: a multi-threaded inclusive scan on all host cores
+    (reduce-then-scan over one chunk per thread, libcpuscan.so beside
+    liblscan.so), the counterpart of the paper's parallel-CPU comparison,
+    on the headline's arrays in host memory; best of `reps` per scan."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_1604_04815_gb300 import build as _build
+    if not os.path.exists(_build.CPU_LIB):
+        return {"unavailable": "libcpuscan.so was not built (no C compiler?)"}
+    lib = ctypes.CDLL(_build.CPU_LIB)
+    lib.cpuscan_inclusive.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+    threads = max(1, min(256, os.cpu_count() or 1))
+    out = {"n": n, "threads": threads,
+           "method": "reduce-then-scan, one contiguous chunk per thread (pthreads)"}
+    tot_t = 0.0
+    for c, op, dt in CASES:
+        x = host[c]
+        y = np.empty_like(x)
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            if lib.cpuscan_inclusive(0 if op == "add" else 1, 0 if dt == "i32" else 1,
+                                     x.ctypes.data, y.ctypes.data, n, threads) != 0:
+                return {"unavailable": "host scan failed"}
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        tot_t += best
+        out[c] = {"gbs": round(8 * n / best / 1e9, 2)}
+        del y
+    out["gbs"] = round(len(CASES) * 8 * n / tot_t / 1e9, 2)
     return out
 
 
@@ -1086,6 +1129,8 @@ def main():
     ap.add_argument("--no-radix", action="store_true")
     ap.add_argument("--no-cub", action="store_true",
                     help="skip the CUB device-scan comparator")
+    ap.add_argument("--no-cpu-parallel", action="store_true",
+                    help="skip the multi-threaded host-scan comparator")
     ap.add_argument("--e2e-chunk", type=int, default=0,
                     help="elements per chunk of lscan_scan_host (0 = the "
                          "library's ramped schedule)")

@@ -21,6 +21,9 @@ LIB = os.path.join(OUT, "liblscan.so")
 # the benchmark's comparator (CUB's device scan), a library of its own
 CMP_SRC = os.path.join(HERE, "compare", "cub_scan.cu")
 CMP_LIB = os.path.join(OUT, "libcubcmp.so")
+# ... and the multi-threaded host scan (plain C, gcc)
+CPU_SRC = os.path.join(HERE, "compare", "cpu_scan.c")
+CPU_LIB = os.path.join(OUT, "libcpuscan.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
               "-Xcompiler", "-O2", "--expt-relaxed-constexpr",
@@ -50,7 +53,7 @@ def _headers():
 
 def _stamp():
     h = hashlib.sha256()
-    for f in _sources() + _headers() + [CMP_SRC, os.path.abspath(__file__)]:
+    for f in _sources() + _headers() + [CMP_SRC, CPU_SRC, os.path.abspath(__file__)]:
         with open(f, "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
@@ -111,6 +114,15 @@ def build(force=False, jobs=None, verbose=False):
             os.replace(tmp, CMP_LIB)
     elif cmp_err is not None and verbose:
         print(f"comparator not built: {cmp_err}", file=sys.stderr)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc and os.path.exists(CPU_SRC):
+        tmp = CPU_LIB + f".tmp{os.getpid()}"
+        r = subprocess.run([cc, "-O3", "-fPIC", "-shared", "-pthread", "-o", tmp, CPU_SRC],
+                           capture_output=True, text=True)
+        if r.returncode == 0:
+            os.replace(tmp, CPU_LIB)
+        elif verbose:
+            print("host comparator not built:\n" + r.stderr, file=sys.stderr)
     with open(stamp_file, "w") as f:
         f.write(stamp)
     return LIB
