@@ -161,3 +161,44 @@ def test_server_rejects_bad_requests():
         assert L.lscan_server_release(srv._h, 12345) == _lib.LSCAN_ERR_INVALID
     finally:
         srv.close()
+
+
+def test_resident_lane_across_chunk_boundaries():
+    """Small-lane requests scanned by the resident kernel, one CTA each, in
+    chunks of 16384 elements of up to 4 bytes or 8192 of 8 bytes: sizes just
+    below, at and above a chunk and over several chunks, so the running
+    carry passes from chunk to chunk, for every kind the lane scans (int32
+    add and max, fp32 and bf16 max, fp32 and bf16 add with the default
+    carry, int64 and double add and max).  The lane bound is raised to 2^16
+    so that requests of several chunks take it."""
+    srv = lscan.Server(budget_bytes=1 << 30, n_streams=2)
+    try:
+        srv.set_lanes(small_max_elems=1 << 16, bulk_batch_tiles=8192, reserve_sms=4)
+        rng = np.random.default_rng(44)
+        cases = []
+        for dtype in ("i32", "f32", "bf16", "i64", "f64"):
+            chunk = 8192 if dtype in ("i64", "f64") else 16384
+            for n in (chunk - 1, chunk, chunk + 1, 3 * chunk + 17, 1 << 16):
+                for op in ("add", "max"):
+                    incl = bool(rng.random() < 0.5)
+                    kind = "full" if dtype in ("i32", "i64") else "signed"
+                    cases.append((op, dtype, incl,
+                                  random_array(dtype, n, rng, kind=kind)))
+        xs = [to_device(x, d) for _, d, _, x in cases]
+        ys = [torch.empty(x.shape[0], dtype=lscan.out_dtype_for(op, TDT[d]),
+                          device="cuda") for op, d, _, x in cases]
+        # queued while the server holds: the bulk lane would launch each
+        # kind's five requests together, the resident lane retires them one
+        # by one (batch_requests == 1 shows which lane took them)
+        srv.hold(True)
+        tks = [srv.submit(xd, op, incl, out=y)
+               for (op, _, incl, _), xd, y in zip(cases, xs, ys)]
+        srv.hold(False)
+        for tk in tks:
+            st = srv.wait(tk)
+            assert st["status"] == 0 and st["batch_requests"] == 1
+            srv.release(tk)
+        for (op, d, incl, x), y in zip(cases, ys):
+            assert_matches(op, d, x, to_host(y), incl)
+    finally:
+        srv.close()
