@@ -9,7 +9,7 @@ import pytest
 import torch
 
 from gpu_util import (assert_matches, run_c_abi, to_device, to_host, LDT, LOP,
-                      PREC_CODE, TEST_WAIT_NS)
+                      PREC_CODE, TEST_WAIT_NS, out_torch_dtype)
 from paper_1604_04815_gb300 import _lib
 from paper_1604_04815_gb300.workloads import (random_array, batched_lengths,
                                               offsets_from_lengths)
@@ -57,6 +57,7 @@ CHAINED_KINDS = _pick("add-i32-exact", "max-i32-exact", "add-f32-f64",
 BATCHED_KINDS = _pick("add-i32-exact", "max-i32-exact", "max-f32-exact",
                       "max-bf16-exact", "add-f32-f64", "add-f32-comp",
                       "add-f32-df", "add-bf16-f64", "add-bf16-df",
+                      "add-bf16-df-bf16out", "add-bf16-comp-bf16out",
                       "add-i64-exact", "max-i64-exact", "max-f64-exact",
                       "add-f64-exact")
 
@@ -228,10 +229,10 @@ def test_batched(kind, inclusive, pattern):
     for config in range(1, 7):  # the configurations built for batched scans
         xd = to_device(x, dtype)
         od = torch.from_numpy(off).cuda()
-        y = torch.empty(n, dtype=torch.float32 if (op == "add" and
-                        dtype == "bf16") else xd.dtype, device="cuda")
+        y = torch.empty(n, dtype=out_torch_dtype(op, dtype, ob), device="cuda")
         opts = _lib.make_options(precision=PREC_CODE[prec] if prec else 0,
-                                 config=config)
+                                 config=config,
+                                 out_dtype=_lib.LSCAN_BF16 if ob else 0)
         s = torch.cuda.current_stream().cuda_stream
         st = _lib.lscan_batched(LOP[op], LDT[dtype], int(inclusive),
                                 xd.data_ptr(), y.data_ptr(), od.data_ptr(),
@@ -239,7 +240,7 @@ def test_batched(kind, inclusive, pattern):
         assert st == _lib.LSCAN_OK
         assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
         assert_matches(op, dtype, x, to_host(y), inclusive, prec or "f64",
-                       offsets=off)
+                       out_bf16=ob, offsets=off)
 
 
 def test_batched_unaligned_and_chained():
