@@ -1,7 +1,9 @@
 """Parity at the full single-array sizes (N = 2^28) in the launch
 configuration bench.py times (default tuned tile configuration, decoupled
-look-back, FP64 carry for fp32 add): every output element is compared with the
-oracle, which finishes a 2^28 scan in about a second."""
+look-back, double-float carry for fp32 add): every output element is compared
+with the oracle, which finishes a 2^28 scan in about a second.  Beyond 2^31
+elements, where a 32-bit element index would overflow, the outputs are
+checked on the device against properties that hold at any size."""
 import numpy as np
 import pytest
 import torch
@@ -99,3 +101,25 @@ def test_full_size_select():
     want = oracle.select_flagged(x, f)
     assert k == want.shape[0]
     assert np.array_equal(out[:k].cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("op", ["add", "max"])
+def test_beyond_2_31_elements(op):
+    """N = 2^31 + 4099 int32 elements (about 8.6 GB per array): the add-scan
+    of all ones is y_j = j + 1 modulo 2^32 (it passes 2^31 and wraps), and
+    the max-scan of a non-decreasing array is the array itself.  Every
+    element is compared on the device."""
+    from paper_1604_04815_gb300 import build
+    build.build()
+    n = (1 << 31) + 4099
+    if op == "add":
+        xd = torch.ones(n, dtype=torch.int32, device="cuda")
+        want = torch.arange(1, n + 1, dtype=torch.int64, device="cuda")
+        want = want.to(torch.int32)  # two's-complement wrap, as modulo 2^32
+    else:
+        want = (torch.arange(n, dtype=torch.int64, device="cuda") // 3).to(torch.int32)
+        xd = want.clone()
+    y = run_c_abi(op, "i32", xd, True)
+    assert torch.equal(y, want)
+    del xd, y, want
+    torch.cuda.empty_cache()
