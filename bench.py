@@ -1152,7 +1152,7 @@ def main():
     ap.add_argument("--serving-small-max", type=int, default=1 << 14,
                     help="largest request (elements) of the resident lane; "
                          "0 = every request in the bulk lane")
-    ap.add_argument("--serving-bulk-tiles", type=int, default=16384,
+    ap.add_argument("--serving-bulk-tiles", type=int, default=32768,
                     help="tiles per bulk-lane batch")
     ap.add_argument("--serving-reserve-sms", type=int, default=4,
                     help="SMs kept for the resident lane's kernel")

@@ -350,7 +350,7 @@ lscan_status lscan_server_hold(lscan_server *srv, int hold);
  * and writes its done word -- no launch per request; the submitting thread
  * publishes the request itself.  The kernel leaves after 20 ms without work
  * and is launched again when work arrives.  Other requests form bulk
- * batches of at most bulk_batch_tiles tiles (default 8192, 1 .. 65536),
+ * batches of at most bulk_batch_tiles tiles (default 32768, 1 .. 65536),
  * launched for (SMs - reserve_sms) SMs.  small_max_elems = 0 puts every
  * request in the bulk lane.  Applies to requests submitted afterwards.
  * (Not in the paper.) */

@@ -300,7 +300,7 @@ class Server:
         return _lib.device_view(stats["y"], stats["n"],
                                 out_dtype_for(op, dtype))
 
-    def set_lanes(self, small_max_elems=1 << 14, bulk_batch_tiles=8192,
+    def set_lanes(self, small_max_elems=1 << 14, bulk_batch_tiles=32768,
                   reserve_sms=4):
         """Size-class lanes (the library's defaults): requests of at most
         small_max_elems elements go to the resident kernel on reserve_sms

@@ -24,16 +24,16 @@
 //    schedulers issue in parallel.  Different kinds run on different streams
 //    and overlap on the device; requests arriving while batches run join the
 //    next launch.
-//  * Size-class lanes.  Requests of at most small_max elements (2^16 by
-//    default) form their own lane: their own admission queue and two launch
-//    slots on a stream created at the device's greatest priority, batched
-//    only with each other.  Bulk batches are capped at bulk_cap tiles (8192
-//    by default, ~128 MiB of 16 KiB tiles), so a small batch waits at most
-//    about one capped bulk launch for SM slots: when a bulk kernel's
-//    persistent CTAs retire, the block scheduler dispatches the
-//    higher-priority small batch before the bulk batch queued behind it.
-//    Bulk batches can also leave reserve_sms SMs' worth of CTA slots free
-//    (0 by default).  FIFO order holds within each lane.
+//  * Size-class lanes.  Requests of at most small_max elements (2^14 by
+//    default) of the kinds the resident kernel scans take the resident lane
+//    (resident_kernel.cu): the submitting thread writes each into a ring in
+//    host memory mapped for the device, where a persistent kernel on
+//    reserve_sms SMs (4 by default) claims it, scans it with one CTA and
+//    writes its done word; a resident worker thread relaunches the kernel
+//    when it has ended (idle) and retires finished requests.  Other
+//    requests form bulk batches capped at bulk_cap tiles (32768 by
+//    default), launched for the SMs the resident lane leaves.  FIFO order
+//    holds within each lane.
 //  * Completion.  Each scheduler polls the end event of its stream's older
 //    in-flight batch (cudaEventQuery; batches on a stream finish in issue
 //    order); nothing host-side sits in the stream, so the batch queued
@@ -69,7 +69,7 @@ constexpr int kSlotsPerStream = 2;          // a second batch queues behind the 
 constexpr int64_t kMinTileBytes = 8192;     // smallest input tile of any config
 constexpr int64_t kMaxBatchRequests = 4096;
 constexpr int64_t kDefaultSmallMax = int64_t{1} << 14;  // elements
-constexpr int64_t kDefaultBulkCap = 8192;               // tiles per bulk batch
+constexpr int64_t kDefaultBulkCap = 32768;              // tiles per bulk batch
 constexpr int kDefaultReserveSms = 4;                   // SMs for the resident lane
 constexpr int kResCtasPerSm = 2;                        // resident CTAs per reserved SM
 constexpr int64_t kResRing = 4096;                      // resident ring entries
