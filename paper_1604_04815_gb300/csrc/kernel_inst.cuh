@@ -154,6 +154,9 @@ void fill_entry(int kind, int variant) {
         e.car_words = status_slot_words<K, Cfg>();  // status words per tile
         e.in_size = int(sizeof(typename K::In));
         e.out_size = int(sizeof(typename K::Out));
+        using S = Swz<K, Cfg, MODE, TMA>;
+        e.swz_in = S::IN ? S::RBI : 0;
+        e.swz_out = S::OUT ? S::RBO : 0;
     }
 }
 

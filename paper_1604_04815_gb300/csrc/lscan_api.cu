@@ -92,6 +92,64 @@ struct Scratch {
 
 std::map<std::pair<int, void *>, Scratch *> g_scratch;
 
+// cuTensorMapEncodeTiled, looked up once through the runtime (the library
+// does not link the driver library itself)
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+std::once_flag g_encode_once;
+EncodeTiledFn g_encode = nullptr;
+
+EncodeTiledFn encode_tiled() {
+    std::call_once(g_encode_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return g_encode;
+}
+
+// Tensor map of `bytes` bytes at `base` (16-byte aligned) seen as rows of rb
+// bytes (32, 64 or 128) in boxes of 32 rows: dimensions [boxes][32][rb],
+// complete boxes only (a tile that reaches past the last one is never copied
+// through the map).  One copy moves `boxes_per_copy` consecutive boxes,
+// laid out in shared memory with the rb-byte swizzle.
+bool encode_row_map(CUtensorMap *m, const void *base, uint64_t bytes, int rb,
+                    int boxes_per_copy) {
+    EncodeTiledFn f = encode_tiled();
+    if (f == nullptr || (rb != 32 && rb != 64 && rb != 128)) return false;
+    const uint64_t boxes = bytes / (32u * static_cast<uint64_t>(rb));
+    if (boxes == 0 || boxes > static_cast<uint64_t>(INT32_MAX)) return false;
+    const cuuint64_t dim[3] = {static_cast<cuuint64_t>(rb), 32u, boxes};
+    const cuuint64_t stride[2] = {static_cast<cuuint64_t>(rb), 32u * static_cast<cuuint64_t>(rb)};
+    const cuuint32_t box[3] = {static_cast<cuuint32_t>(rb), 32u,
+                               static_cast<cuuint32_t>(boxes_per_copy)};
+    const cuuint32_t step[3] = {1u, 1u, 1u};
+    const CUtensorMapSwizzle sw = rb == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+    auto encode = [&] {
+        return f(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3u, const_cast<void *>(base), dim, stride,
+                 box, step, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    CUresult r = encode();
+    if (r == CUDA_ERROR_INVALID_CONTEXT) {
+        // a host thread whose runtime calls so far bound no context (the
+        // encoder needs one): bind the current device's primary context,
+        // as the launch that follows would, and encode again
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
+            r = encode();
+    }
+    return r == CUDA_SUCCESS;
+}
+
 struct FnState {
     bool attr_set = false;
     int blocks_per_sm = 0;
@@ -305,6 +363,20 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     p.values = ls.values;
     p.count_out = ls.count_out;
     p.err_host = ls.err_host;
+    std::memset(&p.tm_x, 0, sizeof(p.tm_x));
+    std::memset(&p.tm_y, 0, sizeof(p.tm_y));
+    if (ls.mode == MODE_SINGLE && ls.n >= e.tile) {
+        // full tiles exist: their swizzled copies go through the maps (a
+        // tile is e.cwarps boxes of x; each consumer warp stores one box of y)
+        if (e.swz_in != 0 &&
+            !encode_row_map(&p.tm_x, ls.x, static_cast<uint64_t>(ls.n) * e.in_size, e.swz_in,
+                            e.cwarps))
+            return LSCAN_ERR_CUDA;
+        if (e.swz_out != 0 &&
+            !encode_row_map(&p.tm_y, ls.y, static_cast<uint64_t>(ls.n) * e.out_size, e.swz_out,
+                            1))
+            return LSCAN_ERR_CUDA;
+    }
     void *args[] = {&p};
     cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
                                       dim3(e.threads), args, e.smem, cs);

@@ -35,37 +35,38 @@ std::mutex g_tab_mu;
 lscan_status load_file(const char *path);
 
 // Fastest configuration per kind on GB300 (GB/s in the comments), single
-// arrays and (first six configurations) batched scans.  Measured at 2^28,
-// and at 2^22 .. 2^26 for the kinds whose best depends on the size: 4- and
-// 8-byte kinds take configuration 8 (32 KiB tiles of 32 items x 8 warps,
-// 64-byte status slots) from 2^22 up; bf16 takes 48 or 56 KiB tiles (17,
-// 12) from 2^25 up, 3-stage 32 KiB tiles (11) from 2^23 and smaller ones
-// below.
+// arrays and (first six configurations) batched scans.  Measured at 2^28
+// with full tiles moved as swizzled tensor copies, and at 2^22 .. 2^26 for
+// the kinds whose best depends on the size: 4- and 8-byte kinds take
+// configuration 8 (32 KiB tiles of 32 items x 8 warps, 64-byte status
+// slots) from 2^22 up, the compensated fp32 add 64 KiB tiles (12) from 2^25;
+// bf16 takes 48, 56 or 16 KiB tiles (17, 12, 13) from 2^25 up, 3-stage
+// 32 KiB tiles (11) from 2^23 and smaller ones below.
 int default_variant(int kind, int mode, int size_cls = 28) {
     const bool single = mode == MODE_SINGLE;
     switch (kind) {
-        case KIND_I32_ADD: return single ? 8 : 6;      // 6147 (2^28), 5634 (2^26)
-        case KIND_I32_MAX: return single ? 8 : 6;      // 6140, 5634
-        case KIND_F32_MAX: return single ? 8 : 5;      // 6084, 5541
-        case KIND_BF16_MAX:  // 5290 (2^28)
+        case KIND_I32_ADD: return single ? 8 : 6;      // 6162 (2^28), 5634 (2^26)
+        case KIND_I32_MAX: return single ? 8 : 6;      // 6183, 5634
+        case KIND_F32_MAX: return single ? 8 : 5;      // 6261, 5541
+        case KIND_BF16_MAX:  // 5354 (2^28)
             return single ? (size_cls >= 25 ? 17 : size_cls >= 23 ? 11 : 5) : 5;
-        case KIND_F32_ADD_PLAIN: return single ? 8 : 6;  // 6175
-        case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5747
-        case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5880, 5327
-        case KIND_F32_ADD_COMP: return single ? 8 : 3;   // 4543
-        case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6214
-        case KIND_BF16_ADD_F64_F32: return single ? (size_cls >= 25 ? 12 : 7) : 5;  // 5581
-        case KIND_BF16_ADD_DF_F32:  // 5621
+        case KIND_F32_ADD_PLAIN: return single ? 8 : 6;  // 6214
+        case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5780
+        case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5960, 5327
+        case KIND_F32_ADD_COMP: return single ? (size_cls >= 25 ? 12 : 8) : 3;  // 5127
+        case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6172
+        case KIND_BF16_ADD_F64_F32: return single ? (size_cls >= 25 ? 12 : 7) : 5;  // 5789
+        case KIND_BF16_ADD_DF_F32:  // 5835
             return single ? (size_cls >= 25 ? 12 : size_cls >= 23 ? 11 : 13) : 2;
-        case KIND_BF16_ADD_COMP_F32: return single ? (size_cls >= 25 ? 17 : 13) : 4;  // 3602
-        case KIND_BF16_ADD_PLAIN_BF16: return single ? (size_cls >= 25 ? 17 : 13) : 4;  // 4871
-        case KIND_BF16_ADD_F64_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4778
-        case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4644
-        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 11 : 13) : 4;  // 2657
-        case KIND_I64_ADD: return single ? 8 : 5;      // 5906, 5625
-        case KIND_I64_MAX: return single ? 8 : 5;
-        case KIND_F64_MAX: return single ? 8 : 4;
-        case KIND_F64_ADD: return single ? 10 : 4;
+        case KIND_BF16_ADD_COMP_F32: return single ? 13 : 4;  // 4031
+        case KIND_BF16_ADD_PLAIN_BF16: return single ? (size_cls >= 25 ? 12 : 13) : 4;  // 4820
+        case KIND_BF16_ADD_F64_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4541
+        case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 12 : 11) : 5;  // 4555
+        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 5 : 13) : 4;  // 2738
+        case KIND_I64_ADD: return single ? 8 : 5;      // 5883, 5625
+        case KIND_I64_MAX: return single ? 8 : 5;      // 5651
+        case KIND_F64_MAX: return single ? 8 : 4;      // 3414
+        case KIND_F64_ADD: return single ? 10 : 4;     // 2038
         default: return 2;
     }
 }

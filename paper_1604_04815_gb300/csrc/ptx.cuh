@@ -1,7 +1,8 @@
 // ptx.cuh -- thin inline-PTX wrappers used by the scan kernels (sm_103a).
 //
-// mbarrier + cp.async.bulk implement the shared-memory tile ring (Section 4.1
-// loads x once, coalesced; here the copy engine does it).  The relaxed,
+// mbarrier + cp.async.bulk (and its tensor form, for swizzled tiles)
+// implement the shared-memory tile ring (Section 4.1 loads x once,
+// coalesced; here the copy engine does it).  The relaxed,
 // gpu-scope 64-bit loads and stores carry the inter-tile status words: each
 // word holds payload and flag together, so one single-copy-atomic access is
 // the whole message (Section 4.3 needs the value/flag pair to be written "in
@@ -76,6 +77,29 @@ __device__ __forceinline__ void bulk_s2g(void *gdst, const void *ssrc,
                      gdst),
                  "r"(smem_addr(ssrc)), "r"(bytes)
                  : "memory");
+}
+
+// Tensor copy of one box of a 3-D tensor map (kernel-parameter space) into
+// shared memory, completion counted on an mbarrier (the box's bytes).  The
+// map's swizzle mode decides where each 16-byte chunk of the box lands.
+__device__ __forceinline__ void tensor_g2s_3d(void *sdst, const void *tmap, int c0, int c1,
+                                              int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(sdst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Tensor copy of one box from shared memory (laid out with the map's
+// swizzle) to global memory, tracked by the issuing thread's bulk groups.
+__device__ __forceinline__ void tensor_s2g_3d(const void *tmap, const void *ssrc, int c0,
+                                              int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            tmap),
+        "r"(smem_addr(ssrc)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
 }
 
 __device__ __forceinline__ void bulk_commit() {

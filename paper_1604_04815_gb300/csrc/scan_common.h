@@ -1,5 +1,7 @@
 // scan_common.h -- definitions shared by the kernels and the host library.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include <cstdint>
 
 namespace lscan {
@@ -20,6 +22,8 @@ enum CtlWord : int {
 enum DevError : uint32_t {
     DEV_ERR_CARRY_WAIT = 1u,    // a predecessor's status never arrived in time
     DEV_ERR_BARRIER_WAIT = 2u,  // a tile-ring barrier never completed in time
+    DEV_ERR_SMEM_ALIGN = 4u,    // dynamic shared memory not 1024-byte aligned
+                                // (swizzled tile copies need it; nothing ran)
 };
 
 // Status word: (payload32 << 32) | tag32, tag = (epoch mod 2^30) << 2 | state.
@@ -77,6 +81,12 @@ struct ScanParams {
     // memory mapped for the device) and clears it, so a caller polling for
     // completion reads it without a device-to-host copy
     uint32_t *err_host;
+    // Single arrays, bulk-copy variants whose rows are 32, 64 or 128 bytes:
+    // x and y viewed as [boxes][32 rows][row bytes] (complete 32-row boxes
+    // only), from which whole tiles are copied with the row-width swizzle
+    // (encoded by the host at launch; unused otherwise)
+    CUtensorMap tm_x;
+    CUtensorMap tm_y;
 };
 
 // Single-CTA kernel for arrays of at most one tile (no inter-tile carry).

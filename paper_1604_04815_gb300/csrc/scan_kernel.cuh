@@ -95,6 +95,33 @@ constexpr int kernel_threads() {
     return Cfg::THREADS + (split_reduce<K, Cfg, MODE, TMA>() ? 32 : 0);
 }
 
+// Full tiles of a single array move between HBM and shared memory as tensor
+// copies with the swizzle of their row width: 16-byte chunk j of row r (one
+// consumer thread's elements) of a 1024-byte aligned tile sits at chunk
+// j ^ f(r), f(r) taken from address bits 7.. (swz_off).  Each quarter-warp's
+// 16-byte accesses then cover all 32 banks while every thread reads and
+// writes its chunks in element order: no register permutation after the
+// load or before the store.  Rows of 32, 64 or 128 bytes; the other
+// variants (batched modes, stream compaction, 16-byte rows, direct stores)
+// keep plain bulk copies and the XOR-rotated accesses.
+template <class K, class Cfg, int MODE, bool TMA>
+struct Swz {
+    static constexpr int RBI = Cfg::ITEMS * int(sizeof(typename K::In));
+    static constexpr int RBO = Cfg::ITEMS * int(sizeof(typename K::Out));
+    static constexpr bool kAny = MODE == MODE_SINGLE && TMA && !is_select<K>::value;
+    static constexpr bool IN = kAny && (RBI == 32 || RBI == 64 || RBI == 128);
+    static constexpr bool OUT =
+        kAny && Cfg::OSTAGES >= 1 && (RBO == 32 || RBO == 64 || RBO == 128);
+};
+
+// Where the byte at offset `off` of a 1024-byte aligned tile with RB-byte
+// rows lives under the RB-byte swizzle: the 16-byte chunk index within the
+// row (address bits 4 .. 3 + log2(RB/16)) XORed with address bits 7 .. .
+template <int RB>
+__device__ __forceinline__ uint32_t swz_off(uint32_t off) {
+    return off ^ (((off >> 7) & uint32_t(RB / 16 - 1)) << 4);
+}
+
 // Shared-memory layout of one CTA.
 template <class K, class Cfg, int MODE, bool TMA>
 struct Layout {
@@ -111,9 +138,12 @@ struct Layout {
     // stream compaction with staged values: each slot's values
     static constexpr int kVal =
         is_staged_select<K>::value ? Cfg::STAGES * Cfg::TILE * int(sizeof(Out)) : 0;
+    // (the ring starts the dynamic shared memory; swizzled tiles need
+    // 1024-byte boundaries, which every slot size keeps)
     static constexpr int off_in = 0;
     static constexpr int off_val = align_up_c(off_in + kIn, 128);
-    static constexpr int off_out = align_up_c(off_val + kVal, 128);
+    static constexpr int off_out =
+        align_up_c(off_val + kVal, Swz<K, Cfg, MODE, TMA>::OUT ? 1024 : 128);
     static constexpr int off_bits = align_up_c(off_out + kOut, 128);
     // carry hand-off ring (carry warps -> consumers), deeper than the tile ring
     // so that no input slot waits for a look-back
@@ -144,6 +174,12 @@ struct Layout {
     static_assert(off_in % 16 == 0 && off_val % 16 == 0 && off_out % 16 == 0 &&
                       off_bits % 16 == 0,
                   "ring");
+    static_assert(!Swz<K, Cfg, MODE, TMA>::IN ||
+                      (Cfg::TILE * int(sizeof(In))) % 1024 == 0,
+                  "swizzled input slots on 1024-byte boundaries");
+    static_assert(!Swz<K, Cfg, MODE, TMA>::OUT ||
+                      (off_out % 1024 == 0 && (32 * Cfg::ITEMS * int(sizeof(Out))) % 1024 == 0),
+                  "swizzled output regions on 1024-byte boundaries");
     static_assert(off_bar % 8 == 0 && off_tile % 8 == 0 && off_tr % 8 == 0 &&
                       off_agg % 8 == 0, "8-byte");
     static_assert(off_carry % 8 == 0 && off_sx % 8 == 0 && off_snt % 4 == 0, "8-byte");
@@ -254,35 +290,41 @@ __device__ __forceinline__ uint32_t chunk_rot(int lane) {
     }
 }
 
-// Thread-blocked load of ITEMS elements from a shared-memory tile.
-template <class E, int ITEMS>
-__device__ __forceinline__ void lds_blocked(const uint8_t *tile_smem, int tid,
+// Thread-blocked load of ITEMS elements (row `row` of a shared-memory
+// tile).  SW: the tile is swizzled (Swz), so chunk j of the row is read from
+// chunk j ^ f(row) and lands in order; otherwise the row is dense and the
+// chunks, read in the rotated order, are put back in order with selects.
+template <class E, int ITEMS, bool SW = false>
+__device__ __forceinline__ void lds_blocked(const uint8_t *tile_smem, int row,
                                             int lane, E (&e)[ITEMS]) {
     constexpr int BYTES = ITEMS * int(sizeof(E));
     constexpr int C = BYTES / 16;
     static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
-    const uint8_t *p = tile_smem + tid * BYTES;
-    const uint32_t xr = chunk_rot<C>(lane);
+    const uint8_t *p = tile_smem + row * BYTES;
+    const uint32_t xr = SW ? ((static_cast<uint32_t>(row) * BYTES) >> 7) & uint32_t(C - 1)
+                           : chunk_rot<C>(lane);
     uint4 t[C];
 #pragma unroll
     for (int j = 0; j < C; ++j)
         t[j] = *reinterpret_cast<const uint4 *>(p + 16 * (j ^ xr));
-    xor_permute<C>(t, xr);
+    if constexpr (!SW) xor_permute<C>(t, xr);
     unpack_chunks<E, ITEMS, C>(t, e);
 }
 
-// Thread-blocked store of ITEMS elements into a shared-memory region.
-template <class E, int ITEMS>
+// Thread-blocked store of ITEMS elements into row `idx` of a shared-memory
+// region (SW: the region is swizzled, as in lds_blocked).
+template <class E, int ITEMS, bool SW = false>
 __device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
                                             const E (&e)[ITEMS]) {
     constexpr int BYTES = ITEMS * int(sizeof(E));
     constexpr int C = BYTES / 16;
     static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
     uint8_t *p = region + idx * BYTES;
-    const uint32_t xr = chunk_rot<C>(lane);
+    const uint32_t xr = SW ? ((static_cast<uint32_t>(idx) * BYTES) >> 7) & uint32_t(C - 1)
+                           : chunk_rot<C>(lane);
     uint4 t[C];
     pack_chunks<E, ITEMS, C>(e, t);
-    xor_permute<C>(t, xr);
+    if constexpr (!SW) xor_permute<C>(t, xr);
 #pragma unroll
     for (int j = 0; j < C; ++j)
         *reinterpret_cast<uint4 *>(p + 16 * (j ^ xr)) = t[j];
@@ -378,7 +420,9 @@ struct TileReduce {
 // +0 and a -0 may precede it: only then (m1 == 0) the tile is searched for
 // its first zero.  Two integer min/max per element (bf16: per two elements,
 // 16-bit SIMD) instead of a compare-select chain with index tracking.
-template <class In, int TILE>
+// SWRB: the tile's row bytes when it is swizzled (0: dense); only the
+// search for the first zero depends on where each element sits.
+template <class In, int TILE, int SWRB = 0>
 __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane) {
     constexpr int WORDS = TILE * int(sizeof(In)) / 4;
     const uint4 *q4 = reinterpret_cast<const uint4 *>(tsm);
@@ -425,7 +469,11 @@ __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane
         const Bits *e = reinterpret_cast<const Bits *>(tsm);
         bits = 0u;
         for (int base = 0; base < TILE; base += 32) {
-            const uint32_t b = static_cast<uint32_t>(e[base + lane]);
+            int i = base + lane;
+            if constexpr (SWRB != 0)
+                i = static_cast<int>(swz_off<SWRB>(static_cast<uint32_t>(i) * sizeof(In)) /
+                                     sizeof(In));
+            const uint32_t b = static_cast<uint32_t>(e[i]);
             const uint32_t z = __ballot_sync(0xffffffffu, (b & MAG) == 0u);
             if (z) {
                 bits = __shfl_sync(0xffffffffu, b, __ffs(z) - 1);
@@ -466,7 +514,7 @@ __device__ __forceinline__ uint32_t packed_max_step(uint32_t w, uint32_t &R) {
 // ------------------------------------------------------------------ kernel
 template <class K, class Cfg, int MODE, bool TMA>
 __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB)
-    lscan_kernel(const ScanParams p) {
+    lscan_kernel(const __grid_constant__ ScanParams p) {
     using In = typename K::In;
     using Out = typename K::Out;
     using Acc = typename K::Acc;
@@ -487,6 +535,10 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     // split reduce: a second reducer warp after the carry warps
     constexpr bool SPLIT = split_reduce<K, Cfg, MODE, TMA>();
     constexpr int W_RED2 = W_CARRY + NC;
+    // full tiles of x in and of y out as swizzled tensor copies (Swz)
+    constexpr bool SWI = Swz<K, Cfg, MODE, TMA>::IN;
+    constexpr bool SWO = Swz<K, Cfg, MODE, TMA>::OUT;
+    constexpr int RBI = Swz<K, Cfg, MODE, TMA>::RBI;
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
     // Each carry warp must see every phase of the ring entries it waits on
@@ -495,7 +547,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     // NC <= ST also keeps the terminator hand-off below safe.
     static_assert(NC >= 1 && ST % NC == 0, "carry warps must own whole entries");
 
-    extern __shared__ __align__(128) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem[];
     // Tile slots (input data, per slot s = k % ST of ring use k) and the
     // carry ring (per entry c = k % CR): the carry warp only touches the
     // ring, so it never holds an input slot while it looks back.
@@ -558,7 +610,14 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     const In *__restrict__ x = static_cast<const In *>(p.x);
     Out *__restrict__ y = static_cast<Out *>(p.y);
 
-    if (warp == W_PROD) {
+    // The swizzle places chunks by shared-memory address bits 4 .. 9, so
+    // the tile ring and the output staging start on 1024-byte boundaries;
+    // should the dynamic shared memory not, nothing runs and the launch
+    // reports it (its CTAs still take part in the launch-end count).
+    const bool misaligned = (SWI || SWO) && (smem_addr(smem) & 1023u) != 0u;
+    if (misaligned) {
+        if (tid == 0) note_gave_up(wc, DEV_ERR_SMEM_ALIGN);
+    } else if (warp == W_PROD) {
         // ============================ producer warp ============================
         uint32_t armed_mask = 0;  // slots whose last phase was a bulk copy
         uint32_t par_mask = 0;    // parity of each slot's last bulk copy
@@ -676,7 +735,14 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     // start the copy now; the slot's phase also needs the
                     // arrival below, made once the head bitmap is written
                     mbar_expect_tx(&full[s], bulk_bytes + vbulk);
-                    bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bulk_bytes, &full[s]);
+                    if (SWI && nt == TILE) {
+                        // the tile is boxes t CW .. t CW + CW - 1 of x's map
+                        tensor_g2s_3d(smem + L::off_in + s * TILE * sizeof(In), &p.tm_x, 0, 0,
+                                      static_cast<int>(t * CW), &full[s]);
+                    } else {
+                        bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bulk_bytes,
+                                 &full[s]);
+                    }
                     if (vbulk > 0u)
                         bulk_g2s(smem + L::off_val + s * TILE * sizeof(Out), tv, vbulk, &full[s]);
                     armed_mask |= 1u << s;
@@ -817,7 +883,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 if constexpr (has_raw_max<K>::value && !SG && TMA) {
                     if (nt == TILE) {
                         // whole tile, one value: every lane holds it
-                        r.v = raw_float_max_tile<In, TILE>(
+                        r.v = raw_float_max_tile<In, TILE, SWI ? RBI : 0>(
                             smem + L::off_in + s * TILE * sizeof(In), lane);
                         r.i = 0;
                         return;
@@ -836,7 +902,9 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     const int c0 = second ? NCH / 2 : 0;
                     const int c1 = (SPLIT && !second) ? NCH / 2 : NCH;
                     for (int c = c0 + lane; c < c1; c += 32) {
-                        const uint4 q = *reinterpret_cast<const uint4 *>(tsm + 16 * c);
+                        const uint32_t qo = SWI ? swz_off<RBI>(16u * static_cast<uint32_t>(c))
+                                                : 16u * static_cast<uint32_t>(c);
+                        const uint4 q = *reinterpret_cast<const uint4 *>(tsm + qo);
                         const uint4 qa[1] = {q};
                         In e[EPC];
                         unpack_chunks<In, EPC, 1>(qa, e);
@@ -1003,8 +1071,8 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
             constexpr int NW = ITEMS / 2;  // packed words per thread
             uint32_t w[NW];
             if (TMA && full_tile) {
-                lds_blocked<uint32_t, NW>(smem + L::off_in + s * TILE * sizeof(In), tid, lane,
-                                          w);
+                lds_blocked<uint32_t, NW, SWI>(smem + L::off_in + s * TILE * sizeof(In), tid,
+                                               lane, w);
             } else {
                 const uint16_t *src =
                     TMA ? reinterpret_cast<const uint16_t *>(smem + L::off_in +
@@ -1127,11 +1195,15 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     }
                 }
                 __syncwarp();
-                sts_blocked<uint32_t, NW>(region, lane, lane, o);
+                sts_blocked<uint32_t, NW, SWO>(region, lane, lane, o);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
+                    if constexpr (SWO) {
+                        tensor_s2g_3d(&p.tm_y, region, 0, 0, static_cast<int>(t * CW + warp));
+                    } else {
+                        bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
+                    }
                     bulk_commit();
                 }
             } else if (TMA && OS >= 1) {
@@ -1183,8 +1255,8 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
             Acc v[ITEMS];
             if (TMA && full_tile) {
                 In xv[ITEMS];
-                lds_blocked<In, ITEMS>(smem + L::off_in + s * TILE * sizeof(In),
-                                       tid, lane, xv);
+                lds_blocked<In, ITEMS, SWI>(smem + L::off_in + s * TILE * sizeof(In),
+                                            tid, lane, xv);
 #pragma unroll
                 for (int i = 0; i < ITEMS; ++i) v[i] = K::load(xv[i]);
             } else {
@@ -1427,11 +1499,16 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     }
                 }
                 __syncwarp();
-                sts_blocked<Out, ITEMS>(region, lane, lane, o);
+                sts_blocked<Out, ITEMS, SWO>(region, lane, lane, o);
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
+                    if constexpr (SWO) {
+                        // this warp's rows: box t CW + warp of y's map
+                        tensor_s2g_3d(&p.tm_y, region, 0, 0, static_cast<int>(t * CW + warp));
+                    } else {
+                        bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
+                    }
                     bulk_commit();
                 }
             } else if (TMA && OS >= 1) {

@@ -281,6 +281,45 @@ def test_many_launches_epoch_and_ticket_rearm():
             assert_matches("add", "i32", x, to_host(outs[rep * len(xs) + i]))
 
 
+def test_new_host_thread_on_a_used_stream():
+    """A host thread whose first library call reuses a stream (and so its
+    scratch) set up by another thread: it makes no CUDA call that binds a
+    context before the launch builds the tile copies' tensor maps, which
+    must still work.  Every kind's default configuration, full tiles and a
+    ragged tail."""
+    import threading
+    s = torch.cuda.Stream()
+    rng = np.random.default_rng(23)
+    cases = [("add", "i32"), ("max", "f32"), ("add", "f32"), ("max", "bf16"),
+             ("add", "f64")]
+    xs = [random_array(dt, (1 << 21) + 13, rng, kind="full") for _, dt in cases]
+    ds = [to_device(x, dt) for x, (_, dt) in zip(xs, cases)]
+    ys = [torch.empty(d.shape[0], dtype=out_torch_dtype(op, dt, False), device="cuda")
+          for d, (op, dt) in zip(ds, cases)]
+    with torch.cuda.stream(s):
+        run_c_abi("add", "i32", ds[0], True, y_dev=ys[0])  # scratch set up here
+    s.synchronize()
+    errs = []
+
+    def worker():
+        try:
+            for d, y, (op, dt) in zip(ds, ys, cases):
+                st = _lib.lscan_scan(LOP[op], LDT[dt], 1, d.data_ptr(),
+                                     y.data_ptr(), d.shape[0], None, s.cuda_stream)
+                assert st == _lib.LSCAN_OK, (op, dt, _lib.strerror(st))
+        except Exception as e:  # reported on the main thread
+            errs.append(e)
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert not errs, errs
+    s.synchronize()
+    assert _lib.lscan_stream_status(s.cuda_stream) == _lib.LSCAN_OK
+    for x, y, (op, dt) in zip(xs, ys, cases):
+        assert_matches(op, dt, x, to_host(y))
+
+
 def test_concurrent_streams_independent_scratch():
     streams = [torch.cuda.Stream() for _ in range(4)]
     rng = np.random.default_rng(5)

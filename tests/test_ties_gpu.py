@@ -21,7 +21,8 @@ import paper_1604_04815_gb300 as lscan
 from gpu_util import (assert_matches, run_c_abi, to_device, to_host, LDT, LOP,
                       TEST_WAIT_NS)
 from paper_1604_04815_gb300 import _lib
-from paper_1604_04815_gb300.workloads import ties_array, offsets_from_lengths
+from paper_1604_04815_gb300.workloads import (f32_to_bf16_bits, ties_array,
+                                              offsets_from_lengths)
 
 pytestmark = pytest.mark.gpu
 
@@ -78,6 +79,41 @@ def test_ties_every_config(dtype, inclusive):
             y = run_c_abi("max", dtype, to_device(x, dtype), inclusive,
                           config=config, carry=carry)
             assert_matches("max", dtype, x, to_host(y), inclusive)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_ties_swizzled_tile_order(dtype):
+    """Full tiles of a single array sit in shared memory with their 16-byte
+    chunks swizzled by row (a row is one thread's elements), and the fp32 /
+    bf16 max reducer searches a tile whose maximum is a zero for its first
+    zero.  Here a -0 opens row 4 of tile 1 and a +0 sits in the chunk of the
+    same row that the swizzle places first in shared memory: element order
+    and shared-memory order disagree, and only element order gives -0 as the
+    tile's total and as every later output."""
+    isz = 2 if dtype == "bf16" else 4
+    epc = 16 // isz
+    for config in range(1, _lib.lscan_num_configs() + 1):
+        info = _lib.lscan_config_info(config, LDT[dtype])
+        tile, items = info["tile"], info["items"]
+        rb = items * isz                       # row bytes
+        rows = max(rb // 16, 1)                # chunks per row
+        xr = ((4 * rb) >> 7) & (rows - 1)      # row 4's chunk XOR
+        later = xr if xr else 1                # (16-byte rows: the next row)
+        n = 3 * tile
+        x = np.full(n, -1.0, dtype=np.float32)
+        first = tile + 4 * items
+        second = first + later * epc
+        x[first] = -0.0
+        x[second] = 0.0
+        if dtype == "bf16":
+            x = f32_to_bf16_bits(x)
+        for inclusive in (True, False):
+            y = run_c_abi("max", dtype, to_device(x, dtype), inclusive,
+                          config=config)
+            got = to_host(y)
+            assert_matches("max", dtype, x, got, inclusive)
+            # the zero after both is -0's bits
+            assert _bits(got[-1:])[0] == _bits(_neg_zero(dtype))[0], (config, inclusive)
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
