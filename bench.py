@@ -108,17 +108,17 @@ def _kernel_source_hash():
 # reported traffic null until it is measured again (files listed in
 # _NOT_SCAN_SOURCES excepted).
 _TRAFFIC = {
-    "kernel_source_hash": "20238651f5923232",
+    "kernel_source_hash": "86bf72a9d9aaa39f",
     "bytes_per_launch": {  # (case, tile configuration)
-        ("i32_add", 6): 1077993216 + 1019591936,
-        ("i32_max", 6): 1078065408 + 1016542464,
-        ("f32_add", 6): 1078019840 + 1016318208,
-        ("i32_add", 8): 1075976704 + 1018890496,
-        ("i32_max", 8): 1076095744 + 1016697856,
-        ("f32_add", 8): 1075994368 + 1015994112,
-        ("i32_add", 17): 1075382272 + 1018702592,
-        ("i32_max", 17): 1075233024 + 1016229376,
-        ("f32_add", 17): 1075398400 + 1015774464,
+        ("i32_add", 6): 1077992192 + 1019292928,
+        ("i32_max", 6): 1078018816 + 1016235264,
+        ("f32_add", 6): 1078023936 + 1016182272,
+        ("i32_add", 8): 1075898368 + 1018773760,
+        ("i32_max", 8): 1076087552 + 1015642368,
+        ("f32_add", 8): 1075936768 + 1016081920,
+        ("i32_add", 17): 1075217408 + 1018725376,
+        ("i32_max", 17): 1075224576 + 1015169792,
+        ("f32_add", 17): 1075270144 + 1015724544,
     },
 }
 

@@ -29,10 +29,10 @@ struct KernelEntry {
     int car_words = 0; // 64-bit status words per tile slot
     int in_size = 0;
     int out_size = 0;
-    // row bytes (32, 64 or 128) of the swizzled tensor copies of full tiles
-    // of x (into the ring) and of y (out of the staging), 0 where the
-    // variant uses plain bulk copies; the launch encodes ScanParams::tm_x /
-    // tm_y from them
+    // thread row bytes (32, 64 or 128) where full tiles of x (into the
+    // ring) and of y (out of the staging) move as 128-byte-swizzled tensor
+    // copies, 0 where the variant uses plain bulk copies; the launch encodes
+    // ScanParams::tm_x / tm_y when they are set
     int swz_in = 0;
     int swz_out = 0;
 };

@@ -114,28 +114,23 @@ EncodeTiledFn encode_tiled() {
     return g_encode;
 }
 
-// Tensor map of `bytes` bytes at `base` (16-byte aligned) seen as rows of rb
-// bytes (32, 64 or 128) in boxes of 32 rows: dimensions [boxes][32][rb],
-// complete boxes only (a tile that reaches past the last one is never copied
-// through the map).  One copy moves `boxes_per_copy` consecutive boxes,
-// laid out in shared memory with the rb-byte swizzle.
-bool encode_row_map(CUtensorMap *m, const void *base, uint64_t bytes, int rb,
-                    int boxes_per_copy) {
+// Tensor map of `bytes` bytes at `base` (16-byte aligned) seen as 1024-byte
+// blocks of eight 128-byte lines: dimensions [blocks][8][128], complete
+// blocks only (a tile that reaches past the last one is never copied through
+// the map).  One copy moves `blocks_per_copy` consecutive blocks, laid out in
+// shared memory with the 128-byte swizzle.
+bool encode_block_map(CUtensorMap *m, const void *base, uint64_t bytes, int blocks_per_copy) {
     EncodeTiledFn f = encode_tiled();
-    if (f == nullptr || (rb != 32 && rb != 64 && rb != 128)) return false;
-    const uint64_t boxes = bytes / (32u * static_cast<uint64_t>(rb));
-    if (boxes == 0 || boxes > static_cast<uint64_t>(INT32_MAX)) return false;
-    const cuuint64_t dim[3] = {static_cast<cuuint64_t>(rb), 32u, boxes};
-    const cuuint64_t stride[2] = {static_cast<cuuint64_t>(rb), 32u * static_cast<cuuint64_t>(rb)};
-    const cuuint32_t box[3] = {static_cast<cuuint32_t>(rb), 32u,
-                               static_cast<cuuint32_t>(boxes_per_copy)};
+    if (f == nullptr || blocks_per_copy < 1 || blocks_per_copy > 256) return false;
+    const uint64_t blocks = bytes / 1024u;
+    if (blocks == 0 || blocks > static_cast<uint64_t>(INT32_MAX)) return false;
+    const cuuint64_t dim[3] = {128u, 8u, blocks};
+    const cuuint64_t stride[2] = {128u, 1024u};
+    const cuuint32_t box[3] = {128u, 8u, static_cast<cuuint32_t>(blocks_per_copy)};
     const cuuint32_t step[3] = {1u, 1u, 1u};
-    const CUtensorMapSwizzle sw = rb == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
-                                  : rb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
-                                             : CU_TENSOR_MAP_SWIZZLE_32B;
     auto encode = [&] {
         return f(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3u, const_cast<void *>(base), dim, stride,
-                 box, step, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                 box, step, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     };
     CUresult r = encode();
@@ -367,14 +362,14 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
     std::memset(&p.tm_y, 0, sizeof(p.tm_y));
     if (ls.mode == MODE_SINGLE && ls.n >= e.tile) {
         // full tiles exist: their swizzled copies go through the maps (a
-        // tile is e.cwarps boxes of x; each consumer warp stores one box of y)
+        // tile of x per copy; each consumer warp stores its rows of y)
         if (e.swz_in != 0 &&
-            !encode_row_map(&p.tm_x, ls.x, static_cast<uint64_t>(ls.n) * e.in_size, e.swz_in,
-                            e.cwarps))
+            !encode_block_map(&p.tm_x, ls.x, static_cast<uint64_t>(ls.n) * e.in_size,
+                              e.tile * e.in_size / 1024))
             return LSCAN_ERR_CUDA;
         if (e.swz_out != 0 &&
-            !encode_row_map(&p.tm_y, ls.y, static_cast<uint64_t>(ls.n) * e.out_size, e.swz_out,
-                            1))
+            !encode_block_map(&p.tm_y, ls.y, static_cast<uint64_t>(ls.n) * e.out_size,
+                              32 * e.items * e.out_size / 1024))
             return LSCAN_ERR_CUDA;
     }
     void *args[] = {&p};

@@ -40,8 +40,8 @@ lscan_status load_file(const char *path);
 // the kinds whose best depends on the size: 4- and 8-byte kinds take
 // configuration 8 (32 KiB tiles of 32 items x 8 warps, 64-byte status
 // slots) from 2^22 up, the compensated fp32 add 64 KiB tiles (12) from 2^25;
-// bf16 takes 48, 56 or 16 KiB tiles (17, 12, 13) from 2^25 up, 3-stage
-// 32 KiB tiles (11) from 2^23 and smaller ones below.
+// bf16 takes 48, 56, 32 or 16 KiB tiles (17, 12, 11, 13) from 2^25 up,
+// 3-stage 32 KiB tiles (11) from 2^23 and smaller ones below.
 int default_variant(int kind, int mode, int size_cls = 28) {
     const bool single = mode == MODE_SINGLE;
     switch (kind) {
@@ -53,16 +53,16 @@ int default_variant(int kind, int mode, int size_cls = 28) {
         case KIND_F32_ADD_PLAIN: return single ? 8 : 6;  // 6214
         case KIND_F32_ADD_F64: return single ? 12 : 5;   // 5780
         case KIND_F32_ADD_DF: return single ? 8 : 5;     // 5960, 5327
-        case KIND_F32_ADD_COMP: return single ? (size_cls >= 25 ? 12 : 8) : 3;  // 5127
+        case KIND_F32_ADD_COMP: return single ? (size_cls >= 25 ? 12 : 8) : 3;  // 5243, 4804
         case KIND_BF16_ADD_PLAIN_F32: return single ? 13 : 4;  // 6172
         case KIND_BF16_ADD_F64_F32: return single ? (size_cls >= 25 ? 12 : 7) : 5;  // 5789
         case KIND_BF16_ADD_DF_F32:  // 5835
             return single ? (size_cls >= 25 ? 12 : size_cls >= 23 ? 11 : 13) : 2;
-        case KIND_BF16_ADD_COMP_F32: return single ? 13 : 4;  // 4031
+        case KIND_BF16_ADD_COMP_F32: return single ? (size_cls >= 25 ? 11 : 13) : 4;  // 4007
         case KIND_BF16_ADD_PLAIN_BF16: return single ? (size_cls >= 25 ? 12 : 13) : 4;  // 4820
         case KIND_BF16_ADD_F64_BF16: return single ? (size_cls >= 25 ? 17 : 11) : 5;  // 4541
         case KIND_BF16_ADD_DF_BF16: return single ? (size_cls >= 25 ? 12 : 11) : 5;  // 4555
-        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 5 : 13) : 4;  // 2738
+        case KIND_BF16_ADD_COMP_BF16: return single ? (size_cls >= 25 ? 11 : 13) : 4;  // 2831
         case KIND_I64_ADD: return single ? 8 : 5;      // 5883, 5625
         case KIND_I64_MAX: return single ? 8 : 5;      // 5651
         case KIND_F64_MAX: return single ? 8 : 4;      // 3414

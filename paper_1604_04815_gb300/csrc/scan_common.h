@@ -81,10 +81,10 @@ struct ScanParams {
     // memory mapped for the device) and clears it, so a caller polling for
     // completion reads it without a device-to-host copy
     uint32_t *err_host;
-    // Single arrays, bulk-copy variants whose rows are 32, 64 or 128 bytes:
-    // x and y viewed as [boxes][32 rows][row bytes] (complete 32-row boxes
-    // only), from which whole tiles are copied with the row-width swizzle
-    // (encoded by the host at launch; unused otherwise)
+    // Single arrays, bulk-copy variants whose thread rows are 32, 64 or 128
+    // bytes: x and y viewed as [1024-byte blocks][8][128 bytes] (complete
+    // blocks only), through which full tiles are copied with the 128-byte
+    // swizzle (encoded by the host at launch; unused otherwise)
     CUtensorMap tm_x;
     CUtensorMap tm_y;
 };

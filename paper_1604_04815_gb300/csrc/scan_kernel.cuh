@@ -81,29 +81,42 @@ struct alignas(16) WarpTotal {
     uint32_t f;
 };
 
-// Kinds whose tile aggregate two reducer warps fold (halves of a full tile
-// in shared memory; single arrays) in configurations of one CTA per SM --
-// with two CTAs per SM the second CTA's reducer already sits on another
-// sub-partition, and the hand-off costs more than it saves (measured) --
-// and the CTA's thread count.
+// Kinds whose tile aggregate several reducer warps fold (consecutive parts
+// of a full tile in shared memory; single arrays) in configurations of one
+// CTA per SM -- with two CTAs per SM the second CTA's reducer already sits
+// on another sub-partition, and the hand-off costs more than it saves
+// (measured) -- how many, and the CTA's thread count.  Three parts put one
+// reducer warp on each SM sub-partition but the carry warp's; two where a
+// third warp would pass the 1024-thread limit of a CTA.
 template <class K, class Cfg, int MODE, bool TMA>
 constexpr bool split_reduce() {
     return has_split_reduce<K>::value && MODE == MODE_SINGLE && TMA && Cfg::MINB == 1;
 }
 template <class K, class Cfg, int MODE, bool TMA>
+constexpr int reduce_parts() {
+    if constexpr (!split_reduce<K, Cfg, MODE, TMA>()) {
+        return 1;
+    } else {
+        return Cfg::THREADS + 64 <= 1024 ? 3 : 2;
+    }
+}
+template <class K, class Cfg, int MODE, bool TMA>
 constexpr int kernel_threads() {
-    return Cfg::THREADS + (split_reduce<K, Cfg, MODE, TMA>() ? 32 : 0);
+    constexpr int n = Cfg::THREADS + 32 * (reduce_parts<K, Cfg, MODE, TMA>() - 1);
+    static_assert(n <= 1024, "a CTA holds at most 1024 threads");
+    return n;
 }
 
 // Full tiles of a single array move between HBM and shared memory as tensor
-// copies with the swizzle of their row width: 16-byte chunk j of row r (one
-// consumer thread's elements) of a 1024-byte aligned tile sits at chunk
-// j ^ f(r), f(r) taken from address bits 7.. (swz_off).  Each quarter-warp's
-// 16-byte accesses then cover all 32 banks while every thread reads and
-// writes its chunks in element order: no register permutation after the
-// load or before the store.  Rows of 32, 64 or 128 bytes; the other
-// variants (batched modes, stream compaction, 16-byte rows, direct stores)
-// keep plain bulk copies and the XOR-rotated accesses.
+// copies with the 128-byte swizzle: in every 1024-byte block of a 1024-byte
+// aligned tile, the 16-byte chunk at byte offset b sits at b ^ (((b >> 7) &
+// 7) << 4) (swz128).  With thread rows (one consumer thread's elements) of
+// 32, 64 or 128 bytes, the eight chunks a quarter-warp reads or writes at
+// once then fall in eight distinct 16-byte bank groups while every thread
+// reads and writes its chunks in element order: no register permutation
+// after the load or before the store.  The other variants (batched modes,
+// stream compaction, 16-byte rows, direct stores) keep plain bulk copies
+// and the XOR-rotated accesses.
 template <class K, class Cfg, int MODE, bool TMA>
 struct Swz {
     static constexpr int RBI = Cfg::ITEMS * int(sizeof(typename K::In));
@@ -112,14 +125,15 @@ struct Swz {
     static constexpr bool IN = kAny && (RBI == 32 || RBI == 64 || RBI == 128);
     static constexpr bool OUT =
         kAny && Cfg::OSTAGES >= 1 && (RBO == 32 || RBO == 64 || RBO == 128);
+    // 1024-byte blocks per input tile and per consumer warp's output rows
+    static constexpr int kInBlocks = Cfg::TILE * int(sizeof(typename K::In)) / 1024;
+    static constexpr int kOutWarpBlocks = 32 * RBO / 1024;
 };
 
-// Where the byte at offset `off` of a 1024-byte aligned tile with RB-byte
-// rows lives under the RB-byte swizzle: the 16-byte chunk index within the
-// row (address bits 4 .. 3 + log2(RB/16)) XORed with address bits 7 .. .
-template <int RB>
-__device__ __forceinline__ uint32_t swz_off(uint32_t off) {
-    return off ^ (((off >> 7) & uint32_t(RB / 16 - 1)) << 4);
+// Where the byte at offset `off` of a 1024-byte aligned tile lives under the
+// 128-byte swizzle.
+__device__ __forceinline__ uint32_t swz128(uint32_t off) {
+    return off ^ (((off >> 7) & 7u) << 4);
 }
 
 // Shared-memory layout of one CTA.
@@ -164,10 +178,13 @@ struct Layout {
     static constexpr int off_wtot = align_up_c(off_snt + 4 * Cfg::STAGES, 16);
     // warp totals, double-buffered by tile parity (one barrier per tile)
     static constexpr int off_abort = off_wtot + 2 * 16 * Cfg::CWARPS;
-    // split reduce: the second reducer warp's half-tile totals (two, by ring
+    // split reduce: the other reducer warps' part totals (two sets, by ring
     // use parity) and mbarriers half_done[2], half_free[2]
     static constexpr int off_half = align_up_c(off_abort + 16, 16);
-    static constexpr int off_hbar = off_half + 2 * 16;
+    static constexpr int off_hbar =
+        off_half + 2 * 16 * (reduce_parts<K, Cfg, MODE, TMA>() > 1
+                                 ? reduce_parts<K, Cfg, MODE, TMA>() - 1
+                                 : 1);
     static constexpr int bytes = align_up_c(off_hbar + 4 * 8, 128);
     // every field is naturally aligned (a misaligned 8-byte shared access
     // faults the launch)
@@ -291,23 +308,31 @@ __device__ __forceinline__ uint32_t chunk_rot(int lane) {
 }
 
 // Thread-blocked load of ITEMS elements (row `row` of a shared-memory
-// tile).  SW: the tile is swizzled (Swz), so chunk j of the row is read from
-// chunk j ^ f(row) and lands in order; otherwise the row is dense and the
-// chunks, read in the rotated order, are put back in order with selects.
+// tile).  SW: the tile is swizzled (swz128), so chunk j of the row is read
+// where the swizzle put it and lands in order; otherwise the row is dense and
+// the chunks, read in the rotated order, are put back in order with selects.
 template <class E, int ITEMS, bool SW = false>
 __device__ __forceinline__ void lds_blocked(const uint8_t *tile_smem, int row,
                                             int lane, E (&e)[ITEMS]) {
     constexpr int BYTES = ITEMS * int(sizeof(E));
     constexpr int C = BYTES / 16;
     static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
-    const uint8_t *p = tile_smem + row * BYTES;
-    const uint32_t xr = SW ? ((static_cast<uint32_t>(row) * BYTES) >> 7) & uint32_t(C - 1)
-                           : chunk_rot<C>(lane);
     uint4 t[C];
+    if constexpr (SW) {
+        // the row's chunks stay inside one 128-byte line: one XOR mask
+        const uint32_t base = static_cast<uint32_t>(row) * BYTES;
+        const uint32_t xm = ((base >> 7) & 7u) << 4;
 #pragma unroll
-    for (int j = 0; j < C; ++j)
-        t[j] = *reinterpret_cast<const uint4 *>(p + 16 * (j ^ xr));
-    if constexpr (!SW) xor_permute<C>(t, xr);
+        for (int j = 0; j < C; ++j)
+            t[j] = *reinterpret_cast<const uint4 *>(tile_smem + ((base + 16u * j) ^ xm));
+    } else {
+        const uint8_t *p = tile_smem + row * BYTES;
+        const uint32_t xr = chunk_rot<C>(lane);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            t[j] = *reinterpret_cast<const uint4 *>(p + 16 * (j ^ xr));
+        xor_permute<C>(t, xr);
+    }
     unpack_chunks<E, ITEMS, C>(t, e);
 }
 
@@ -319,15 +344,22 @@ __device__ __forceinline__ void sts_blocked(uint8_t *region, int idx, int lane,
     constexpr int BYTES = ITEMS * int(sizeof(E));
     constexpr int C = BYTES / 16;
     static_assert(C >= 1 && C <= 8 && (C & (C - 1)) == 0, "1..8 chunks");
-    uint8_t *p = region + idx * BYTES;
-    const uint32_t xr = SW ? ((static_cast<uint32_t>(idx) * BYTES) >> 7) & uint32_t(C - 1)
-                           : chunk_rot<C>(lane);
     uint4 t[C];
     pack_chunks<E, ITEMS, C>(e, t);
-    if constexpr (!SW) xor_permute<C>(t, xr);
+    if constexpr (SW) {
+        const uint32_t base = static_cast<uint32_t>(idx) * BYTES;
+        const uint32_t xm = ((base >> 7) & 7u) << 4;
 #pragma unroll
-    for (int j = 0; j < C; ++j)
-        *reinterpret_cast<uint4 *>(p + 16 * (j ^ xr)) = t[j];
+        for (int j = 0; j < C; ++j)
+            *reinterpret_cast<uint4 *>(region + ((base + 16u * j) ^ xm)) = t[j];
+    } else {
+        uint8_t *p = region + idx * BYTES;
+        const uint32_t xr = chunk_rot<C>(lane);
+        xor_permute<C>(t, xr);
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            *reinterpret_cast<uint4 *>(p + 16 * (j ^ xr)) = t[j];
+    }
 }
 
 // The carry-in of a single-array scan: the caller's output-type element, a
@@ -420,9 +452,9 @@ struct TileReduce {
 // +0 and a -0 may precede it: only then (m1 == 0) the tile is searched for
 // its first zero.  Two integer min/max per element (bf16: per two elements,
 // 16-bit SIMD) instead of a compare-select chain with index tracking.
-// SWRB: the tile's row bytes when it is swizzled (0: dense); only the
-// search for the first zero depends on where each element sits.
-template <class In, int TILE, int SWRB = 0>
+// SW: the tile is swizzled (swz128); only the search for the first zero
+// depends on where each element sits.
+template <class In, int TILE, bool SW = false>
 __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane) {
     constexpr int WORDS = TILE * int(sizeof(In)) / 4;
     const uint4 *q4 = reinterpret_cast<const uint4 *>(tsm);
@@ -470,9 +502,8 @@ __device__ __forceinline__ float raw_float_max_tile(const uint8_t *tsm, int lane
         bits = 0u;
         for (int base = 0; base < TILE; base += 32) {
             int i = base + lane;
-            if constexpr (SWRB != 0)
-                i = static_cast<int>(swz_off<SWRB>(static_cast<uint32_t>(i) * sizeof(In)) /
-                                     sizeof(In));
+            if constexpr (SW)
+                i = static_cast<int>(swz128(static_cast<uint32_t>(i) * sizeof(In)) / sizeof(In));
             const uint32_t b = static_cast<uint32_t>(e[i]);
             const uint32_t z = __ballot_sync(0xffffffffu, (b & MAG) == 0u);
             if (z) {
@@ -532,13 +563,15 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     constexpr int CR = L::CR;
     constexpr int SLOT = status_slot_words<K, Cfg>();  // status words per tile
     constexpr int W_PROD = CW, W_RED = CW + 1, W_CARRY = CW + 2;  // .. + NC - 1
-    // split reduce: a second reducer warp after the carry warps
+    // split reduce: NRP - 1 more reducer warps after the carry warps
     constexpr bool SPLIT = split_reduce<K, Cfg, MODE, TMA>();
+    constexpr int NRP = reduce_parts<K, Cfg, MODE, TMA>();
     constexpr int W_RED2 = W_CARRY + NC;
     // full tiles of x in and of y out as swizzled tensor copies (Swz)
     constexpr bool SWI = Swz<K, Cfg, MODE, TMA>::IN;
     constexpr bool SWO = Swz<K, Cfg, MODE, TMA>::OUT;
-    constexpr int RBI = Swz<K, Cfg, MODE, TMA>::RBI;
+    constexpr int kInBlocks = Swz<K, Cfg, MODE, TMA>::kInBlocks;
+    constexpr int kOutWarpBlocks = Swz<K, Cfg, MODE, TMA>::kOutWarpBlocks;
     static_assert(ITEMS <= 32 && (32 % ITEMS) == 0, "head bits in one word");
     static_assert(OS >= 0 && OS <= 2, "0 (direct stores), 1 or 2 staging buffers");
     // Each carry warp must see every phase of the ring entries it waits on
@@ -568,7 +601,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     WarpTotal<Acc> *wtot = reinterpret_cast<WarpTotal<Acc> *>(smem + L::off_wtot);
     volatile uint32_t *abort_s = reinterpret_cast<uint32_t *>(smem + L::off_abort);
     uint32_t *bits = reinterpret_cast<uint32_t *>(smem + L::off_bits);
-    Acc *half_s = reinterpret_cast<Acc *>(smem + L::off_half);         // [2]
+    Acc *half_s = reinterpret_cast<Acc *>(smem + L::off_half);   // [2][NRP - 1]
     uint64_t *half_done = reinterpret_cast<uint64_t *>(smem + L::off_hbar);  // [2]
     uint64_t *half_free = half_done + 2;                                 // [2]
     const In *volatile *slot_x = reinterpret_cast<const In *volatile *>(smem + L::off_sx);
@@ -582,7 +615,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
     if (tid == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW + 1 + (SPLIT ? 1 : 0));  // consumer warps + reducer(s)
+            mbar_init(&empty[s], CW + NRP);  // consumer warps + reducer warps
             tile_of[s] = INT64_MAX;
             inner_s[s] = 0;
         }
@@ -596,7 +629,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
             stop_s[c] = 0;
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&half_done[b], 1);
+            mbar_init(&half_done[b], NRP > 1 ? NRP - 1 : 1);
             mbar_init(&half_free[b], 1);
         }
         *abort_s = 0;
@@ -736,9 +769,9 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     // arrival below, made once the head bitmap is written
                     mbar_expect_tx(&full[s], bulk_bytes + vbulk);
                     if (SWI && nt == TILE) {
-                        // the tile is boxes t CW .. t CW + CW - 1 of x's map
+                        // the tile is 1024-byte blocks t kInBlocks .. of x's map
                         tensor_g2s_3d(smem + L::off_in + s * TILE * sizeof(In), &p.tm_x, 0, 0,
-                                      static_cast<int>(t * CW), &full[s]);
+                                      static_cast<int>(t * kInBlocks), &full[s]);
                     } else {
                         bulk_g2s(smem + L::off_in + s * TILE * sizeof(In), tx, bulk_bytes,
                                  &full[s]);
@@ -838,16 +871,17 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 if (armed_mask & (1u << s))
                     (void)wait_phase(&full[s], (par_mask >> s) & 1u, wc);
         }
-    } else if (warp == W_RED || (SPLIT && warp == W_RED2)) {
+    } else if (warp == W_RED || (SPLIT && warp >= W_RED2 && warp < W_RED2 + NRP - 1)) {
         // ======================= reducer warp =========================
         // Publishes each tile's aggregate as soon as its data lands, so the
         // carry of later tiles never waits on this CTA's consumer queue.
-        // Split reduce: the second reducer warp folds the second half of a
-        // full tile and hands its total to the first (half_done), which
-        // combines the halves in order and publishes; the first frees the
-        // hand-off buffer (half_free) for the use two tiles later.  Both
+        // Split reduce: reducer warp q > 0 folds part q of a full tile and
+        // hands its total to the first (half_done, one arrival per part),
+        // which combines the parts in order and publishes; the first frees
+        // the hand-off buffers (half_free) for the use two tiles later.  All
         // waits are bounded like every other.
-        const bool second = SPLIT && warp == W_RED2;
+        const int part = (SPLIT && warp != W_RED) ? warp - W_RED2 + 1 : 0;
+        const bool second = part > 0;
         for (int64_t k = 0;; ++k) {
             const int s = static_cast<int>(k % ST);
             const bool ok = wait_phase(&full[s], static_cast<uint32_t>((k / ST) & 1), wc);
@@ -883,7 +917,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 if constexpr (has_raw_max<K>::value && !SG && TMA) {
                     if (nt == TILE) {
                         // whole tile, one value: every lane holds it
-                        r.v = raw_float_max_tile<In, TILE, SWI ? RBI : 0>(
+                        r.v = raw_float_max_tile<In, TILE, SWI>(
                             smem + L::off_in + s * TILE * sizeof(In), lane);
                         r.i = 0;
                         return;
@@ -899,10 +933,13 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
 #pragma unroll
                     for (int u = 0; u < EPC; ++u) ra[u].init();
                     constexpr int NCH = TILE / EPC;  // 16-byte chunks
-                    const int c0 = second ? NCH / 2 : 0;
-                    const int c1 = (SPLIT && !second) ? NCH / 2 : NCH;
+                    // parts start on 128-byte lines: eight consecutive
+                    // chunks of one line fill the 32 banks once (swizzled or
+                    // not); eight that straddle two lines may collide
+                    const int c0 = part * (NCH / 8) / NRP * 8;
+                    const int c1 = (part + 1) * (NCH / 8) / NRP * 8;
                     for (int c = c0 + lane; c < c1; c += 32) {
-                        const uint32_t qo = SWI ? swz_off<RBI>(16u * static_cast<uint32_t>(c))
+                        const uint32_t qo = SWI ? swz128(16u * static_cast<uint32_t>(c))
                                                 : 16u * static_cast<uint32_t>(c);
                         const uint4 q = *reinterpret_cast<const uint4 *>(tsm + qo);
                         const uint4 qa[1] = {q};
@@ -947,7 +984,7 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     okf = __shfl_sync(0xffffffffu, okf, 0);
                     if (lane == 0) {
                         if (!okf) *abort_s = 1;
-                        half_s[b] = r.v;
+                        half_s[b * (NRP - 1) + part - 1] = r.v;
                         mbar_arrive(&half_done[b]);
                     }
                     __syncwarp();
@@ -959,7 +996,9 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 okh = __shfl_sync(0xffffffffu, okh, 0);
                 if (lane == 0) {
                     if (okh) {
-                        r.v = K::op(r.v, half_s[b]);  // first half, then second
+#pragma unroll
+                        for (int q = 0; q < NRP - 1; ++q)  // parts in order
+                            r.v = K::op(r.v, half_s[b * (NRP - 1) + q]);
                     } else {
                         *abort_s = 1;
                     }
@@ -1200,7 +1239,8 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 __syncwarp();
                 if (lane == 0) {
                     if constexpr (SWO) {
-                        tensor_s2g_3d(&p.tm_y, region, 0, 0, static_cast<int>(t * CW + warp));
+                        tensor_s2g_3d(&p.tm_y, region, 0, 0,
+                                      static_cast<int>((t * CW + warp) * kOutWarpBlocks));
                     } else {
                         bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
                     }
@@ -1445,6 +1485,26 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 has_fin_f<K>::value && sizeof(Out) == 2 && ITEMS % 2 == 0;
             Out o[ITEMS];
             float of[kPackBf16Out ? ITEMS : 1];
+            // element i's output from base b and in-thread prefix pv
+            auto emit = [&](int i, const CarA &b, const Acc &pv) {
+                if constexpr (kPackBf16Out) {
+                    of[i] = K::fin_f(b, pv);
+                } else {
+                    o[i] = K::fin(b, pv);
+                }
+            };
+            if constexpr (!SG) {
+                // no heads: one base for the thread, and the inclusive /
+                // exclusive choice made once rather than per element
+                if (p.inclusive) {
+#pragma unroll
+                    for (int i = 0; i < ITEMS; ++i) emit(i, B, v[i]);
+                } else {
+                    emit(0, B, K::ident());
+#pragma unroll
+                    for (int i = 1; i < ITEMS; ++i) emit(i, B, v[i - 1]);
+                }
+            } else {
 #pragma unroll
             for (int i = 0; i < ITEMS; ++i) {
                 Acc pv;
@@ -1463,11 +1523,8 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                     pf = SG && ((hb & ((1u << i) - 1u)) != 0u);
                 }
                 const CarA b = pf ? BI : ((SG && tbf) ? BL : B);
-                if constexpr (kPackBf16Out) {
-                    of[i] = K::fin_f(b, pv);
-                } else {
-                    o[i] = K::fin(b, pv);
-                }
+                emit(i, b, pv);
+            }
             }
             if constexpr (kPackBf16Out) {
                 // bf16 output: each pair rounded and packed by one conversion
@@ -1504,8 +1561,9 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
                 __syncwarp();
                 if (lane == 0) {
                     if constexpr (SWO) {
-                        // this warp's rows: box t CW + warp of y's map
-                        tensor_s2g_3d(&p.tm_y, region, 0, 0, static_cast<int>(t * CW + warp));
+                        // this warp's rows: 1024-byte blocks (t CW + warp) kOutWarpBlocks ..
+                        tensor_s2g_3d(&p.tm_y, region, 0, 0,
+                                      static_cast<int>((t * CW + warp) * kOutWarpBlocks));
                     } else {
                         bulk_s2g(ty + warp * 32 * ITEMS, region, WBYTES);
                     }

@@ -86,19 +86,23 @@ def test_ties_swizzled_tile_order(dtype):
     """Full tiles of a single array sit in shared memory with their 16-byte
     chunks swizzled by row (a row is one thread's elements), and the fp32 /
     bf16 max reducer searches a tile whose maximum is a zero for its first
-    zero.  Here a -0 opens row 4 of tile 1 and a +0 sits in the chunk of the
-    same row that the swizzle places first in shared memory: element order
-    and shared-memory order disagree, and only element order gives -0 as the
-    tile's total and as every later output."""
+    zero.  Here a -0 opens row 4 of tile 1 and a +0 sits in a later chunk of
+    the same row that the swizzle places before it in shared memory: element
+    order and shared-memory order disagree, and only element order gives -0
+    as the tile's total and as every later output."""
     isz = 2 if dtype == "bf16" else 4
     epc = 16 // isz
     for config in range(1, _lib.lscan_num_configs() + 1):
         info = _lib.lscan_config_info(config, LDT[dtype])
         tile, items = info["tile"], info["items"]
         rb = items * isz                       # row bytes
-        rows = max(rb // 16, 1)                # chunks per row
-        xr = ((4 * rb) >> 7) & (rows - 1)      # row 4's chunk XOR
-        later = xr if xr else 1                # (16-byte rows: the next row)
+        chunks = max(rb // 16, 1)              # 16-byte chunks per row
+
+        def phys(b):                           # the 128-byte swizzle
+            return b ^ (((b >> 7) & 7) << 4)
+        base = 4 * rb                          # row 4
+        ahead = [j for j in range(1, chunks) if phys(base + 16 * j) < phys(base)]
+        later = ahead[0] if ahead else 1       # (16-byte rows: the next row)
         n = 3 * tile
         x = np.full(n, -1.0, dtype=np.float32)
         first = tile + 4 * items
