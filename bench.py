@@ -108,17 +108,17 @@ def _kernel_source_hash():
 # reported traffic null until it is measured again (files listed in
 # _NOT_SCAN_SOURCES excepted).
 _TRAFFIC = {
-    "kernel_source_hash": "86bf72a9d9aaa39f",
+    "kernel_source_hash": "8cc17aee046ee2af",
     "bytes_per_launch": {  # (case, tile configuration)
-        ("i32_add", 6): 1077992192 + 1019292928,
-        ("i32_max", 6): 1078018816 + 1016235264,
-        ("f32_add", 6): 1078023936 + 1016182272,
-        ("i32_add", 8): 1075898368 + 1018773760,
-        ("i32_max", 8): 1076087552 + 1015642368,
-        ("f32_add", 8): 1075936768 + 1016081920,
-        ("i32_add", 17): 1075217408 + 1018725376,
-        ("i32_max", 17): 1075224576 + 1015169792,
-        ("f32_add", 17): 1075270144 + 1015724544,
+        ("i32_add", 6): 1077993216 + 1019572992,
+        ("i32_max", 6): 1077990912 + 1016316160,
+        ("f32_add", 6): 1078080512 + 1016428032,
+        ("i32_add", 8): 1075898880 + 1019142656,
+        ("i32_max", 8): 1075948800 + 1016191744,
+        ("f32_add", 8): 1075965952 + 1016437504,
+        ("i32_add", 17): 1075273472 + 1018695168,
+        ("i32_max", 17): 1075228928 + 1015876352,
+        ("f32_add", 17): 1075234304 + 1015827200,
     },
 }
 

@@ -315,8 +315,8 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
         tp.reserved = 0;
         tp.total_out = ls.total_out;
         void *args[] = {&tp};
-        if (cudaLaunchKernel(g_tiny_kernels[ls.kind], dim3(1), dim3(kTinyThreads), args, 0,
-                             cs) != cudaSuccess)
+        if (launch_serialized(g_tiny_kernels[ls.kind], dim3(1), dim3(kTinyThreads), 0, cs, args) !=
+            cudaSuccess)
             return LSCAN_ERR_CUDA;
         g_launches.fetch_add(1);
         return LSCAN_OK;
@@ -373,8 +373,8 @@ lscan_status launch_scan(const LaunchSpec &ls, const DevBuffers &buf,
             return LSCAN_ERR_CUDA;
     }
     void *args[] = {&p};
-    cudaError_t ce = cudaLaunchKernel(e.fn, dim3(static_cast<unsigned>(grid)),
-                                      dim3(e.threads), args, e.smem, cs);
+    cudaError_t ce = launch_serialized(e.fn, dim3(static_cast<unsigned>(grid)),
+                                       dim3(e.threads), e.smem, cs, args);
     if (ce != cudaSuccess) return LSCAN_ERR_CUDA;
     g_launches.fetch_add(1);
     return LSCAN_OK;
@@ -508,6 +508,21 @@ void ensure_kernels_registered() { std::call_once(g_reg_once, register_all_kerne
 int carry_words(int kind) { return g_kernels[kind][MODE_SINGLE][1].car_words; }  // config 1
 
 void note_launch() { g_launches.fetch_add(1); }
+
+cudaError_t launch_serialized(const void *fn, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, void **args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = stream;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelExC(&lc, fn, args);
+}
 
 }  // namespace lscan
 

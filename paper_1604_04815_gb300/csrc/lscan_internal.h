@@ -76,6 +76,13 @@ void shutdown_host_pipes();  // frees the staging of lscan_scan_host
 void shutdown_radix();       // frees the counters of lscan_radix_offsets
 int dtype_size(int dt);
 void note_launch();  // counts one kernel launch of this library
+
+// cudaLaunchKernel with programmatic stream serialization: the kernel's CTAs
+// may be scheduled while the previous kernel of the stream finishes.  Only
+// for kernels that wait for their predecessor (griddepcontrol.wait) before
+// they touch global memory.
+cudaError_t launch_serialized(const void *fn, dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, void **args);
 // entry = configuration | carry << 8
 void set_tuned_variant(int kind, int mode, int size_cls, int entry);
 

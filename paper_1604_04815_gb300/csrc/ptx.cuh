@@ -102,6 +102,19 @@ __device__ __forceinline__ void tensor_s2g_3d(const void *tmap, const void *ssrc
         : "memory");
 }
 
+// Programmatic dependent launch: wait until the grids this one depends on
+// (the previous kernel in the stream, when launched with programmatic
+// stream serialization) have completed and their memory is visible; a
+// no-op otherwise.
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+// Lets the next kernel in the stream (if launched with programmatic stream
+// serialization) start its CTAs once every CTA of this grid has issued it.
+__device__ __forceinline__ void grid_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
 __device__ __forceinline__ void bulk_commit() {
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }

@@ -29,6 +29,7 @@
 
 #include "../../include/lscan.h"
 #include "lscan_internal.h"
+#include "ptx.cuh"
 
 namespace lscan {
 namespace {
@@ -114,6 +115,10 @@ template <class Key>
 __global__ void __launch_bounds__(kRadixThreads, 3) radix_offsets_kernel(const RadixParams p) {
     extern __shared__ uint32_t hist[];  // copies x P x B
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // launched with programmatic stream serialization: wait for the previous
+    // kernel of the stream (it may have re-armed this scratch) first
+    grid_dependency_wait();
+    grid_launch_dependents();
     const int b = p.digit_bits, P = p.positions, B = 1 << b;
     const int NB = P * B;
     const Key mask = static_cast<Key>(B - 1);
@@ -196,6 +201,10 @@ __device__ __forceinline__ void count_pair(uint32_t *tab, Key k, int sh, int m,
 template <class Key>
 __global__ void __launch_bounds__(kPairThreads, 1) radix_pairs_kernel(const RadixParams p) {
     extern __shared__ uint32_t tab[];  // kPairWords, then row and column sums
+    // launched with programmatic stream serialization: wait for the previous
+    // kernel of the stream (it may have re-armed this scratch) first
+    grid_dependency_wait();
+    grid_launch_dependents();
     uint32_t *srow = tab + kPairWords;     // [256] by the high digit of the pair
     uint32_t *scol = srow + 256;           // [256] by the low digit
     const int tid = threadIdx.x, lane = tid & 31;
@@ -396,8 +405,8 @@ extern "C" lscan_status lscan_radix_offsets(const void *keys, int32_t key_bytes,
     rp.aligned = reinterpret_cast<uintptr_t>(keys) % 16 == 0 ? 1 : 0;
     rp.groups = group;
     void *args[] = {&rp};
-    if (cudaLaunchKernel(fn, dim3(static_cast<unsigned>(grid)), dim3(threads), args, fn_smem,
-                         cs) != cudaSuccess)
+    if (launch_serialized(fn, dim3(static_cast<unsigned>(grid)), dim3(threads), fn_smem, cs,
+                          args) != cudaSuccess)
         return LSCAN_ERR_CUDA;
     note_launch();
     return LSCAN_OK;

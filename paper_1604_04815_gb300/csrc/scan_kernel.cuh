@@ -636,6 +636,13 @@ __global__ void __launch_bounds__(kernel_threads<K, Cfg, MODE, TMA>(), Cfg::MINB
         fence_mbar_init();
     }
     __syncthreads();
+    // Launched with programmatic stream serialization, this CTA may start
+    // while the previous kernel of the stream still runs: everything above
+    // touched only this CTA's shared memory.  Wait for that kernel (its
+    // writes, and the scratch it re-armed at its end, are then visible),
+    // then let the next kernel's CTAs be scheduled early in turn.
+    grid_dependency_wait();
+    grid_launch_dependents();
 
     const uint32_t epoch = *reinterpret_cast<volatile uint32_t *>(p.ctl + CTL_EPOCH);
     const uint32_t ebase = (epoch & kEpochMask) << 2;

@@ -28,6 +28,10 @@ __global__ void __launch_bounds__(kTinyThreads) lscan_tiny_kernel(const TinyPara
     __shared__ __align__(16) uint8_t buf[kTinyMax * EB];
     __shared__ Acc wsum[W];
 
+    // launched with programmatic stream serialization: wait for the
+    // previous kernel of the stream before reading or writing global memory
+    grid_dependency_wait();
+    grid_launch_dependents();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = p.n;
     const In *x = static_cast<const In *>(p.x);
