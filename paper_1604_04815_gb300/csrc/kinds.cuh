@@ -274,10 +274,10 @@ struct KFAddDF {
 template <class InT, class OutT>
 struct KFAddComp {
     static constexpr bool kTieOrdered = false;
-    // two reducer warps fold a tile's halves where one CTA runs per SM (a
-    // compensated fold per element is as much arithmetic as the consumers'
-    // scan: one reducer warp on one SM sub-partition carries twice the load
-    // of the others)
+    // several reducer warps fold a tile's parts where one CTA runs per SM
+    // (a compensated fold per element is as much arithmetic as the
+    // consumers' scan: one reducer warp on one SM sub-partition carries
+    // twice the load of the others)
     static constexpr bool kSplitReduce = true;
     using In = InT;
     using Out = OutT;
