@@ -32,7 +32,14 @@
  *    cudaMalloc and released by lscan_shutdown().  Growing it is not allowed
  *    while the stream is being captured; call lscan_reserve() first.
  *  - Different streams may be used from different host threads concurrently;
- *    two calls on the same stream are ordered by the stream.
+ *    two calls on the same stream are ordered by the stream.  A host thread
+ *    with no current CUDA context gets the current device's primary context
+ *    bound by its first call (as any CUDA runtime call would bind it).
+ *  - The scan, single-CTA and digit-offset kernels are launched with
+ *    programmatic stream serialization: their thread blocks may be
+ *    scheduled while the previous kernel of the stream is finishing, but
+ *    each waits for that kernel to complete (and its writes to be visible)
+ *    before it reads or writes global memory, so stream order holds.
  *  - Output dtype equals the input dtype, except bf16 add, which writes fp32
  *    unless lscan_options.out_dtype asks for bf16.
  *  - int32 add wraps modulo 2^32; max keeps the earlier element on ties
