@@ -281,6 +281,30 @@ def test_many_launches_epoch_and_ticket_rearm():
             assert_matches("add", "i32", x, to_host(outs[rep * len(xs) + i]))
 
 
+def test_chained_scans_back_to_back_in_one_stream():
+    """Each scan reads the previous one's output, queued without a host
+    synchronisation: kernels launched with programmatic stream serialization
+    may start while their predecessor finishes, and must still see all of
+    its output (persistent -> persistent -> single-CTA -> persistent)."""
+    import oracle
+    rng = np.random.default_rng(29)
+    n = 3_000_017
+    x = random_array("i32", n, rng, kind="full")
+    xd = to_device(x, "i32")
+    y1 = run_c_abi("add", "i32", xd, True, check_status=False)
+    y2 = run_c_abi("add", "i32", y1, True, check_status=False)
+    y3 = run_c_abi("add", "i32", y2[:4000], False, check_status=False)
+    y4 = run_c_abi("add", "i32", y2, False, check_status=False)
+    s = torch.cuda.current_stream().cuda_stream
+    assert _lib.lscan_stream_status(s) == _lib.LSCAN_OK
+    w1 = oracle.scan("add", "i32", x, True)
+    w2 = oracle.scan("add", "i32", w1, True)
+    assert np.array_equal(to_host(y1), w1)
+    assert np.array_equal(to_host(y2), w2)
+    assert np.array_equal(to_host(y3), oracle.scan("add", "i32", w2[:4000], False))
+    assert np.array_equal(to_host(y4), oracle.scan("add", "i32", w2, False))
+
+
 def test_new_host_thread_on_a_used_stream():
     """A host thread whose first library call reuses a stream (and so its
     scratch) set up by another thread: it makes no CUDA call that binds a
