@@ -8,14 +8,14 @@
 //    is resident; the ticket keeps the "earlier tiles are owned by running
 //    blocks" property under any residency, e.g. beside concurrent kernels).
 //  * Loads (Section 4.1 step 1, Section 4.5).  One producer warp per CTA
-//    issues cp.async.bulk copies of whole tiles into a STAGES-deep shared
-//    memory ring, up to STAGES-1 tiles ahead, so HBM reads stay in flight
-//    while the consumer warps wait on a carry (the ragged last tile of an
-//    array: a bulk copy of its 16-byte-aligned prefix, the last few bytes
-//    copied by the producer lanes).  x is read exactly once.
+//    copies whole tiles (tensor copies with the 128-byte swizzle, or plain
+//    bulk copies) into a STAGES-deep shared-memory ring, STAGES-1 tiles
+//    ahead, so HBM reads stay in flight while the consumer warps wait on a
+//    carry (a ragged last tile: a bulk copy of its 16-byte-aligned prefix,
+//    the last few bytes copied by the producer lanes).  x is read once.
 //  * Intra-warp local scan (Section 4.1, Algorithm 2).  Each thread holds
-//    ITEMS consecutive elements (read from shared memory as 16-byte vectors,
-//    XOR-rotated so that each quarter-warp touches 32 distinct banks), scans
+//    ITEMS consecutive elements (16-byte shared-memory reads that cover all
+//    32 banks per quarter-warp: swizzled tiles, or XOR-rotated reads), scans
 //    them sequentially (the matrix-scan row of Section 2.3), then the warp
 //    runs the Hillis-Steele shuffle scan of Section 2.1 on the 32 thread
 //    totals (5 rounds of shfl.up).
@@ -33,10 +33,10 @@
 //    reports DEV_ERR_CARRY_WAIT instead of hanging.
 //  * Intra-block global scan (Section 4.4, Algorithm 5).  Each element gets
 //    carry (+) block offset (+) lane offset (+) own prefix, and y is written
-//    exactly once: staged per warp in shared memory and stored with
-//    cp.async.bulk (full tiles) or with coalesced plain stores from the same
-//    staging (the ragged last tile); unaligned pointers take plain stores
-//    straight from registers.
+//    exactly once: staged per warp in shared memory and stored with a tensor
+//    or bulk copy (full tiles) or coalesced plain stores from the staging
+//    (the ragged last tile); unaligned pointers take plain stores straight
+//    from registers.
 //  * Batched mode (MODE_SEGMENTED, not in the paper).  The producer warp
 //    marks segment heads of its tile in a bitmap (warp-parallel lower_bound
 //    on the offsets); the scan operator is lifted to (head flag, value); a
